@@ -1,0 +1,374 @@
+"""Benchmark of the SPSTD hot path on GB300: grid-point-steps per second.
+
+Default workload: the 3D anisotropic harmonic oscillator at scale -- 256^3 grid
+on [-12, 12]^3, omegas (1.0, 1.3, 1.7), five seeded Gaussians, FP32 fields
+with FP64 reductions, the six-stage SUZUKI6 integrator (11 half-stages per
+step), 8 probes recorded every step.  One "step" is one full time step of
+Eq. 17/18 (every half-stage: FFT second derivatives along x, y, z, the V term
+and the axpy) plus the probe record.  The fields (3 x 64 MB) are larger than
+the 129 MB L2, so no flush is needed between timed steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank runs an independent replica (weak scaling; the solves
+share no data, so there is no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "aniso_ho_3d_256": dict(precision=32),
+    "ho_3d_64_fp32": dict(precision=32),
+    "ho_3d_64_fp64": dict(precision=64),
+}
+
+
+def make_problem(name, steps):
+    from paper_1805_03155_gb300 import inputs
+    if name == "aniso_ho_3d_256":
+        return inputs.aniso_ho_3d(steps=steps)
+    return inputs.ho_3d(steps=steps)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def algorithmic_bytes(kind, n_total, es):
+    """Compulsory bytes of one launch: x pass reads src, V, dst and writes dst;
+    a strided pass reads src, dst and writes dst."""
+    return (4 if kind == "x_pass" else 3) * es * n_total
+
+
+def cpu_baseline(problem, budget_s=20.0):
+    """The FP64 oracle on the host: one half-stage (K apply + axpy) on the
+    full grid, repeated while the budget lasts, scaled to grid-point-steps/s
+    with the integrator's half-stages per step."""
+    import oracle
+
+    g = oracle.make_grid(problem.dims, problem.n[: problem.dims], problem.lo[: problem.dims],
+                         problem.hi[: problem.dims], problem.hbar, problem.mass)
+    c, d = oracle.preset(problem.integrator)
+    h = int(np.count_nonzero(c) + np.count_nonzero(d))
+    reps, t0 = 0, time.perf_counter()
+    R = problem.psiR.copy()
+    while True:
+        k = oracle.apply_K(problem.psiI, problem.V, g)
+        R += c[0] * problem.dt * k
+        reps += 1
+        if time.perf_counter() - t0 > budget_s / 2 or reps >= 64:
+            break
+    t = (time.perf_counter() - t0) / reps
+    return {"value": problem.n_total / (h * t), "unit": "grid-point-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"{reps} half-stage(s) (K apply + axpy) on the full {problem.n_total}-point grid, "
+                      f"{t:.2f} s each, scaled by {h} half-stages per step; single thread, FP64"}
+
+
+def run_reference(args):
+    """The oracle as it stands, on the host cores, same metric and workload.
+    Each step is a bounded sample of one half-stage: the oracle's spectral
+    second derivative along x, y and z over 256 full-length lines per axis
+    (the per-line work of a full-grid K apply), plus the V term and the axpy,
+    scaled to grid-point-steps/s by the half-stages per step."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    problem = make_problem(args.workload, 1)
+    c, d = oracle.preset(problem.integrator)
+    h = int(np.count_nonzero(c) + np.count_nonzero(d))
+    n = problem.n[0]
+    lines = 256 if n >= 16 else n * n
+    side = int(round(np.sqrt(lines)))
+    lo, hi = problem.lo[:3], problem.hi[:3]
+    grids = []
+    for ax in range(3):
+        shape = [side, side, side]
+        shape[ax] = problem.n[ax]
+        grids.append((ax, oracle.make_grid(3, shape, lo, hi, problem.hbar, problem.mass)))
+    S = side * side * n
+    rng = np.random.default_rng(0)
+    src = rng.standard_normal(S)
+    V = rng.standard_normal(S)
+    dst = np.zeros(S)
+
+    def sample():
+        acc = (V / problem.hbar) * src
+        for ax, g in grids:
+            acc += problem.hbar / (2 * problem.mass) * oracle.laplacian_axis(src, g, ax)
+        dst[:] += c[0] * problem.dt * acc
+
+    for _ in range(args.warmup):
+        sample()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sample()
+    t = time.perf_counter() - t0
+    value = S * args.steps / (h * t)
+    what = (f"each step: the oracle's x, y and z line transforms over {side * side} full-length lines per axis "
+            f"({S} grid points, the per-point work of one half-stage) plus the V term and axpy, scaled by "
+            f"{h} half-stages per step; single thread, FP64")
+    out = {"impl": "reference", "metric": "grid-point-steps/s", "value": value, "unit": "grid-point-steps/s",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * t * h * (problem.n_total / S) / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": args.workload, "grid": list(problem.n), "integrator": problem.integrator},
+           "cpu_baseline": {"value": value, "unit": "grid-point-steps/s", "cores": 1, "kind": "oracle",
+                            "sample": what},
+           "e2e": {"value": value, "unit": "grid-point-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="aniso_ho_3d_256", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_1805_03155_gb300 import build, spstd
+    if rank == 0 or not os.path.exists(build.LIB):
+        build.build()
+    if dist is not None:
+        dist.barrier()
+
+    wl = WORKLOADS[args.workload]
+    prec = wl["precision"]
+    es = 4 if prec == 32 else 8
+    problem = make_problem(args.workload, args.steps)
+    total_steps = args.warmup + args.steps + 8
+    stream = torch.cuda.Stream(device=local)
+    s = spstd.solver_for(problem, precision=prec, probe_capacity=total_steps, stream=stream, device=local)
+    N = problem.n_total
+
+    # warm-up (also captures the step graph)
+    s.spstd_step(args.warmup)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, device resident -------------------------------
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    s.spstd_step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    launches = s.spstd_launch_count(args.steps)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = N * args.steps * ws / (ms * 1e-3)
+
+    # ---- per-kernel device times (event pair around each launch) ------------
+    prof_steps = max(2, min(8, args.steps))
+    prof = s.spstd_profile_steps(prof_steps)
+    kinds = {k: v for k, v in prof.items() if v[1] > 0}
+    dom = max(kinds, key=lambda k: kinds[k][0])
+    dom_ms = kinds[dom][0] / kinds[dom][1]
+    peak, peak_src = measured_peaks()
+    abytes = algorithmic_bytes(dom, N, es)
+    achieved = abytes / (dom_ms * 1e-3) / 1e9
+    step_bytes = sum(algorithmic_bytes(k, N, es) * kinds[k][1] for k in ("x_pass", "y_pass", "z_pass")
+                     if k in kinds) / prof_steps
+    half_stages = kinds.get("x_pass", (0, 0))[1] // prof_steps
+
+    # ---- end to end through the C ABI with pinned host buffers --------------
+    pin_r = torch.empty(N, dtype=torch.float64, pin_memory=True)
+    pin_i = torch.empty(N, dtype=torch.float64, pin_memory=True)
+    pin_r.numpy()[:] = problem.psiR
+    pin_i.numpy()[:] = problem.psiI
+    hr, hi_ = pin_r.numpy(), pin_i.numpy()
+    out_r = torch.empty(N, dtype=torch.float64, pin_memory=True).numpy()
+    out_i = torch.empty(N, dtype=torch.float64, pin_memory=True).numpy()
+    probe_bytes = 16 * len(problem.probes)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.spstd_set_state(hr, hi_)
+    chunk = 10
+    done = 0
+    while done < args.steps:
+        n = min(chunk, args.steps - done)
+        s.spstd_step(n)
+        for q in range(len(problem.probes)):
+            s.spstd_probe(q, cap=n)
+        done += n
+    s.spstd_get_state(out_r, out_i)
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([t_e2e], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    nv, ev = s.spstd_energy_norm()
+    s.close()
+
+    if rank == 0:
+        out = {
+            "metric": "grid-point-steps/s",
+            "value": value,
+            "unit": "grid-point-steps/s",
+            "n_gpus": ws,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": ms / args.steps,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32" if prec == 32 else "f64",
+            "data": "synthetic",
+            "config": {
+                "workload": args.workload,
+                "grid": list(problem.n),
+                "box": [problem.lo[0], problem.hi[0]],
+                "integrator": problem.integrator,
+                "half_stages_per_step": int(half_stages),
+                "fields": "fp32" if prec == 32 else "fp64",
+                "reductions": "fp64",
+                "probes": len(problem.probes),
+                "dt": problem.dt,
+                "l2_policy": "inputs larger than L2 (psi_R, psi_I, V = 3 x %d MB), no flush" % (N * es >> 20)
+                             if 3 * N * es > 129 * 2 ** 20 else "L2-resident grid: not flushed between steps",
+                "parallelism": f"replicas{ws}",
+            },
+            "clocks": clk,
+            "gpu_launches": int(launches),
+            "roofline": {
+                "bound": "hbm",
+                "kernel": dom,
+                "achieved": achieved,
+                "peak": peak,
+                "unit": "GB/s",
+                "frac": achieved / peak,
+                "peak_source": f"{peak_src} hbm_gbs (burst copy)",
+                "traffic": None,
+                "algorithmic_bytes_per_launch": abytes,
+                "avg_launch_ms": dom_ms,
+                "step_algorithmic_bytes": step_bytes,
+                "step_floor_bytes": 4 * es * N * half_stages,
+                "step_floor_frac": (4 * es * N * half_stages) / (ms / args.steps * 1e-3) / 1e9 / peak,
+                "per_kernel_ms": {k: v[0] / v[1] for k, v in kinds.items()},
+                "per_kernel_share": {k: v[0] / sum(x[0] for x in kinds.values()) for k, v in kinds.items()},
+            },
+            "e2e": {
+                "value": N * args.steps * ws / t_e2e,
+                "unit": "grid-point-steps/s",
+                "h2d_bytes_per_step": 2 * 8 * N / args.steps,
+                "d2h_bytes_per_step": (2 * 8 * N + probe_bytes * args.steps) / args.steps,
+                "what": "spstd_set_state from pinned FP64 host arrays, K steps in chunks of 10 with every "
+                        "probe read back after each chunk, spstd_get_state to pinned FP64 host arrays",
+            },
+            "check": {"norm_after": nv, "energy_after": ev},
+        }
+        if not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(problem)
+        print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,205 @@
+/*
+ * spstd.h -- C ABI of the GB300 (sm_103a) SPSTD library.
+ *
+ * The library advances the time-dependent Schroedinger equation
+ *     i hbar d psi/dt = -(hbar^2/2m*) lap psi + V(r) psi            (Eq. 1)
+ * split into the real fields psi = psi_R + i psi_I (Eq. 2-4), with the
+ * symplectic pseudospectral time-domain (SPSTD) scheme of arXiv 1805.03155:
+ * spatial second derivatives by FFT (Eq. 7-10) and an m-stage partitioned
+ * symplectic product in time (Eq. 14-18).  Eigen-energies are read off the
+ * spectrum of probe-point time series (Tables 2-4).
+ *
+ * Conventions shared by every entry point:
+ *  - Every call returns an spstd_status; nothing throws across the ABI.
+ *  - Grids are periodic boxes [lo_d, hi_d) with n_d points per axis,
+ *    x_j = lo + j (hi - lo)/n (Eq. 5/6).  Field arrays are [n2][n1][n0] with
+ *    axis 0 (x) fastest; unused axes have n = 1.
+ *  - Host arrays are owned by the caller and only read or written during the
+ *    call (set_* copy in, get_* copy out).
+ *  - Device memory: the caller allocates ONE device buffer of
+ *    spstd_workspace_size() bytes (256-byte aligned) and hands it to
+ *    spstd_create(); the library carves all its device state from it and never
+ *    allocates device memory itself.  The buffer must outlive the context.
+ *  - All device work is enqueued on cfg.stream (NULL = the legacy default
+ *    stream).  spstd_step() returns without waiting; the calls that return
+ *    host results (get_state, probe, spectrum, energy_norm,
+ *    apply_hamiltonian) synchronise that stream.
+ *  - A context is not thread safe; distinct contexts are independent.
+ *  - On error the context keeps its previous state where possible and
+ *    spstd_last_error() describes the failure.
+ */
+#ifndef SPSTD_H
+#define SPSTD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct spstd_ctx spstd_ctx;
+
+typedef enum {
+    SPSTD_OK = 0,
+    SPSTD_EINVAL = 1,       /* bad argument (NULL, size out of range, bad index) */
+    SPSTD_ENOMEM = 2,       /* workspace too small, or host allocation failed */
+    SPSTD_ECUDA = 3,        /* a CUDA runtime call failed (message in last_error) */
+    SPSTD_EUNSTABLE = 4,    /* dt above the stability limit s_star/w_max (Eq. 25/30) */
+    SPSTD_EDIVERGED = 5,    /* norm or energy is NaN/Inf */
+    SPSTD_ETIMEOUT = 6,     /* reserved: a bounded device wait gave up */
+    SPSTD_ENOTREADY = 7,    /* nothing to return yet (no probe samples) */
+    SPSTD_EUNSUPPORTED = 8  /* valid request this build does not implement */
+} spstd_status;
+
+/* Integrator presets for Eq. 17 (coefficients c_l, d_l, l = 1..m).
+ *  SPSTD_LEAPFROG  m = 1, c = d = 1: the traditional explicit PSTD update
+ *                  (Eq. 11/12), order 1 in this partitioned form.
+ *  SPSTD_STRANG    m = 2, c = (1/2, 1/2), d = (1, 0): order 2.
+ *  SPSTD_PAPER3    the paper's set (after Eq. 18): c = (0.26833010,
+ *                  -0.18799162, 0.91966152), d_l = c_{m-l+1}.
+ *  SPSTD_FR4       Yoshida triple jump of the Strang step (order 4),
+ *                  x = 1/(2 - 2^(1/3)): c = (x/2, (1-x)/2, (1-x)/2, x/2),
+ *                  d = (x, 1-2x, x, 0).
+ *  SPSTD_SUZUKI6   Suzuki five-fold Strang composition (order 4),
+ *                  p = 1/(4 - 4^(1/3)): c = (p/2, p, (1-3p)/2, (1-3p)/2, p, p/2),
+ *                  d = (p, p, 1-4p, p, p, 0).
+ *  SPSTD_CUSTOM    use cfg.m, cfg.c, cfg.d as given (m <= 8). */
+enum {
+    SPSTD_CUSTOM = -1,
+    SPSTD_LEAPFROG = 0,
+    SPSTD_STRANG = 1,
+    SPSTD_PAPER3 = 2,
+    SPSTD_FR4 = 3,
+    SPSTD_SUZUKI6 = 4
+};
+
+#define SPSTD_MAX_STAGES 8
+#define SPSTD_MAX_PROBES 16
+
+typedef struct {
+    int dims;             /* 1, 2 or 3 */
+    int64_t n[3];         /* points per axis, x first.  Each used axis: a power
+                             of two, 2 <= n <= 8192 for dims == 1 and
+                             2 <= n <= 1024 otherwise; unused axes: 1 */
+    double lo[3], hi[3];  /* periodic box per axis, hi > lo */
+    double hbar, mass;    /* hbar and effective mass m* (> 0) */
+    int precision;        /* 32 or 64: type of the fields and of the FFTs;
+                             reductions and spectra are FP64 in both */
+    int preset;           /* SPSTD_* preset id, or SPSTD_CUSTOM */
+    int m;                /* SPSTD_CUSTOM only: stages (1..8) */
+    double c[SPSTD_MAX_STAGES], d[SPSTD_MAX_STAGES]; /* SPSTD_CUSTOM only */
+    double dt;            /* time step; <= 0 selects half the stability limit */
+    int n_probe;          /* 0..16 probe points */
+    int64_t probe_idx[SPSTD_MAX_PROBES]; /* flat grid index of each probe */
+    int64_t probe_capacity; /* samples kept per probe (ring buffer), >= 1 */
+    int64_t max_nfft;     /* largest spectrum length (power of two); <= 0
+                             selects next_pow2(4 * probe_capacity) */
+    int nyquist_zero;     /* 0: k^2 = (pi/dx)^2 at the Nyquist index (default);
+                             1: Nyquist mode zeroed (literal Eq. 10) */
+    int device;           /* CUDA device ordinal the workspace lives on */
+    void *stream;         /* cudaStream_t for all work; NULL = legacy default */
+} spstd_config;
+
+/* Fills cfg with defaults: dims 1, n = (256, 1, 1), box [0, 1), hbar = m* = 1,
+ * precision 64, SPSTD_FR4, dt = 0 (auto), no probes, capacity 1024. */
+void spstd_config_init(spstd_config *cfg);
+
+/* Bytes of device workspace a context for cfg needs.  Validates cfg
+ * (SPSTD_EINVAL / SPSTD_EUNSUPPORTED / SPSTD_EUNSTABLE as spstd_create). */
+spstd_status spstd_workspace_size(const spstd_config *cfg, size_t *bytes);
+
+/* Stability of the configured scheme (Eq. 23-25, Table 1): s_star is the
+ * largest s with |tr M(s')| <= 2 for all 0 <= s' <= s, M the per-mode step
+ * matrix; dt_max = s_star / w_max with the Weyl bound
+ * w_max = (hbar/2m*) sum_d (pi/dx_d)^2 + max(V, 0)/hbar, using vmax for max V. */
+spstd_status spstd_stability_limit(const spstd_config *cfg, double vmax, double *s_star,
+                                   double *dt_max);
+
+/* Creates a context on the caller's workspace (device pointer, 256-byte
+ * aligned, >= spstd_workspace_size bytes).  Uploads the FFT twiddles and the
+ * per-stage k^2 multipliers (both computed in FP64 and rounded to the field
+ * precision once).  Fields start at zero, V at zero.  If cfg.dt <= 0 the time
+ * step is chosen at set_potential time as half the stability limit.
+ * *out is NULL on failure. */
+spstd_status spstd_create(const spstd_config *cfg, void *d_workspace, size_t workspace_bytes,
+                          spstd_ctx **out);
+
+/* Releases the host side of the context (the workspace stays the caller's).
+ * Waits for the context's stream first.  NULL is accepted. */
+spstd_status spstd_destroy(spstd_ctx *ctx);
+
+/* Copies V (host, FP64, n_total values, x fastest) to the device, rounded to
+ * the field precision.  Re-derives dt when cfg.dt <= 0 and re-checks the
+ * stability limit (SPSTD_EUNSTABLE if a fixed dt is above it). */
+spstd_status spstd_set_potential(spstd_ctx *ctx, const double *V);
+
+/* Copies the state (host, FP64, n_total values each) to the device and resets
+ * the probe recorder (step counter 0, no samples). */
+spstd_status spstd_set_state(spstd_ctx *ctx, const double *psiR, const double *psiI);
+
+/* Copies the current state to the host as FP64 (synchronises). */
+spstd_status spstd_get_state(spstd_ctx *ctx, double *psiR, double *psiI);
+
+/* Enqueues nsteps full steps of Eq. 17/18: for l = 1..m,
+ *     psi_R += c_l dt K psi_I,  then  psi_I -= d_l dt K psi_R,
+ * K = -(hbar/2m*) lap + V/hbar (Eq. 16), zero coefficients skipped, and after
+ * every step records psi_R + i psi_I at each probe.  nsteps = 0 is a no-op.
+ * Asynchronous; repeated chunks are replayed from a captured CUDA graph. */
+spstd_status spstd_step(spstd_ctx *ctx, int64_t nsteps);
+
+/* Copies the recorded series of probe p (0 <= p < n_probe), oldest first,
+ * FP64: up to cap samples (the most recent ones if more were kept); *len gets
+ * the count.  SPSTD_ENOTREADY if no step has been recorded. */
+spstd_status spstd_probe(spstd_ctx *ctx, int p, double *re, double *im, int64_t cap,
+                         int64_t *len);
+
+/* Eigen-energies from the spectrum of probe p's series (p = -1: the sum of all
+ * probes), computed on the device in FP64: symmetric Hann window, zero padding
+ * to nfft (power of two, M <= nfft <= max_nfft; <= 0 picks next_pow2(4M)),
+ * peaks among positive energies that are the largest value within the
+ * window's main-lobe half width ceil(2 nfft/M) bins and >= thresh * the
+ * largest, the max_peaks largest kept, each refined by 60 golden-section
+ * steps on the windowed DTFT.  E = hbar theta/dt; with phase_correct != 0 the
+ * map's dispersion is inverted (theta = arccos(tr M(w dt)/2) solved for w) and
+ * E = hbar w.  Outputs sorted by E ascending: E[i], amp[i] (DTFT magnitude
+ * over the window sum), *npeaks <= max_peaks.  Synchronises. */
+spstd_status spstd_spectrum(spstd_ctx *ctx, int p, int64_t nfft, int max_peaks, double thresh,
+                            int phase_correct, double *E, double *amp, int *npeaks);
+
+/* norm = dV sum(psi_R^2 + psi_I^2) and energy = dV sum(psi_R H psi_R +
+ * psi_I H psi_I), H = hbar K, accumulated in FP64 on the device in a fixed
+ * order (bitwise reproducible).  Synchronises.  SPSTD_EDIVERGED if either is
+ * not finite (the values are still written). */
+spstd_status spstd_energy_norm(spstd_ctx *ctx, double *norm, double *energy);
+
+/* out = H psi_which (which 0: psi_R, 1: psi_I) as FP64 on the host, computed by
+ * the same FFT pass kernels as a step.  Synchronises. */
+spstd_status spstd_apply_hamiltonian(spstd_ctx *ctx, int which, double *out);
+
+/* The time step in use, the steps taken since set_state, the integrator. */
+spstd_status spstd_get_dt(const spstd_ctx *ctx, double *dt);
+spstd_status spstd_steps_taken(const spstd_ctx *ctx, int64_t *steps);
+spstd_status spstd_get_coefficients(const spstd_ctx *ctx, int *m, double *c, double *d);
+
+/* Number of kernels spstd_step(ctx, nsteps) runs on the device (kernel nodes
+ * of replayed graphs included). */
+spstd_status spstd_launch_count(const spstd_ctx *ctx, int64_t nsteps, int64_t *launches);
+
+/* Per-kernel timing: runs nsteps steps (real steps: the state advances and the
+ * probes record) with direct launches instead of graph replays, a CUDA event
+ * pair around every launch on the context's stream, and returns per kernel
+ * kind k the summed device time ms[k] (milliseconds) and launch count cnt[k]:
+ * k = 0 x pass, 1 y pass, 2 z pass, 3 probe recorder, 4 resident 1D solver.
+ * Synchronises. */
+#define SPSTD_KERNEL_KINDS 5
+spstd_status spstd_profile_steps(spstd_ctx *ctx, int64_t nsteps, double *ms, int64_t *cnt);
+
+/* Human-readable text of the last failure on ctx (never NULL). */
+const char *spstd_last_error(const spstd_ctx *ctx);
+const char *spstd_status_string(spstd_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPSTD_H */

@@ -1,0 +1,982 @@
+// api.cu -- the C ABI of include/spstd.h: validation, device workspace
+// layout, FP64 host tables, the time-step driver (direct launches and captured
+// CUDA graphs) and the host halves of the reductions and the spectrum.
+//
+// The host code here computes only setup quantities (coefficient presets,
+// the stability limit of Eq. 23-25, twiddle and k^2 tables, dispersion
+// inversion of a few spectrum peaks); every step of the time integration,
+// every reduction and every spectrum runs in the CUDA kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/spstd.h"
+#include "launch.cuh"
+#include "spectrum.h"
+
+using namespace spstd;
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846264338327950288;
+constexpr int kPartials = 1024;        // blocks of the FP64 reductions (fixed: reproducible sums)
+constexpr int kGraphSteps = 16;        // steps per captured graph (2D/3D)
+
+struct HalfStage {
+    int dst;      // field updated: 0 = psi_R, 1 = psi_I
+    int table;    // multiplier table index
+    double a;     // s coef dt hbar/2m*
+    double bV;    // s coef dt/hbar
+};
+
+struct Layout {
+    size_t psi[2], V, tmp, staging, ring, counter, partial, dout, tw[3], mult, spec, total;
+};
+
+bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+int64_t next_pow2(int64_t v)
+{
+    int64_t p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
+
+// ---- integrator coefficients (Eq. 17) ---------------------------------------
+bool preset_coefficients(int id, int *m, double *c, double *d)
+{
+    switch (id) {
+    case SPSTD_LEAPFROG:
+        *m = 1;
+        c[0] = 1.0;
+        d[0] = 1.0;
+        return true;
+    case SPSTD_STRANG:
+        *m = 2;
+        c[0] = c[1] = 0.5;
+        d[0] = 1.0;
+        d[1] = 0.0;
+        return true;
+    case SPSTD_PAPER3: {
+        // printed after Eq. 18, with d_l = c_{m-l+1}
+        const double p[3] = {0.26833010, -0.18799162, 0.91966152};
+        *m = 3;
+        for (int l = 0; l < 3; ++l) {
+            c[l] = p[l];
+            d[l] = p[2 - l];
+        }
+        return true;
+    }
+    case SPSTD_FR4: {
+        const double x = 1.0 / (2.0 - std::cbrt(2.0));
+        const double cc[4] = {x / 2, (1 - x) / 2, (1 - x) / 2, x / 2};
+        const double dd[4] = {x, 1 - 2 * x, x, 0.0};
+        *m = 4;
+        for (int l = 0; l < 4; ++l) {
+            c[l] = cc[l];
+            d[l] = dd[l];
+        }
+        return true;
+    }
+    case SPSTD_SUZUKI6: {
+        const double p = 1.0 / (4.0 - std::cbrt(4.0));
+        const double cc[6] = {p / 2, p, (1 - 3 * p) / 2, (1 - 3 * p) / 2, p, p / 2};
+        const double dd[6] = {p, p, 1 - 4 * p, p, p, 0.0};
+        *m = 6;
+        for (int l = 0; l < 6; ++l) {
+            c[l] = cc[l];
+            d[l] = dd[l];
+        }
+        return true;
+    }
+    default:
+        return false;
+    }
+}
+
+// ---- stability (Eq. 23-25) ---------------------------------------------------
+// Per-mode map of one step for s = w dt in stage order: each stage applies
+// [[1, c s], [0, 1]] then [[1, 0], [-d s, 1]].
+double step_trace(int m, const double *c, const double *d, double s)
+{
+    double m00 = 1, m01 = 0, m10 = 0, m11 = 1;
+    for (int l = 0; l < m; ++l) {
+        m00 += c[l] * s * m10;
+        m01 += c[l] * s * m11;
+        m10 -= d[l] * s * m00;
+        m11 -= d[l] * s * m01;
+    }
+    return m00 + m11;
+}
+
+double stability_s_star(int m, const double *c, const double *d)
+{
+    const double h = 1e-4, smax = 64.0;
+    double s = 0.0;
+    while (s + h <= smax && std::fabs(step_trace(m, c, d, s + h)) <= 2.0) s += h;
+    if (s + h > smax) return smax;
+    double lo = s, hi = s + h;
+    for (int i = 0; i < 200; ++i) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (std::fabs(step_trace(m, c, d, mid)) <= 2.0) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+double map_angle(int m, const double *c, const double *d, double s)
+{
+    double t = 0.5 * step_trace(m, c, d, s);
+    t = std::min(1.0, std::max(-1.0, t));
+    return std::acos(t);
+}
+
+// s with map_angle(s) = theta on the first increasing branch (Eq. 24/25: the
+// eigenvalues of a det-1 map are exp(+-i theta), theta = arccos(tr/2)).
+double dispersion_inverse(int m, const double *c, const double *d, double s_star, double theta)
+{
+    const double h = 1e-4;
+    double top = 0.0;
+    while (top + h <= s_star && map_angle(m, c, d, top + h) > map_angle(m, c, d, top)) top += h;
+    if (theta >= map_angle(m, c, d, top)) return top;
+    double lo = 0.0, hi = top;
+    for (int i = 0; i < 200; ++i) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (map_angle(m, c, d, mid) < theta) lo = mid;
+        else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+double w_max_of(const spstd_config &cfg, double vmax)
+{
+    double w = 0.0;
+    for (int a = 0; a < cfg.dims; ++a) {
+        const double dx = (cfg.hi[a] - cfg.lo[a]) / (double)cfg.n[a];
+        w += (kPi / dx) * (kPi / dx);
+    }
+    return cfg.hbar / (2.0 * cfg.mass) * w + std::max(vmax, 0.0) / cfg.hbar;
+}
+
+// ---- validation and layout ---------------------------------------------------
+spstd_status validate(const spstd_config *cfg, std::string *why, int *m, double *c, double *d)
+{
+    auto bad = [&](const char *w) {
+        if (why) *why = w;
+        return SPSTD_EINVAL;
+    };
+    if (!cfg) return bad("config is NULL");
+    if (cfg->dims < 1 || cfg->dims > 3) return bad("dims must be 1, 2 or 3");
+    if (cfg->precision != 32 && cfg->precision != 64) return bad("precision must be 32 or 64");
+    for (int a = 0; a < 3; ++a) {
+        if (a < cfg->dims) {
+            if (!is_pow2(cfg->n[a]) || cfg->n[a] < 2) return bad("each used axis needs a power-of-two size >= 2");
+            if (!(cfg->hi[a] > cfg->lo[a]) || !std::isfinite(cfg->hi[a] - cfg->lo[a])) return bad("box needs hi > lo");
+        } else if (cfg->n[a] != 1) {
+            return bad("unused axes must have n = 1");
+        }
+    }
+    const int64_t max1 = cfg->precision == 32 ? Launch<float>::resident_max_n() : Launch<double>::resident_max_n();
+    for (int a = 0; a < cfg->dims; ++a) {
+        const int64_t lim = cfg->dims == 1 ? max1 : 1024;
+        if (cfg->n[a] > lim) {
+            if (why) *why = "axis longer than this build supports (1D: 8192 FP32 / 4096 FP64; 2D/3D: 1024)";
+            return SPSTD_EUNSUPPORTED;
+        }
+    }
+    if (!(cfg->hbar > 0) || !(cfg->mass > 0)) return bad("hbar and mass must be > 0");
+    if (cfg->preset == SPSTD_CUSTOM) {
+        if (cfg->m < 1 || cfg->m > SPSTD_MAX_STAGES) return bad("custom integrator needs 1 <= m <= 8");
+        *m = cfg->m;
+        for (int l = 0; l < cfg->m; ++l) {
+            if (!std::isfinite(cfg->c[l]) || !std::isfinite(cfg->d[l])) return bad("non-finite coefficient");
+            c[l] = cfg->c[l];
+            d[l] = cfg->d[l];
+        }
+    } else if (!preset_coefficients(cfg->preset, m, c, d)) {
+        return bad("unknown integrator preset");
+    }
+    int nh = 0;
+    for (int l = 0; l < *m; ++l) nh += (c[l] != 0.0) + (d[l] != 0.0);
+    if (nh == 0) return bad("all integrator coefficients are zero");
+    if (nh > kMaxHalfStages) return bad("too many nonzero coefficients");
+    if (cfg->n_probe < 0 || cfg->n_probe > SPSTD_MAX_PROBES) return bad("n_probe must be 0..16");
+    const int64_t ntot = cfg->n[0] * cfg->n[1] * cfg->n[2];
+    for (int q = 0; q < cfg->n_probe; ++q)
+        if (cfg->probe_idx[q] < 0 || cfg->probe_idx[q] >= ntot) return bad("probe index outside the grid");
+    if (cfg->probe_capacity < 1) return bad("probe_capacity must be >= 1");
+    if (cfg->max_nfft > 0 && (!is_pow2(cfg->max_nfft) || cfg->max_nfft < 4)) return bad("max_nfft must be a power of two >= 4");
+    if (!std::isfinite(cfg->dt)) return bad("dt is not finite");
+    return SPSTD_OK;
+}
+
+int64_t effective_max_nfft(const spstd_config &cfg)
+{
+    if (cfg.max_nfft > 0) return cfg.max_nfft;
+    return std::max<int64_t>(4, next_pow2(4 * cfg.probe_capacity));
+}
+
+Layout make_layout(const spstd_config &cfg, int m)
+{
+    Layout L{};
+    const int64_t ntot = cfg.n[0] * cfg.n[1] * cfg.n[2];
+    const size_t es = cfg.precision == 32 ? 4 : 8;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off += al256(bytes);
+        return o;
+    };
+    L.psi[0] = take(es * ntot);
+    L.psi[1] = take(es * ntot);
+    L.V = take(es * ntot);
+    L.tmp = take(es * ntot);
+    L.staging = take(cfg.precision == 32 ? 8 * ntot : 0);
+    L.ring = take(16 * (size_t)std::max(cfg.n_probe, 1) * cfg.probe_capacity);
+    L.counter = take(8);
+    L.partial = take(8 * kPartials);
+    L.dout = take(8 * 8);
+    int64_t sum_n = 0;
+    for (int a = 0; a < 3; ++a) {
+        L.tw[a] = take(a < cfg.dims ? 2 * es * cfg.n[a] : 0);
+        if (a < cfg.dims) sum_n += cfg.n[a];
+    }
+    L.mult = take(es * (size_t)(2 * m + 1) * sum_n);
+    L.spec = take(spectrum_scratch_bytes(effective_max_nfft(cfg), cfg.probe_capacity));
+    L.total = off;
+    return L;
+}
+
+}  // namespace
+
+struct spstd_ctx {
+    spstd_config cfg;
+    int m = 0;
+    double c[SPSTD_MAX_STAGES] = {0}, d[SPSTD_MAX_STAGES] = {0};
+    double s_star = 0, dt = 0, vmax = 0;
+    bool dt_auto = false;
+    int64_t ntot = 0, sum_n = 0;
+    Layout L{};
+    unsigned char *ws = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    std::vector<HalfStage> hs;
+    int64_t steps_taken = 0;
+    cudaGraphExec_t gexec = nullptr;
+    std::string err;
+
+    void *ptr(size_t off) { return ws + off; }
+};
+
+namespace {
+
+spstd_status fail(spstd_ctx *ctx, spstd_status s, const std::string &msg)
+{
+    if (ctx) ctx->err = msg;
+    return s;
+}
+spstd_status cuda_fail(spstd_ctx *ctx, cudaError_t e, const char *where)
+{
+    return fail(ctx, SPSTD_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+#define SPSTD_CU(ctx, call)                                   \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+void drop_graph(spstd_ctx *ctx)
+{
+    if (ctx->gexec) {
+        cudaGraphExecDestroy(ctx->gexec);
+        ctx->gexec = nullptr;
+    }
+}
+
+// k^2 of DFT index j on an n-point axis of period L (wrapped index, Eq. 8).
+double k2_of(int64_t j, int64_t n, double L, int nyquist_zero)
+{
+    if (nyquist_zero && j == n / 2) return 0.0;
+    const int64_t w = (j <= n / 2) ? j : j - n;
+    const double k = 2.0 * kPi * (double)w / L;
+    return k * k;
+}
+
+template <typename T>
+spstd_status upload_tables(spstd_ctx *ctx)
+{
+    const spstd_config &cfg = ctx->cfg;
+    // twiddles W_N[k] = exp(-2 pi i k/N), FP64 then rounded
+    for (int a = 0; a < cfg.dims; ++a) {
+        const int64_t n = cfg.n[a];
+        std::vector<T> tw(2 * n);
+        for (int64_t k = 0; k < n; ++k) {
+            const double ang = 2.0 * kPi * (double)k / (double)n;
+            tw[2 * k] = (T)std::cos(ang);
+            tw[2 * k + 1] = (T)(-std::sin(ang));
+        }
+        SPSTD_CU(ctx, cudaMemcpyAsync(ctx->ptr(ctx->L.tw[a]), tw.data(), sizeof(T) * 2 * n, cudaMemcpyHostToDevice,
+                                      ctx->stream));
+    }
+    // per half-stage (and H) multipliers a k_d^2(n)/N_d, FP64 then rounded
+    const int ntab = 2 * ctx->m + 1;
+    std::vector<double> a_of(ntab, 0.0);
+    for (int l = 0; l < ctx->m; ++l) {
+        a_of[2 * l] = +ctx->c[l] * ctx->dt * cfg.hbar / (2.0 * cfg.mass);
+        a_of[2 * l + 1] = -ctx->d[l] * ctx->dt * cfg.hbar / (2.0 * cfg.mass);
+    }
+    a_of[2 * ctx->m] = cfg.hbar * cfg.hbar / (2.0 * cfg.mass);
+    std::vector<T> mult((size_t)ntab * ctx->sum_n);
+    for (int t = 0; t < ntab; ++t) {
+        int64_t off = 0;
+        for (int a = 0; a < cfg.dims; ++a) {
+            const int64_t n = cfg.n[a];
+            const double L = cfg.hi[a] - cfg.lo[a];
+            for (int64_t j = 0; j < n; ++j)
+                mult[(size_t)t * ctx->sum_n + off + j] = (T)(a_of[t] * k2_of(j, n, L, cfg.nyquist_zero) / (double)n);
+            off += n;
+        }
+    }
+    SPSTD_CU(ctx, cudaMemcpyAsync(ctx->ptr(ctx->L.mult), mult.data(), sizeof(T) * mult.size(),
+                                  cudaMemcpyHostToDevice, ctx->stream));
+    // the host vectors die here: wait until the copies have read them
+    SPSTD_CU(ctx, cudaStreamSynchronize(ctx->stream));
+    return SPSTD_OK;
+}
+
+spstd_status set_dt(spstd_ctx *ctx, double vmax)
+{
+    const double wmax = w_max_of(ctx->cfg, vmax);
+    const double dt_max = ctx->s_star / wmax;
+    double dt = ctx->dt_auto ? 0.5 * dt_max : ctx->cfg.dt;
+    if (!ctx->dt_auto && dt > dt_max)
+        return fail(ctx, SPSTD_EUNSTABLE, "dt is above the stability limit s*/w_max = " + std::to_string(dt_max));
+    const bool changed = dt != ctx->dt;
+    ctx->dt = dt;
+    ctx->hs.clear();
+    for (int l = 0; l < ctx->m; ++l) {
+        const double k = ctx->cfg.hbar / (2.0 * ctx->cfg.mass);
+        if (ctx->c[l] != 0.0) ctx->hs.push_back({0, 2 * l, ctx->c[l] * dt * k, ctx->c[l] * dt / ctx->cfg.hbar});
+        if (ctx->d[l] != 0.0) ctx->hs.push_back({1, 2 * l + 1, -ctx->d[l] * dt * k, -ctx->d[l] * dt / ctx->cfg.hbar});
+    }
+    if (changed || ctx->gexec == nullptr) {
+        drop_graph(ctx);
+        spstd_status s = ctx->cfg.precision == 32 ? upload_tables<float>(ctx) : upload_tables<double>(ctx);
+        if (s != SPSTD_OK) return s;
+    }
+    return SPSTD_OK;
+}
+
+// dst += a sum_d L_d src + bV V src  (table: multiplier set, use_V: add the V term)
+// Optional per-launch timing: when set, an event pair brackets every launch.
+struct LaunchTimer {
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> kind;
+    cudaError_t begin(cudaStream_t s)
+    {
+        cudaEvent_t e;
+        cudaError_t r = cudaEventCreate(&e);
+        if (r != cudaSuccess) return r;
+        ev.push_back(e);
+        return cudaEventRecord(e, s);
+    }
+    cudaError_t end(cudaStream_t s, int k)
+    {
+        kind.push_back(k);
+        return begin(s);
+    }
+    ~LaunchTimer()
+    {
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    }
+};
+
+#define SPSTD_TIMED(timer, s, k, call)                  \
+    do {                                                \
+        if (timer) {                                    \
+            cudaError_t e0_ = (timer)->begin(s);        \
+            if (e0_ != cudaSuccess) return e0_;         \
+        }                                               \
+        cudaError_t e1_ = (call);                       \
+        if (e1_ != cudaSuccess) return e1_;             \
+        if (timer) {                                    \
+            cudaError_t e2_ = (timer)->end(s, k);       \
+            if (e2_ != cudaSuccess) return e2_;         \
+        }                                               \
+    } while (0)
+
+template <typename T>
+cudaError_t enqueue_apply(spstd_ctx *ctx, const T *src, T *dst, int table, double bV, int reverse, cudaStream_t s,
+                          LaunchTimer *timer = nullptr)
+{
+    const spstd_config &cfg = ctx->cfg;
+    const T *mult = (const T *)ctx->ptr(ctx->L.mult) + (size_t)table * ctx->sum_n;
+    const int64_t n0 = cfg.n[0], n1 = cfg.n[1], n2 = cfg.n[2];
+    PassArgs<T> x{};
+    x.src = src;
+    x.dst = dst;
+    x.V = (const T *)ctx->ptr(ctx->L.V);
+    x.tw = (const cpx<T> *)ctx->ptr(ctx->L.tw[0]);
+    x.mult = mult;
+    x.bV = (T)bV;
+    x.use_V = 1;
+    x.n_rows = n1 * n2;
+    x.reverse = reverse;
+    SPSTD_TIMED(timer, s, 0, Launch<T>::xpass((int)n0, x, s));
+    if (cfg.dims < 2) return cudaSuccess;
+    PassArgs<T> y{};
+    y.src = src;
+    y.dst = dst;
+    y.tw = (const cpx<T> *)ctx->ptr(ctx->L.tw[1]);
+    y.mult = mult + n0;
+    y.stride = n0;
+    y.outer_stride = n0 * n1;
+    y.n_outer = n2;
+    y.nx = (int)n0;
+    y.reverse = !reverse;
+    SPSTD_TIMED(timer, s, 1, Launch<T>::spass((int)n1, y, s));
+    if (cfg.dims < 3) return cudaSuccess;
+    PassArgs<T> z{};
+    z.src = src;
+    z.dst = dst;
+    z.tw = (const cpx<T> *)ctx->ptr(ctx->L.tw[2]);
+    z.mult = mult + n0 + n1;
+    z.stride = n0 * n1;
+    z.outer_stride = n0;
+    z.n_outer = n1;
+    z.nx = (int)n0;
+    z.reverse = reverse;
+    SPSTD_TIMED(timer, s, 2, Launch<T>::spass((int)n2, z, s));
+    return cudaSuccess;
+}
+
+template <typename T>
+ProbeArgs probe_args(spstd_ctx *ctx)
+{
+    ProbeArgs p{};
+    p.n_probe = ctx->cfg.n_probe;
+    for (int q = 0; q < p.n_probe; ++q) p.idx[q] = ctx->cfg.probe_idx[q];
+    p.ring = (double2 *)ctx->ptr(ctx->L.ring);
+    p.cap = ctx->cfg.probe_capacity;
+    p.counter = (int64_t *)ctx->ptr(ctx->L.counter);
+    return p;
+}
+
+// One full step of Eq. 17/18 (2D/3D): every half-stage as x, y(, z) passes,
+// then the probe recorder.
+template <typename T>
+cudaError_t enqueue_one_step(spstd_ctx *ctx, cudaStream_t s, LaunchTimer *timer = nullptr)
+{
+    T *psi[2] = {(T *)ctx->ptr(ctx->L.psi[0]), (T *)ctx->ptr(ctx->L.psi[1])};
+    int parity = 0;
+    for (const HalfStage &h : ctx->hs) {
+        cudaError_t e = enqueue_apply<T>(ctx, psi[1 - h.dst], psi[h.dst], h.table, h.bV, parity, s, timer);
+        if (e != cudaSuccess) return e;
+        parity ^= 1;
+    }
+    if (ctx->cfg.n_probe > 0) SPSTD_TIMED(timer, s, 3, Launch<T>::probe(psi[0], psi[1], probe_args<T>(ctx), s));
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t launch_resident(spstd_ctx *ctx, int64_t nsteps, LaunchTimer *timer)
+{
+    const spstd_config &cfg = ctx->cfg;
+    ResidentArgs<T> r{};
+    r.psiR = (T *)ctx->ptr(ctx->L.psi[0]);
+    r.psiI = (T *)ctx->ptr(ctx->L.psi[1]);
+    r.V = (const T *)ctx->ptr(ctx->L.V);
+    r.tw = (const cpx<T> *)ctx->ptr(ctx->L.tw[0]);
+    r.mult = (const T *)ctx->ptr(ctx->L.mult);
+    r.nh = (int)ctx->hs.size();
+    for (int h = 0; h < r.nh; ++h) {
+        r.bV[h] = (T)ctx->hs[h].bV;
+        r.hfield[h] = ctx->hs[h].dst;
+        r.htable[h] = ctx->hs[h].table;
+    }
+    r.nsteps = nsteps;
+    ProbeArgs p = probe_args<T>(ctx);
+    r.n_probe = p.n_probe;
+    for (int q = 0; q < p.n_probe; ++q) r.probe_idx[q] = p.idx[q];
+    r.ring = p.ring;
+    r.cap = p.cap;
+    r.counter = p.counter;
+    SPSTD_TIMED(timer, ctx->stream, 4, Launch<T>::resident1d((int)cfg.n[0], r, ctx->stream));
+    return cudaSuccess;
+}
+
+template <typename T>
+spstd_status step_impl(spstd_ctx *ctx, int64_t nsteps)
+{
+    const spstd_config &cfg = ctx->cfg;
+    T *psi0 = (T *)ctx->ptr(ctx->L.psi[0]);
+    T *psi1 = (T *)ctx->ptr(ctx->L.psi[1]);
+    if (cfg.dims == 1) {
+        SPSTD_CU(ctx, launch_resident<T>(ctx, nsteps, nullptr));
+        ctx->steps_taken += nsteps;
+        return SPSTD_OK;
+    }
+    cudaError_t e;
+    if (nsteps >= kGraphSteps) {
+        if (!ctx->gexec) {
+            // raise the shared-memory limits of the kernels once, outside the capture
+            PassArgs<T> none{};
+            SPSTD_CU(ctx, Launch<T>::xpass((int)cfg.n[0], none, ctx->stream));
+            none.nx = (int)cfg.n[0];
+            SPSTD_CU(ctx, Launch<T>::spass((int)cfg.n[1], none, ctx->stream));
+            if (cfg.dims == 3) SPSTD_CU(ctx, Launch<T>::spass((int)cfg.n[2], none, ctx->stream));
+            cudaGraph_t g = nullptr;
+            SPSTD_CU(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+            for (int i = 0; i < kGraphSteps; ++i) {
+                e = enqueue_one_step<T>(ctx, ctx->cap_stream);
+                if (e != cudaSuccess) {
+                    cudaStreamEndCapture(ctx->cap_stream, &g);
+                    if (g) cudaGraphDestroy(g);
+                    return cuda_fail(ctx, e, "graph capture");
+                }
+            }
+            SPSTD_CU(ctx, cudaStreamEndCapture(ctx->cap_stream, &g));
+            e = cudaGraphInstantiate(&ctx->gexec, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                ctx->gexec = nullptr;
+                return cuda_fail(ctx, e, "cudaGraphInstantiate");
+            }
+        }
+        const int64_t reps = nsteps / kGraphSteps;
+        for (int64_t i = 0; i < reps; ++i) SPSTD_CU(ctx, cudaGraphLaunch(ctx->gexec, ctx->stream));
+        nsteps -= reps * kGraphSteps;
+        ctx->steps_taken += reps * kGraphSteps;
+    }
+    for (int64_t i = 0; i < nsteps; ++i) {
+        e = enqueue_one_step<T>(ctx, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "step launch");
+        ctx->steps_taken += 1;
+    }
+    return SPSTD_OK;
+}
+
+}  // namespace
+
+// =============================================================================
+// C ABI
+// =============================================================================
+extern "C" {
+
+void spstd_config_init(spstd_config *cfg)
+{
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->dims = 1;
+    cfg->n[0] = 256;
+    cfg->n[1] = cfg->n[2] = 1;
+    for (int a = 0; a < 3; ++a) {
+        cfg->lo[a] = 0.0;
+        cfg->hi[a] = 1.0;
+    }
+    cfg->hbar = 1.0;
+    cfg->mass = 1.0;
+    cfg->precision = 64;
+    cfg->preset = SPSTD_FR4;
+    cfg->dt = 0.0;
+    cfg->probe_capacity = 1024;
+}
+
+const char *spstd_status_string(spstd_status s)
+{
+    switch (s) {
+    case SPSTD_OK: return "ok";
+    case SPSTD_EINVAL: return "invalid argument";
+    case SPSTD_ENOMEM: return "out of memory / workspace too small";
+    case SPSTD_ECUDA: return "CUDA error";
+    case SPSTD_EUNSTABLE: return "time step above the stability limit";
+    case SPSTD_EDIVERGED: return "solution diverged (NaN/Inf)";
+    case SPSTD_ETIMEOUT: return "device wait timed out";
+    case SPSTD_ENOTREADY: return "no data yet";
+    case SPSTD_EUNSUPPORTED: return "unsupported by this build";
+    }
+    return "unknown status";
+}
+
+const char *spstd_last_error(const spstd_ctx *ctx)
+{
+    if (!ctx) return "no context";
+    return ctx->err.c_str();
+}
+
+spstd_status spstd_workspace_size(const spstd_config *cfg, size_t *bytes)
+{
+    if (!bytes) return SPSTD_EINVAL;
+    int m;
+    double c[SPSTD_MAX_STAGES], d[SPSTD_MAX_STAGES];
+    spstd_status s = validate(cfg, nullptr, &m, c, d);
+    if (s != SPSTD_OK) return s;
+    if (cfg->dt > 0) {
+        const double ss = stability_s_star(m, c, d);
+        if (cfg->dt > ss / w_max_of(*cfg, 0.0)) return SPSTD_EUNSTABLE;
+    }
+    *bytes = make_layout(*cfg, m).total;
+    return SPSTD_OK;
+}
+
+spstd_status spstd_stability_limit(const spstd_config *cfg, double vmax, double *s_star, double *dt_max)
+{
+    int m;
+    double c[SPSTD_MAX_STAGES], d[SPSTD_MAX_STAGES];
+    spstd_status s = validate(cfg, nullptr, &m, c, d);
+    if (s != SPSTD_OK) return s;
+    const double ss = stability_s_star(m, c, d);
+    if (s_star) *s_star = ss;
+    if (dt_max) *dt_max = ss / w_max_of(*cfg, vmax);
+    return SPSTD_OK;
+}
+
+spstd_status spstd_create(const spstd_config *cfg, void *d_workspace, size_t workspace_bytes, spstd_ctx **out)
+{
+    if (!out) return SPSTD_EINVAL;
+    *out = nullptr;
+    spstd_ctx *ctx = new (std::nothrow) spstd_ctx();
+    if (!ctx) return SPSTD_ENOMEM;
+    std::string why;
+    spstd_status st = validate(cfg, &why, &ctx->m, ctx->c, ctx->d);
+    if (st != SPSTD_OK) {
+        delete ctx;
+        return st;
+    }
+    ctx->cfg = *cfg;
+    ctx->L = make_layout(*cfg, ctx->m);
+    if (!d_workspace || ((uintptr_t)d_workspace & 255)) {
+        delete ctx;
+        return SPSTD_EINVAL;
+    }
+    if (workspace_bytes < ctx->L.total) {
+        delete ctx;
+        return SPSTD_ENOMEM;
+    }
+    ctx->ws = (unsigned char *)d_workspace;
+    ctx->ntot = cfg->n[0] * cfg->n[1] * cfg->n[2];
+    for (int a = 0; a < cfg->dims; ++a) ctx->sum_n += cfg->n[a];
+    ctx->stream = (cudaStream_t)cfg->stream;
+    ctx->s_star = stability_s_star(ctx->m, ctx->c, ctx->d);
+    ctx->dt_auto = !(cfg->dt > 0);
+    ctx->dt = -1.0;  // forces the first table upload
+    auto bail = [&](spstd_status s) {
+        if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+        delete ctx;
+        return s;
+    };
+    if (cudaSetDevice(cfg->device) != cudaSuccess) return bail(SPSTD_ECUDA);
+    if (cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess) return bail(SPSTD_ECUDA);
+    if (cudaMemsetAsync(ctx->ws, 0, ctx->L.total, ctx->stream) != cudaSuccess) return bail(SPSTD_ECUDA);
+    st = set_dt(ctx, 0.0);
+    if (st != SPSTD_OK) return bail(st);
+    *out = ctx;
+    return SPSTD_OK;
+}
+
+spstd_status spstd_destroy(spstd_ctx *ctx)
+{
+    if (!ctx) return SPSTD_OK;
+    cudaStreamSynchronize(ctx->stream);
+    drop_graph(ctx);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    delete ctx;
+    return SPSTD_OK;
+}
+
+}  // extern "C"
+
+namespace {
+template <typename T>
+spstd_status upload_field(spstd_ctx *ctx, const double *host, size_t off)
+{
+    if (sizeof(T) == 8) {
+        SPSTD_CU(ctx, cudaMemcpyAsync(ctx->ptr(off), host, 8 * ctx->ntot, cudaMemcpyHostToDevice, ctx->stream));
+    } else {
+        double *st = (double *)ctx->ptr(ctx->L.staging);
+        SPSTD_CU(ctx, cudaMemcpyAsync(st, host, 8 * ctx->ntot, cudaMemcpyHostToDevice, ctx->stream));
+        SPSTD_CU(ctx, Launch<T>::from_f64(st, (T *)ctx->ptr(off), ctx->ntot, ctx->stream));
+    }
+    return SPSTD_OK;
+}
+template <typename T>
+spstd_status download_field(spstd_ctx *ctx, const void *dev, double *host)
+{
+    if (sizeof(T) == 8) {
+        SPSTD_CU(ctx, cudaMemcpyAsync(host, dev, 8 * ctx->ntot, cudaMemcpyDeviceToHost, ctx->stream));
+    } else {
+        double *st = (double *)ctx->ptr(ctx->L.staging);
+        SPSTD_CU(ctx, Launch<T>::to_f64((const T *)dev, st, ctx->ntot, ctx->stream));
+        SPSTD_CU(ctx, cudaMemcpyAsync(host, st, 8 * ctx->ntot, cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    SPSTD_CU(ctx, cudaStreamSynchronize(ctx->stream));
+    return SPSTD_OK;
+}
+}  // namespace
+
+extern "C" {
+
+spstd_status spstd_set_potential(spstd_ctx *ctx, const double *V)
+{
+    if (!ctx || !V) return SPSTD_EINVAL;
+    double vmax = -INFINITY;
+    for (int64_t i = 0; i < ctx->ntot; ++i) {
+        if (!std::isfinite(V[i])) return fail(ctx, SPSTD_EINVAL, "V has a non-finite value");
+        vmax = std::max(vmax, V[i]);
+    }
+    spstd_status s = ctx->cfg.precision == 32 ? upload_field<float>(ctx, V, ctx->L.V)
+                                              : upload_field<double>(ctx, V, ctx->L.V);
+    if (s != SPSTD_OK) return s;
+    ctx->vmax = vmax;
+    return set_dt(ctx, vmax);
+}
+
+spstd_status spstd_set_state(spstd_ctx *ctx, const double *psiR, const double *psiI)
+{
+    if (!ctx || !psiR || !psiI) return SPSTD_EINVAL;
+    spstd_status s = ctx->cfg.precision == 32 ? upload_field<float>(ctx, psiR, ctx->L.psi[0])
+                                              : upload_field<double>(ctx, psiR, ctx->L.psi[0]);
+    if (s != SPSTD_OK) return s;
+    s = ctx->cfg.precision == 32 ? upload_field<float>(ctx, psiI, ctx->L.psi[1])
+                                 : upload_field<double>(ctx, psiI, ctx->L.psi[1]);
+    if (s != SPSTD_OK) return s;
+    SPSTD_CU(ctx, cudaMemsetAsync(ctx->ptr(ctx->L.counter), 0, 8, ctx->stream));
+    ctx->steps_taken = 0;
+    return SPSTD_OK;
+}
+
+spstd_status spstd_get_state(spstd_ctx *ctx, double *psiR, double *psiI)
+{
+    if (!ctx || !psiR || !psiI) return SPSTD_EINVAL;
+    spstd_status s = ctx->cfg.precision == 32 ? download_field<float>(ctx, ctx->ptr(ctx->L.psi[0]), psiR)
+                                              : download_field<double>(ctx, ctx->ptr(ctx->L.psi[0]), psiR);
+    if (s != SPSTD_OK) return s;
+    return ctx->cfg.precision == 32 ? download_field<float>(ctx, ctx->ptr(ctx->L.psi[1]), psiI)
+                                    : download_field<double>(ctx, ctx->ptr(ctx->L.psi[1]), psiI);
+}
+
+spstd_status spstd_step(spstd_ctx *ctx, int64_t nsteps)
+{
+    if (!ctx || nsteps < 0) return SPSTD_EINVAL;
+    if (nsteps == 0) return SPSTD_OK;
+    return ctx->cfg.precision == 32 ? step_impl<float>(ctx, nsteps) : step_impl<double>(ctx, nsteps);
+}
+
+spstd_status spstd_probe(spstd_ctx *ctx, int p, double *re, double *im, int64_t cap, int64_t *len)
+{
+    if (!ctx || !re || !im || !len || cap < 0 || p < 0 || p >= ctx->cfg.n_probe) return SPSTD_EINVAL;
+    *len = 0;
+    if (ctx->steps_taken == 0) return fail(ctx, SPSTD_ENOTREADY, "no step recorded since set_state");
+    const int64_t C = ctx->cfg.probe_capacity;
+    const int64_t kept = std::min(ctx->steps_taken, C);
+    std::vector<double2> row(C);
+    SPSTD_CU(ctx, cudaMemcpyAsync(row.data(), (double2 *)ctx->ptr(ctx->L.ring) + (size_t)p * C, sizeof(double2) * C,
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+    SPSTD_CU(ctx, cudaStreamSynchronize(ctx->stream));
+    const int64_t nout = std::min(kept, cap);
+    const int64_t first = ctx->steps_taken - nout;  // global index of the first sample returned
+    for (int64_t i = 0; i < nout; ++i) {
+        const double2 v = row[(first + i) % C];
+        re[i] = v.x;
+        im[i] = v.y;
+    }
+    *len = nout;
+    return SPSTD_OK;
+}
+
+spstd_status spstd_spectrum(spstd_ctx *ctx, int p, int64_t nfft, int max_peaks, double thresh, int phase_correct,
+                            double *E, double *amp, int *npeaks)
+{
+    if (!ctx || !E || !amp || !npeaks) return SPSTD_EINVAL;
+    *npeaks = 0;
+    if (p < -1 || p >= ctx->cfg.n_probe || ctx->cfg.n_probe == 0) return fail(ctx, SPSTD_EINVAL, "bad probe");
+    if (max_peaks < 1 || max_peaks > kMaxSpectrumPeaks) return fail(ctx, SPSTD_EINVAL, "max_peaks must be 1..64");
+    if (!(thresh >= 0.0)) return fail(ctx, SPSTD_EINVAL, "thresh must be >= 0");
+    const int64_t C = ctx->cfg.probe_capacity;
+    const int64_t M = std::min(ctx->steps_taken, C);
+    if (M < 2) return fail(ctx, SPSTD_ENOTREADY, "need at least 2 recorded steps");
+    const int64_t maxn = effective_max_nfft(ctx->cfg);
+    if (nfft <= 0) nfft = std::min(maxn, next_pow2(4 * M));
+    if (!is_pow2(nfft) || nfft < M || nfft > maxn || nfft < 4)
+        return fail(ctx, SPSTD_EINVAL, "nfft must be a power of two with M <= nfft <= max_nfft");
+    SpectrumArgs a{};
+    a.ring = (const double2 *)ctx->ptr(ctx->L.ring);
+    a.n_probe = ctx->cfg.n_probe;
+    a.p = p;
+    a.cap = C;
+    a.first_slot = (ctx->steps_taken - M) % C;
+    a.M = M;
+    a.nfft = nfft;
+    a.max_nfft = maxn;
+    a.max_peaks = max_peaks;
+    a.thresh = thresh;
+    a.scratch = ctx->ptr(ctx->L.spec);
+    int np = 0;
+    std::vector<double> th(max_peaks), am(max_peaks);
+    a.h_npeaks = &np;
+    a.h_theta = th.data();
+    a.h_amp = am.data();
+    SPSTD_CU(ctx, launch_spectrum(a, ctx->stream));
+    std::vector<std::pair<double, double>> res;
+    for (int i = 0; i < np; ++i) {
+        double e = ctx->cfg.hbar * th[i] / ctx->dt;
+        if (phase_correct) e = ctx->cfg.hbar * dispersion_inverse(ctx->m, ctx->c, ctx->d, ctx->s_star, th[i]) / ctx->dt;
+        res.push_back({e, am[i]});
+    }
+    std::stable_sort(res.begin(), res.end(), [](const auto &x, const auto &y) { return x.first < y.first; });
+    for (int i = 0; i < np; ++i) {
+        E[i] = res[i].first;
+        amp[i] = res[i].second;
+    }
+    *npeaks = np;
+    return SPSTD_OK;
+}
+
+}  // extern "C"
+
+namespace {
+template <typename T>
+spstd_status energy_norm_impl(spstd_ctx *ctx, double *norm, double *energy)
+{
+    cudaStream_t s = ctx->stream;
+    T *pr = (T *)ctx->ptr(ctx->L.psi[0]);
+    T *pi = (T *)ctx->ptr(ctx->L.psi[1]);
+    T *tmp = (T *)ctx->ptr(ctx->L.tmp);
+    double *part = (double *)ctx->ptr(ctx->L.partial);
+    double *dout = (double *)ctx->ptr(ctx->L.dout);
+    const int nb = (int)std::min<int64_t>(kPartials, (ctx->ntot + 255) / 256);
+    const int tH = 2 * ctx->m;
+    // sum psi_R^2 + psi_I^2
+    SPSTD_CU(ctx, Launch<T>::dot2(pr, pr, pi, pi, ctx->ntot, part, nb, s));
+    SPSTD_CU(ctx, launch_sum_partials(part, nb, dout + 0, s));
+    // sum psi_R H psi_R
+    SPSTD_CU(ctx, cudaMemsetAsync(tmp, 0, sizeof(T) * ctx->ntot, s));
+    SPSTD_CU(ctx, enqueue_apply<T>(ctx, pr, tmp, tH, 1.0, 0, s));
+    SPSTD_CU(ctx, Launch<T>::dot2(pr, tmp, nullptr, nullptr, ctx->ntot, part, nb, s));
+    SPSTD_CU(ctx, launch_sum_partials(part, nb, dout + 1, s));
+    // sum psi_I H psi_I
+    SPSTD_CU(ctx, cudaMemsetAsync(tmp, 0, sizeof(T) * ctx->ntot, s));
+    SPSTD_CU(ctx, enqueue_apply<T>(ctx, pi, tmp, tH, 1.0, 0, s));
+    SPSTD_CU(ctx, Launch<T>::dot2(pi, tmp, nullptr, nullptr, ctx->ntot, part, nb, s));
+    SPSTD_CU(ctx, launch_sum_partials(part, nb, dout + 2, s));
+    double h[3];
+    SPSTD_CU(ctx, cudaMemcpyAsync(h, dout, sizeof(h), cudaMemcpyDeviceToHost, s));
+    SPSTD_CU(ctx, cudaStreamSynchronize(s));
+    double dV = 1.0;
+    for (int a = 0; a < ctx->cfg.dims; ++a) dV *= (ctx->cfg.hi[a] - ctx->cfg.lo[a]) / (double)ctx->cfg.n[a];
+    *norm = dV * h[0];
+    *energy = dV * (h[1] + h[2]);
+    if (!std::isfinite(*norm) || !std::isfinite(*energy)) return fail(ctx, SPSTD_EDIVERGED, "norm or energy is not finite");
+    return SPSTD_OK;
+}
+
+template <typename T>
+spstd_status apply_h_impl(spstd_ctx *ctx, int which, double *out)
+{
+    T *src = (T *)ctx->ptr(ctx->L.psi[which]);
+    T *tmp = (T *)ctx->ptr(ctx->L.tmp);
+    SPSTD_CU(ctx, cudaMemsetAsync(tmp, 0, sizeof(T) * ctx->ntot, ctx->stream));
+    SPSTD_CU(ctx, enqueue_apply<T>(ctx, src, tmp, 2 * ctx->m, 1.0, 0, ctx->stream));
+    return download_field<T>(ctx, tmp, out);
+}
+}  // namespace
+
+extern "C" {
+
+spstd_status spstd_energy_norm(spstd_ctx *ctx, double *norm, double *energy)
+{
+    if (!ctx || !norm || !energy) return SPSTD_EINVAL;
+    return ctx->cfg.precision == 32 ? energy_norm_impl<float>(ctx, norm, energy)
+                                    : energy_norm_impl<double>(ctx, norm, energy);
+}
+
+spstd_status spstd_apply_hamiltonian(spstd_ctx *ctx, int which, double *out)
+{
+    if (!ctx || !out || (which != 0 && which != 1)) return SPSTD_EINVAL;
+    return ctx->cfg.precision == 32 ? apply_h_impl<float>(ctx, which, out) : apply_h_impl<double>(ctx, which, out);
+}
+
+}  // extern "C"
+
+namespace {
+template <typename T>
+spstd_status profile_impl(spstd_ctx *ctx, int64_t nsteps, double *ms, int64_t *cnt)
+{
+    LaunchTimer timer;
+    if (ctx->cfg.dims == 1) {
+        SPSTD_CU(ctx, launch_resident<T>(ctx, nsteps, &timer));
+    } else {
+        for (int64_t i = 0; i < nsteps; ++i) SPSTD_CU(ctx, enqueue_one_step<T>(ctx, ctx->stream, &timer));
+    }
+    ctx->steps_taken += nsteps;
+    SPSTD_CU(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int k = 0; k < SPSTD_KERNEL_KINDS; ++k) {
+        ms[k] = 0.0;
+        cnt[k] = 0;
+    }
+    for (size_t i = 0; i < timer.kind.size(); ++i) {
+        float t = 0.f;
+        SPSTD_CU(ctx, cudaEventElapsedTime(&t, timer.ev[2 * i], timer.ev[2 * i + 1]));
+        ms[timer.kind[i]] += t;
+        cnt[timer.kind[i]] += 1;
+    }
+    return SPSTD_OK;
+}
+}  // namespace
+
+extern "C" {
+
+spstd_status spstd_profile_steps(spstd_ctx *ctx, int64_t nsteps, double *ms, int64_t *cnt)
+{
+    if (!ctx || !ms || !cnt || nsteps < 0) return SPSTD_EINVAL;
+    return ctx->cfg.precision == 32 ? profile_impl<float>(ctx, nsteps, ms, cnt)
+                                    : profile_impl<double>(ctx, nsteps, ms, cnt);
+}
+
+spstd_status spstd_get_dt(const spstd_ctx *ctx, double *dt)
+{
+    if (!ctx || !dt) return SPSTD_EINVAL;
+    *dt = ctx->dt;
+    return SPSTD_OK;
+}
+
+spstd_status spstd_steps_taken(const spstd_ctx *ctx, int64_t *steps)
+{
+    if (!ctx || !steps) return SPSTD_EINVAL;
+    *steps = ctx->steps_taken;
+    return SPSTD_OK;
+}
+
+spstd_status spstd_get_coefficients(const spstd_ctx *ctx, int *m, double *c, double *d)
+{
+    if (!ctx || !m || !c || !d) return SPSTD_EINVAL;
+    *m = ctx->m;
+    for (int l = 0; l < ctx->m; ++l) {
+        c[l] = ctx->c[l];
+        d[l] = ctx->d[l];
+    }
+    return SPSTD_OK;
+}
+
+spstd_status spstd_launch_count(const spstd_ctx *ctx, int64_t nsteps, int64_t *launches)
+{
+    if (!ctx || !launches || nsteps < 0) return SPSTD_EINVAL;
+    if (nsteps == 0) {
+        *launches = 0;
+    } else if (ctx->cfg.dims == 1) {
+        *launches = 1;
+    } else {
+        *launches = nsteps * ((int64_t)ctx->hs.size() * ctx->cfg.dims + (ctx->cfg.n_probe > 0 ? 1 : 0));
+    }
+    return SPSTD_OK;
+}
+
+}  // extern "C"

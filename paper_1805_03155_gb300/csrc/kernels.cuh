@@ -1,0 +1,451 @@
+// kernels.cuh -- the device kernels of one SPSTD half-stage (Eq. 16-18) and
+// their helpers.  Each half-stage is
+//     dst += a * sum_d L_d src + bV * V * src,
+// with L_d = F_d^-1 k_d^2 F_d the spectral -d^2/dx_d^2 along axis d (Eq. 10),
+// a = s coef dt hbar/2m* and bV = s coef dt/hbar (s = +1 for psi_R <- psi_I,
+// s = -1 for psi_I <- psi_R).  The factor a k^2/N of the inverse transform is
+// pre-multiplied into one table per half-stage and axis (FP64 on the host,
+// rounded once).
+//
+// Two real lines travel as the real and imaginary parts of one complex line:
+// k^2 is real and even, so F^-1 k^2 F maps a real line to a real line and the
+// two never mix.
+#pragma once
+
+#include "fft_line.cuh"
+
+namespace spstd {
+
+template <typename T>
+struct PassArgs {
+    const T *src;
+    T *dst;
+    const T *V;             // used when use_V != 0
+    const cpx<T> *tw;       // W_N[k], k < N
+    const T *mult;          // a k^2(n)/N, n < N
+    T bV;
+    int use_V;
+    int64_t n_rows;         // x pass: number of contiguous lines of N points
+    int64_t stride;         // strided pass: elements between points along the axis
+    int64_t outer_stride;   // strided pass: elements between consecutive line groups
+    int64_t n_outer;        // strided pass: number of line groups
+    int nx;                 // strided pass: columns (points along x)
+    int reverse;            // walk the tiles in reverse order (L2 reuse)
+};
+
+constexpr int kMaxHalfStages = 16;
+constexpr int kMaxProbes = 16;
+
+template <typename T>
+struct ResidentArgs {
+    T *psiR;
+    T *psiI;
+    const T *V;
+    const cpx<T> *tw;
+    const T *mult;                // multiplier rows of N values
+    T bV[kMaxHalfStages];
+    int hfield[kMaxHalfStages];   // 0: psi_R += .. K psi_I ; 1: psi_I += .. K psi_R
+    int htable[kMaxHalfStages];   // multiplier row of each executed half-stage
+    int nh;
+    int64_t nsteps;
+    int n_probe;
+    int64_t probe_idx[kMaxProbes];
+    double2 *ring;
+    int64_t cap;
+    int64_t *counter;
+};
+
+struct ProbeArgs {
+    int n_probe;
+    int64_t idx[kMaxProbes];
+    double2 *ring;
+    int64_t cap;
+    int64_t *counter;
+};
+
+// ---------------------------------------------------------------------------
+// Exchange buffers.
+// ---------------------------------------------------------------------------
+
+// One contiguous line per thread group, index fastest, one pad slot per 32.
+template <typename T, bool BLOCKSYNC>
+struct XcRow {
+    cpx<T> *base;
+    int bufstride;
+    int cur;
+    unsigned mask;  // lanes of this warp that exist (blocks narrower than a warp)
+    __device__ __forceinline__ cpx<T> &at(int idx) { return base[cur * bufstride + idx + (idx >> 5)]; }
+    __device__ __forceinline__ void st(int idx, cpx<T> v) { at(idx) = v; }
+    __device__ __forceinline__ cpx<T> ld(int idx) { return at(idx); }
+    __device__ __forceinline__ void sync()
+    {
+        if constexpr (BLOCKSYNC) __syncthreads();
+        else __syncwarp(mask);
+    }
+    __device__ __forceinline__ void flip() { cur ^= 1; }
+};
+
+// LPC column lines side by side, line fastest (conflict-free for a warp that
+// spans consecutive lines).
+template <typename T, int LPC>
+struct XcCol {
+    cpx<T> *base;
+    int bufstride;
+    int cur;
+    __device__ __forceinline__ cpx<T> &at(int idx) { return base[cur * bufstride + idx * LPC]; }
+    __device__ __forceinline__ void st(int idx, cpx<T> v) { at(idx) = v; }
+    __device__ __forceinline__ cpx<T> ld(int idx) { return at(idx); }
+    __device__ __forceinline__ void sync() { __syncthreads(); }
+    __device__ __forceinline__ void flip() { cur ^= 1; }
+};
+
+__host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+
+// Mask of the lanes of a warp that exist when a block has nthreads threads.
+__device__ __forceinline__ unsigned lane_mask(int nthreads)
+{
+    return nthreads >= 32 ? 0xffffffffu : ((1u << nthreads) - 1u);
+}
+
+// Lines up to this length stage their twiddle and multiplier tables in shared
+// memory; longer lines read them through L1 (their exchange buffers need the room).
+constexpr int kMaxStagedN = 1024;
+
+template <typename T, int N>
+__host__ __device__ constexpr size_t table_bytes()
+{
+    return N <= kMaxStagedN ? align16(sizeof(cpx<T>) * N) + align16(sizeof(T) * N) : 0;
+}
+
+template <typename T, int N, int LPC>
+__host__ __device__ constexpr size_t xpass_smem()
+{
+    return table_bytes<T, N>() + 2 * (size_t)LPC * (N + N / 32) * sizeof(cpx<T>);
+}
+template <typename T, int N, int LPC>
+__host__ __device__ constexpr size_t spass_smem()
+{
+    return table_bytes<T, N>() + 2 * (size_t)LPC * N * sizeof(cpx<T>);
+}
+template <typename T, int N>
+__host__ __device__ constexpr size_t resident_smem()
+{
+    return align16(sizeof(cpx<T>) * N) + 2 * (size_t)(N + N / 32) * sizeof(cpx<T>);
+}
+
+template <typename T, int N>
+__device__ __forceinline__ void stage_tables(const PassArgs<T> &a, cpx<T> *s_tw, T *s_mult, int tid,
+                                             int nthreads)
+{
+    for (int i = tid; i < N; i += nthreads) {
+        s_tw[i] = a.tw[i];
+        s_mult[i] = a.mult[i];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// x pass: contiguous lines.  Block (TT, LPC); line pair lp covers rows 2lp and
+// 2lp+1 (the second may be past the end: its half of the complex line is 0).
+// ---------------------------------------------------------------------------
+template <typename T, int N, int LPC>
+__global__ void __launch_bounds__((N / line_e<T, N>::value) * LPC)
+xpass_kernel(const PassArgs<T> a)
+{
+    constexpr int E = line_e<T, N>::value;
+    constexpr int TT = N / E;
+    constexpr int LS = N + N / 32;
+    extern __shared__ __align__(16) unsigned char smem[];
+    cpx<T> *s_tw = reinterpret_cast<cpx<T> *>(smem);
+    T *s_mult = reinterpret_cast<T *>(smem + align16(sizeof(cpx<T>) * N));
+    cpx<T> *s_ex = reinterpret_cast<cpx<T> *>(smem + table_bytes<T, N>());
+
+    const int t = threadIdx.x;
+    const int l = threadIdx.y;
+    const cpx<T> *tw = a.tw;
+    const T *mult = a.mult;
+    if constexpr (N <= kMaxStagedN) {
+        stage_tables<T, N>(a, s_tw, s_mult, l * TT + t, TT * LPC);
+        __syncthreads();
+        tw = s_tw;
+        mult = s_mult;
+    }
+
+    const int64_t blk = a.reverse ? (int64_t)(gridDim.x - 1 - blockIdx.x) : (int64_t)blockIdx.x;
+    const int64_t lp = blk * LPC + l;
+    const int64_t r0 = 2 * lp, r1 = r0 + 1;
+    const bool ok0 = r0 < a.n_rows, ok1 = r1 < a.n_rows;
+    const T *s0 = a.src + r0 * N;
+    const T *s1 = a.src + r1 * N;
+
+    cpx<T> v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int i = t + e * TT;
+        v[e] = mk<T>(ok0 ? s0[i] : T(0), ok1 ? s1[i] : T(0));
+    }
+    XcRow<T, (TT > 32)> xc{s_ex + l * LS, LPC * LS, 0, lane_mask(TT * LPC)};
+    fft_line<T, N, E, false>(v, t, xc, tw);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const T m = mult[t + e * TT];
+        v[e].x *= m;
+        v[e].y *= m;
+    }
+    fft_line<T, N, E, true>(v, t, xc, tw);
+
+    T *d0 = a.dst + r0 * N;
+    T *d1 = a.dst + r1 * N;
+    const T *V0 = a.use_V ? a.V + r0 * N : nullptr;
+    const T *V1 = a.use_V ? a.V + r1 * N : nullptr;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int i = t + e * TT;
+        if (ok0) {
+            T acc = d0[i] + v[e].x;
+            if (a.use_V) acc = fma(a.bV * V0[i], s0[i], acc);
+            d0[i] = acc;
+        }
+        if (ok1) {
+            T acc = d1[i] + v[e].y;
+            if (a.use_V) acc = fma(a.bV * V1[i], s1[i], acc);
+            d1[i] = acc;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Strided pass (y or z axis).  Block (LPC, TT): threadIdx.x picks the column
+// pair (2p, 2p+1) inside a tile of 2 LPC adjacent x columns, threadIdx.y the
+// thread within the line, so each warp reads 2 LPC consecutive values of a
+// row per access.  Tile id = outer * n_xt + xt.
+// ---------------------------------------------------------------------------
+template <typename T, int N, int LPC>
+__global__ void __launch_bounds__((N / line_e<T, N>::value) * LPC)
+spass_kernel(const PassArgs<T> a)
+{
+    constexpr int E = line_e<T, N>::value;
+    constexpr int TT = N / E;
+    extern __shared__ __align__(16) unsigned char smem[];
+    cpx<T> *s_tw = reinterpret_cast<cpx<T> *>(smem);
+    T *s_mult = reinterpret_cast<T *>(smem + align16(sizeof(cpx<T>) * N));
+    cpx<T> *s_ex = reinterpret_cast<cpx<T> *>(smem + table_bytes<T, N>());
+
+    const int p = threadIdx.x;
+    const int t = threadIdx.y;
+    stage_tables<T, N>(a, s_tw, s_mult, t * LPC + p, TT * LPC);
+    __syncthreads();
+
+    const int n_xt = (a.nx + 2 * LPC - 1) / (2 * LPC);
+    const int64_t blk = a.reverse ? (int64_t)(gridDim.x - 1 - blockIdx.x) : (int64_t)blockIdx.x;
+    const int64_t outer = blk / n_xt;
+    const int xt = (int)(blk - outer * n_xt);
+    const int c0 = xt * 2 * LPC + 2 * p;
+    const bool ok0 = c0 < a.nx, ok1 = c0 + 1 < a.nx;
+    const bool vec = ok1 && !(a.nx & 1);
+    const int64_t base = outer * a.outer_stride + c0;
+
+    cpx<T> v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int64_t off = base + (int64_t)(t + e * TT) * a.stride;
+        if (vec) {
+            v[e] = *reinterpret_cast<const cpx<T> *>(a.src + off);
+        } else {
+            v[e] = mk<T>(ok0 ? a.src[off] : T(0), ok1 ? a.src[off + 1] : T(0));
+        }
+    }
+    XcCol<T, LPC> xc{s_ex + p, LPC * N, 0};
+    fft_line<T, N, E, false>(v, t, xc, s_tw);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const T m = s_mult[t + e * TT];
+        v[e].x *= m;
+        v[e].y *= m;
+    }
+    fft_line<T, N, E, true>(v, t, xc, s_tw);
+
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int64_t off = base + (int64_t)(t + e * TT) * a.stride;
+        if (vec) {
+            cpx<T> d = *reinterpret_cast<const cpx<T> *>(a.dst + off);
+            d.x += v[e].x;
+            d.y += v[e].y;
+            if (a.use_V) {
+                const cpx<T> s = *reinterpret_cast<const cpx<T> *>(a.src + off);
+                const cpx<T> w = *reinterpret_cast<const cpx<T> *>(a.V + off);
+                d.x = fma(a.bV * w.x, s.x, d.x);
+                d.y = fma(a.bV * w.y, s.y, d.y);
+            }
+            *reinterpret_cast<cpx<T> *>(a.dst + off) = d;
+        } else {
+            if (ok0) {
+                T acc = a.dst[off] + v[e].x;
+                if (a.use_V) acc = fma(a.bV * a.V[off], a.src[off], acc);
+                a.dst[off] = acc;
+            }
+            if (ok1) {
+                T acc = a.dst[off + 1] + v[e].y;
+                if (a.use_V) acc = fma(a.bV * a.V[off + 1], a.src[off + 1], acc);
+                a.dst[off + 1] = acc;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Resident 1D solver: one block owns a whole 1D grid for all nsteps steps.
+// Thread t keeps psi_R, psi_I and V at points t + e TT in registers (the same
+// natural layout the line FFT uses), so a half-stage touches global memory
+// only for its multiplier table; the probes are written after every step.
+// ---------------------------------------------------------------------------
+template <typename T, int N>
+__global__ void __launch_bounds__(N / line_e<T, N>::value)
+resident1d_kernel(const ResidentArgs<T> a)
+{
+    constexpr int E = line_e<T, N>::value;
+    constexpr int TT = N / E;
+    constexpr int LS = N + N / 32;
+    extern __shared__ __align__(16) unsigned char smem[];
+    cpx<T> *s_tw = reinterpret_cast<cpx<T> *>(smem);
+    cpx<T> *s_ex = reinterpret_cast<cpx<T> *>(smem + align16(sizeof(cpx<T>) * N));
+
+    const int t = threadIdx.x;
+    for (int i = t; i < N; i += TT) s_tw[i] = a.tw[i];
+
+    T R[E], I[E], W[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int i = t + e * TT;
+        R[e] = a.psiR[i];
+        I[e] = a.psiI[i];
+        W[e] = a.V[i];
+    }
+    const int64_t c0 = *a.counter;
+    __syncthreads();
+
+    XcRow<T, (TT > 32)> xc{s_ex, LS, 0, lane_mask(TT)};
+    for (int64_t step = 0; step < a.nsteps; ++step) {
+        for (int h = 0; h < a.nh; ++h) {
+            const bool toR = a.hfield[h] == 0;
+            const T *mult = a.mult + (int64_t)a.htable[h] * N;
+            cpx<T> v[E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) v[e] = mk<T>(toR ? I[e] : R[e], T(0));
+            fft_line<T, N, E, false>(v, t, xc, s_tw);
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const T m = __ldg(mult + t + e * TT);
+                v[e].x *= m;
+                v[e].y *= m;
+            }
+            fft_line<T, N, E, true>(v, t, xc, s_tw);
+            const T bV = a.bV[h];
+            if (toR) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) R[e] = fma(bV * W[e], I[e], R[e] + v[e].x);
+            } else {
+#pragma unroll
+                for (int e = 0; e < E; ++e) I[e] = fma(bV * W[e], R[e], I[e] + v[e].x);
+            }
+        }
+        const int64_t slot = (c0 + step) % a.cap;
+        for (int q = 0; q < a.n_probe; ++q) {
+            const int64_t idx = a.probe_idx[q];
+            if ((int)(idx % TT) == t) {
+                const int eo = (int)(idx / TT);
+                T pr = T(0), pi = T(0);
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    if (e == eo) {
+                        pr = R[e];
+                        pi = I[e];
+                    }
+                }
+                a.ring[(int64_t)q * a.cap + slot] = make_double2((double)pr, (double)pi);
+            }
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int i = t + e * TT;
+        a.psiR[i] = R[e];
+        a.psiI[i] = I[e];
+    }
+    __syncthreads();
+    if (t == 0) *a.counter = c0 + a.nsteps;
+}
+
+// ---------------------------------------------------------------------------
+// Probe recorder (one block): ring[q][counter % cap] = (psi_R, psi_I)(idx_q).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void probe_kernel(const T *__restrict__ psiR, const T *__restrict__ psiI, const ProbeArgs a)
+{
+    const int64_t c = *a.counter;
+    const int q = threadIdx.x;
+    if (q < a.n_probe) {
+        const int64_t idx = a.idx[q];
+        a.ring[(int64_t)q * a.cap + c % a.cap] = make_double2((double)psiR[idx], (double)psiI[idx]);
+    }
+    __syncthreads();
+    if (q == 0) *a.counter = c + 1;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 reductions in a fixed order: partial[b] = sum over block b's grid-stride
+// elements of x1 y1 (+ x2 y2), then one block sums the partials.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double block_sum(double v, double *s_w)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    v = warp_sum(v);
+    if (lane == 0) s_w[w] = v;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    v = (threadIdx.x < nw) ? s_w[threadIdx.x] : 0.0;
+    if (w == 0) v = warp_sum(v);
+    __syncthreads();
+    return v;  // valid in thread 0
+}
+
+template <typename T>
+__global__ void dot2_kernel(const T *__restrict__ x1, const T *__restrict__ y1, const T *__restrict__ x2,
+                            const T *__restrict__ y2, int64_t n, double *__restrict__ partial)
+{
+    __shared__ double s_w[32];
+    double acc = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        double v = (double)x1[i] * (double)y1[i];
+        if (x2) v = fma((double)x2[i], (double)y2[i], v);
+        acc += v;
+    }
+    acc = block_sum(acc, s_w);
+    if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+// ---------------------------------------------------------------------------
+// Precision conversion of host-staged FP64 data.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void from_f64_kernel(const double *__restrict__ in, T *__restrict__ out, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (T)in[i];
+}
+template <typename T>
+__global__ void to_f64_kernel(const T *__restrict__ in, double *__restrict__ out, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (double)in[i];
+}
+
+}  // namespace spstd

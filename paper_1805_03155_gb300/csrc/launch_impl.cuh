@@ -1,0 +1,119 @@
+// launch_impl.cuh -- definitions of Launch<T>; included by exactly one
+// translation unit per precision.
+#pragma once
+
+#include "launch.cuh"
+
+namespace spstd {
+
+template <typename T>
+cudaError_t Launch<T>::xpass(int N, const PassArgs<T> &a, cudaStream_t s)
+{
+#define SPSTD_X(n) xpass_n<T, n>(a, s)
+    switch (N) {
+    case 2: return SPSTD_X(2);
+    case 4: return SPSTD_X(4);
+    case 8: return SPSTD_X(8);
+    case 16: return SPSTD_X(16);
+    case 32: return SPSTD_X(32);
+    case 64: return SPSTD_X(64);
+    case 128: return SPSTD_X(128);
+    case 256: return SPSTD_X(256);
+    case 512: return SPSTD_X(512);
+    case 1024: return SPSTD_X(1024);
+    case 2048: return SPSTD_X(2048);
+    case 4096: return SPSTD_X(4096);
+    case 8192: return SPSTD_X(8192);
+    default: return cudaErrorInvalidValue;
+    }
+#undef SPSTD_X
+}
+
+template <typename T>
+cudaError_t Launch<T>::spass(int N, const PassArgs<T> &a, cudaStream_t s)
+{
+#define SPSTD_S(n) spass_n<T, n>(a, s)
+    switch (N) {
+    case 2: return SPSTD_S(2);
+    case 4: return SPSTD_S(4);
+    case 8: return SPSTD_S(8);
+    case 16: return SPSTD_S(16);
+    case 32: return SPSTD_S(32);
+    case 64: return SPSTD_S(64);
+    case 128: return SPSTD_S(128);
+    case 256: return SPSTD_S(256);
+    case 512: return SPSTD_S(512);
+    case 1024: return SPSTD_S(1024);
+    default: return cudaErrorInvalidValue;
+    }
+#undef SPSTD_S
+}
+
+template <typename T>
+int Launch<T>::resident_max_n()
+{
+    return sizeof(T) == 4 ? 8192 : 4096;
+}
+
+template <typename T>
+cudaError_t Launch<T>::resident1d(int N, const ResidentArgs<T> &a, cudaStream_t s)
+{
+#define SPSTD_R(n) resident_n<T, n>(a, s)
+    switch (N) {
+    case 2: return SPSTD_R(2);
+    case 4: return SPSTD_R(4);
+    case 8: return SPSTD_R(8);
+    case 16: return SPSTD_R(16);
+    case 32: return SPSTD_R(32);
+    case 64: return SPSTD_R(64);
+    case 128: return SPSTD_R(128);
+    case 256: return SPSTD_R(256);
+    case 512: return SPSTD_R(512);
+    case 1024: return SPSTD_R(1024);
+    case 2048: return SPSTD_R(2048);
+    case 4096: return SPSTD_R(4096);
+    default: break;
+    }
+    if constexpr (sizeof(T) == 4) {
+        if (N == 8192) return SPSTD_R(8192);
+    }
+    return cudaErrorInvalidValue;
+#undef SPSTD_R
+}
+
+template <typename T>
+cudaError_t Launch<T>::probe(const T *psiR, const T *psiI, const ProbeArgs &a, cudaStream_t s)
+{
+    probe_kernel<T><<<1, 32, 0, s>>>(psiR, psiI, a);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::dot2(const T *x1, const T *y1, const T *x2, const T *y2, int64_t n, double *partial,
+                            int nblocks, cudaStream_t s)
+{
+    dot2_kernel<T><<<nblocks, 256, 0, s>>>(x1, y1, x2, y2, n, partial);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::from_f64(const double *in, T *out, int64_t n, cudaStream_t s)
+{
+    int64_t b = (n + 255) / 256;
+    if (b > 4096) b = 4096;
+    if (b < 1) b = 1;
+    from_f64_kernel<T><<<(unsigned)b, 256, 0, s>>>(in, out, n);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::to_f64(const T *in, double *out, int64_t n, cudaStream_t s)
+{
+    int64_t b = (n + 255) / 256;
+    if (b > 4096) b = 4096;
+    if (b < 1) b = 1;
+    to_f64_kernel<T><<<(unsigned)b, 256, 0, s>>>(in, out, n);
+    return cudaGetLastError();
+}
+
+}  // namespace spstd
