@@ -47,11 +47,19 @@ def test_hamiltonian_apply_matches_oracle(shape, precision):
     p = small_problem(shape)
     s = gpu_solver(p, precision)
     g = oracle_grid(p)
+    # error scale of a spectral second derivative: the operator norm of H times
+    # the field's size (a rounding of the input at the highest wave number is
+    # amplified by (pi/dx)^2), ||H|| <= (hbar^2/2m) sum (pi/dx_d)^2 + max V
+    hnorm = p.hbar ** 2 / (2 * p.mass) * sum((np.pi * p.n[a] / (p.hi[a] - p.lo[a])) ** 2
+                                             for a in range(p.dims)) + np.max(np.abs(p.V))
     for which, f in ((0, p.psiR), (1, p.psiI)):
         got = s.spstd_apply_hamiltonian(which)
         ref = p.hbar * oracle.apply_K(f, p.V, g)
-        tol = 1e-11 if precision == 64 else 2e-5
-        assert np.max(np.abs(got - ref)) <= tol * np.max(np.abs(ref)), (which, np.max(np.abs(got - ref)))
+        err = np.max(np.abs(got - ref))
+        if precision == 64:
+            assert err <= 1e-11 * np.max(np.abs(ref)), (which, err)
+        else:  # ~8 FP32 epsilons of ||H|| max|psi|
+            assert err <= 1e-6 * hnorm * np.max(np.abs(f)), (which, err, hnorm)
     s.close()
 
 
@@ -154,7 +162,10 @@ def test_spectrum_matches_oracle_on_well(precision):
     oEc = np.array([oracle.phase_correct(t, c, d) / p.dt for t in th])
     big = oA > 1e-2 * oA.max()
     assert len(E) == len(oE)
-    tol = 1e-9 if precision == 64 else 1e-5
+    # FP64: both sides maximise the same flat peak |S(theta)| = f0 (1 - a d^2),
+    # a ~ (M/2)^2; rounding-level differences of f move the argmax by
+    # ~sqrt(eps/a), 1e-7 relative at M = 3000.  FP32: the 1e-5 energy target.
+    tol = 1e-6 if precision == 64 else 1e-5
     assert np.max(np.abs(E[big] - oE[big]) / oE[big]) <= tol
     assert np.max(np.abs(Ec[big] - oEc[big]) / oEc[big]) <= tol
     assert np.allclose(A[big], oA[big], rtol=1e-4)
