@@ -195,6 +195,27 @@ spstd_status spstd_launch_count(const spstd_ctx *ctx, int64_t nsteps, int64_t *l
 #define SPSTD_KERNEL_KINDS 5
 spstd_status spstd_profile_steps(spstd_ctx *ctx, int64_t nsteps, double *ms, int64_t *cnt);
 
+/* Norm without device allocation (the paper has no counterpart: this is a
+ * service for callers that may not allocate device memory where they call).
+ * Computes *d_norm = cell_volume * sum_i (psiR[i]^2 + psiI[i]^2) in FP64, in a
+ * fixed order, from n values of psiR and psiI (device pointers, FP32 or FP64
+ * per precision, caller-owned) into d_norm (a device double, caller-owned),
+ * enqueued on stream (cudaStream_t; NULL = legacy default) without waiting.
+ * Its per-block partial sums live in a static device array of
+ * SPSTD_NOALLOC_MAX_PARTIALS doubles (512 KB on every GPU that loads the
+ * library, kept until the process exits) instead of caller memory; it calls no
+ * cudaMalloc, cudaFree or allocating library routine.  Every call on a device
+ * shares that array: calls that overlap on the GPU race and must be
+ * serialised (e.g. one stream).  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress, with that device current);
+ * make that first call before any stream capture.  SPSTD_EINVAL for NULL
+ * pointers, n <= 0, a bad precision, or n > SPSTD_NOALLOC_MAX_ELEMS;
+ * SPSTD_ECUDA if the set-up or a launch fails. */
+#define SPSTD_NOALLOC_MAX_PARTIALS 65536
+#define SPSTD_NOALLOC_MAX_ELEMS ((int64_t)SPSTD_NOALLOC_MAX_PARTIALS * 2048)
+spstd_status spstd_norm_noalloc(const void *psiR, const void *psiI, int64_t n, int precision,
+                                double cell_volume, double *d_norm, void *stream);
+
 /* Human-readable text of the last failure on ctx (never NULL). */
 const char *spstd_last_error(const spstd_ctx *ctx);
 const char *spstd_status_string(spstd_status s);

@@ -94,6 +94,7 @@ def lib():
         "spstd_get_coefficients": (C.c_int, [vp, C.POINTER(C.c_int), dp, dp]),
         "spstd_launch_count": (C.c_int, [vp, C.c_int64, ip]),
         "spstd_profile_steps": (C.c_int, [vp, C.c_int64, dp, ip]),
+        "spstd_norm_noalloc": (C.c_int, [vp, vp, C.c_int64, C.c_int, C.c_double, vp, vp]),
         "spstd_last_error": (C.c_char_p, [vp]),
         "spstd_status_string": (C.c_char_p, [C.c_int]),
     }
@@ -275,6 +276,17 @@ def stability_limit(cfg: spstd_config, vmax=0.0):
     if st != SPSTD_OK:
         raise SpstdError(st, lib().spstd_status_string(st).decode())
     return s.value, dtm.value
+
+
+NOALLOC_MAX_ELEMS = 65536 * 2048
+
+
+def spstd_norm_noalloc(psiR_ptr, psiI_ptr, n, precision, cell_volume, out_ptr, stream_ptr=0):
+    """Norm of two device arrays into a device double, with no device
+    allocation (scratch in the library's static device array).  Pointers are
+    integers (e.g. torch tensor data_ptr()); returns the status code."""
+    return lib().spstd_norm_noalloc(C.c_void_p(psiR_ptr), C.c_void_p(psiI_ptr), int(n), int(precision),
+                                    float(cell_volume), C.c_void_p(out_ptr), C.c_void_p(stream_ptr))
 
 
 def solver_for(problem, precision=64, probe_capacity=None, stream=None, device=0, dt=None):
