@@ -47,7 +47,7 @@ typedef enum {
     SPSTD_ECUDA = 3,        /* a CUDA runtime call failed (message in last_error) */
     SPSTD_EUNSTABLE = 4,    /* dt above the stability limit s_star/w_max (Eq. 25/30) */
     SPSTD_EDIVERGED = 5,    /* norm or energy is NaN/Inf */
-    SPSTD_ETIMEOUT = 6,     /* reserved: a bounded device wait gave up */
+    SPSTD_ETIMEOUT = 6,     /* a bounded device wait gave up (reported at the next synchronising call) */
     SPSTD_ENOTREADY = 7,    /* nothing to return yet (no probe samples) */
     SPSTD_EUNSUPPORTED = 8  /* valid request this build does not implement */
 } spstd_status;

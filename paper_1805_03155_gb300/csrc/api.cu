@@ -6,6 +6,8 @@
 // the stability limit of Eq. 23-25, twiddle and k^2 tables, dispersion
 // inversion of a few spectrum peaks); every step of the time integration,
 // every reduction and every spectrum runs in the CUDA kernels.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -18,6 +20,7 @@
 
 #include "../../include/spstd.h"
 #include "launch.cuh"
+#include "pass_tma_launch.h"
 #include "spectrum.h"
 
 using namespace spstd;
@@ -36,7 +39,7 @@ struct HalfStage {
 };
 
 struct Layout {
-    size_t psi[2], V, tmp, staging, ring, counter, partial, dout, tw[3], mult, spec, total;
+    size_t psi[2], V, tmp, staging, ring, counter, status, partial, dout, tw[3], mult, spec, total;
 };
 
 bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
@@ -242,6 +245,7 @@ Layout make_layout(const spstd_config &cfg, int m)
     L.staging = take(cfg.precision == 32 ? 8 * ntot : 0);
     L.ring = take(16 * (size_t)std::max(cfg.n_probe, 1) * cfg.probe_capacity);
     L.counter = take(8);
+    L.status = take(8);
     L.partial = take(8 * kPartials);
     L.dout = take(8 * 8);
     int64_t sum_n = 0;
@@ -272,8 +276,12 @@ struct spstd_ctx {
     int64_t steps_taken = 0;
     cudaGraphExec_t gexec = nullptr;
     std::string err;
+    // pipelined FP32 passes: tensor maps [field: psi_R, psi_I, tmp][view: x, y, z]
+    bool tma[3] = {false, false, false};
+    CUtensorMap tmap[3][3];
 
     void *ptr(size_t off) { return ws + off; }
+    size_t field_off(int f) const { return f == 0 ? L.psi[0] : f == 1 ? L.psi[1] : L.tmp; }
 };
 
 namespace {
@@ -292,6 +300,18 @@ spstd_status cuda_fail(spstd_ctx *ctx, cudaError_t e, const char *where)
         cudaError_t e_ = (call);                              \
         if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
     } while (0)
+
+// Reads the device status word after a synchronisation: a kernel that gave up
+// a bounded wait leaves kStatusTimeout there.
+spstd_status check_device_status(spstd_ctx *ctx)
+{
+    int st = 0;
+    cudaError_t e = cudaMemcpyAsync(&st, ctx->ptr(ctx->L.status), sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "status read");
+    if (st != 0) return fail(ctx, SPSTD_ETIMEOUT, "a device wait timed out (status word set by a pass kernel)");
+    return SPSTD_OK;
+}
 
 void drop_graph(spstd_ctx *ctx)
 {
@@ -350,6 +370,61 @@ spstd_status upload_tables(spstd_ctx *ctx)
     // the host vectors die here: wait until the copies have read them
     SPSTD_CU(ctx, cudaStreamSynchronize(ctx->stream));
     return SPSTD_OK;
+}
+
+// cuTensorMapEncodeTiled from the driver, without linking libcuda.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// 3D FP32 tensor map over a field viewed as dims (d0, d1, d2), x fastest, with
+// the given box; out-of-range box elements load as zero and are not stored.
+bool encode_map(CUtensorMap *m, void *base, uint64_t d0, uint64_t d1, uint64_t d2, uint32_t b0, uint32_t b1,
+                uint32_t b2, bool swizzle128)
+{
+    auto enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[3] = {d0, d1, d2};
+    const cuuint64_t strides[2] = {d0 * sizeof(float), d0 * d1 * sizeof(float)};
+    const cuuint32_t box[3] = {b0, b1, b2};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Enables the pipelined passes for FP32 axes of 64..256 points.
+void setup_tma(spstd_ctx *ctx)
+{
+    const spstd_config &cfg = ctx->cfg;
+    if (cfg.precision != 32 || cfg.dims < 2) return;
+    const uint64_t n0 = cfg.n[0], n1 = cfg.n[1], n2 = cfg.n[2];
+    auto eligible = [](int64_t n) { return n == 64 || n == 128 || n == 256; };
+    bool want[3] = {eligible(cfg.n[0]), eligible(cfg.n[1]), cfg.dims == 3 && eligible(cfg.n[2])};
+    for (int v = 0; v < 3; ++v) {
+        if (!want[v]) continue;
+        bool ok = true;
+        for (int f = 0; f < 3 && ok; ++f) {
+            void *base = ctx->ptr(ctx->field_off(f));
+            if (v == 0)
+                ok = encode_map(&ctx->tmap[f][0], base, n0, n1 * n2, 1, (uint32_t)n0, tma_rows_per_tile(), 1, false);
+            if (v == 1)
+                ok = encode_map(&ctx->tmap[f][1], base, n0, n1, n2, tma_cols_per_tile(), (uint32_t)n1, 1, false);
+            if (v == 2)
+                ok = encode_map(&ctx->tmap[f][2], base, n0, n1, n2, tma_cols_per_tile(), 1, (uint32_t)n2, false);
+        }
+        ctx->tma[v] = ok;
+    }
 }
 
 spstd_status set_dt(spstd_ctx *ctx, double vmax)
@@ -414,47 +489,70 @@ struct LaunchTimer {
     } while (0)
 
 template <typename T>
-cudaError_t enqueue_apply(spstd_ctx *ctx, const T *src, T *dst, int table, double bV, int reverse, cudaStream_t s,
+T *field_ptr(spstd_ctx *ctx, int f)
+{
+    return (T *)ctx->ptr(ctx->field_off(f));
+}
+
+// dst += a sum_d L_d src + bV V src for fields fsrc -> fdst (0 psi_R, 1 psi_I,
+// 2 scratch), multiplier set `table`; the V term rides on the x pass.
+template <typename T>
+cudaError_t enqueue_apply(spstd_ctx *ctx, int fsrc, int fdst, int table, double bV, int reverse, cudaStream_t s,
                           LaunchTimer *timer = nullptr)
 {
     const spstd_config &cfg = ctx->cfg;
+    const T *src = field_ptr<T>(ctx, fsrc);
+    T *dst = field_ptr<T>(ctx, fdst);
     const T *mult = (const T *)ctx->ptr(ctx->L.mult) + (size_t)table * ctx->sum_n;
     const int64_t n0 = cfg.n[0], n1 = cfg.n[1], n2 = cfg.n[2];
-    PassArgs<T> x{};
-    x.src = src;
-    x.dst = dst;
-    x.V = (const T *)ctx->ptr(ctx->L.V);
-    x.tw = (const cpx<T> *)ctx->ptr(ctx->L.tw[0]);
-    x.mult = mult;
-    x.bV = (T)bV;
-    x.use_V = 1;
-    x.n_rows = n1 * n2;
-    x.reverse = reverse;
-    SPSTD_TIMED(timer, s, 0, Launch<T>::xpass((int)n0, x, s));
-    if (cfg.dims < 2) return cudaSuccess;
-    PassArgs<T> y{};
-    y.src = src;
-    y.dst = dst;
-    y.tw = (const cpx<T> *)ctx->ptr(ctx->L.tw[1]);
-    y.mult = mult + n0;
-    y.stride = n0;
-    y.outer_stride = n0 * n1;
-    y.n_outer = n2;
-    y.nx = (int)n0;
-    y.reverse = !reverse;
-    SPSTD_TIMED(timer, s, 1, Launch<T>::spass((int)n1, y, s));
-    if (cfg.dims < 3) return cudaSuccess;
-    PassArgs<T> z{};
-    z.src = src;
-    z.dst = dst;
-    z.tw = (const cpx<T> *)ctx->ptr(ctx->L.tw[2]);
-    z.mult = mult + n0 + n1;
-    z.stride = n0 * n1;
-    z.outer_stride = n0;
-    z.n_outer = n1;
-    z.nx = (int)n0;
-    z.reverse = reverse;
-    SPSTD_TIMED(timer, s, 2, Launch<T>::spass((int)n2, z, s));
+    const int64_t off[3] = {0, n0, n0 + n1};
+    int *status = (int *)ctx->ptr(ctx->L.status);
+    for (int ax = 0; ax < cfg.dims; ++ax) {
+        const int rev = ax == 1 ? !reverse : reverse;
+        const int64_t N = cfg.n[ax];
+        const cpx<T> *tw = (const cpx<T> *)ctx->ptr(ctx->L.tw[ax]);
+        if constexpr (sizeof(T) == 4) {
+            if (ctx->tma[ax]) {
+                TmaPassArgs ta{};
+                ta.tw = (const float2 *)tw;
+                ta.mult = (const float *)(mult + off[ax]);
+                ta.V = (const float *)ctx->ptr(ctx->L.V);
+                ta.bV = (float)bV;
+                ta.use_V = ax == 0;
+                ta.rows = (int)(n1 * n2);
+                ta.axis = ax;
+                ta.reverse = rev;
+                ta.status = status;
+                if (ax == 0) {
+                    ta.n_tiles = (int)((n1 * n2 + tma_rows_per_tile() - 1) / tma_rows_per_tile());
+                } else {
+                    ta.n_xt = (int)((n0 + tma_cols_per_tile() - 1) / tma_cols_per_tile());
+                    ta.n_tiles = ta.n_xt * (int)(ax == 1 ? n2 : n1);
+                }
+                SPSTD_TIMED(timer, s, ax, launch_pass_tma(ax, (int)N, ctx->tmap[fsrc][ax], ctx->tmap[fdst][ax], ta, s));
+                continue;
+            }
+        }
+        PassArgs<T> a{};
+        a.src = src;
+        a.dst = dst;
+        a.tw = tw;
+        a.mult = mult + off[ax];
+        a.reverse = rev;
+        if (ax == 0) {
+            a.V = (const T *)ctx->ptr(ctx->L.V);
+            a.bV = (T)bV;
+            a.use_V = 1;
+            a.n_rows = n1 * n2;
+            SPSTD_TIMED(timer, s, 0, Launch<T>::xpass((int)N, a, s));
+        } else {
+            a.stride = ax == 1 ? n0 : n0 * n1;
+            a.outer_stride = ax == 1 ? n0 * n1 : n0;
+            a.n_outer = ax == 1 ? n2 : n1;
+            a.nx = (int)n0;
+            SPSTD_TIMED(timer, s, ax, Launch<T>::spass((int)N, a, s));
+        }
+    }
     return cudaSuccess;
 }
 
@@ -478,7 +576,7 @@ cudaError_t enqueue_one_step(spstd_ctx *ctx, cudaStream_t s, LaunchTimer *timer 
     T *psi[2] = {(T *)ctx->ptr(ctx->L.psi[0]), (T *)ctx->ptr(ctx->L.psi[1])};
     int parity = 0;
     for (const HalfStage &h : ctx->hs) {
-        cudaError_t e = enqueue_apply<T>(ctx, psi[1 - h.dst], psi[h.dst], h.table, h.bV, parity, s, timer);
+        cudaError_t e = enqueue_apply<T>(ctx, 1 - h.dst, h.dst, h.table, h.bV, parity, s, timer);
         if (e != cudaSuccess) return e;
         parity ^= 1;
     }
@@ -533,6 +631,8 @@ spstd_status step_impl(spstd_ctx *ctx, int64_t nsteps)
             none.nx = (int)cfg.n[0];
             SPSTD_CU(ctx, Launch<T>::spass((int)cfg.n[1], none, ctx->stream));
             if (cfg.dims == 3) SPSTD_CU(ctx, Launch<T>::spass((int)cfg.n[2], none, ctx->stream));
+            for (int ax = 0; ax < cfg.dims; ++ax)
+                if (ctx->tma[ax]) SPSTD_CU(ctx, prepare_pass_tma(ax, (int)cfg.n[ax]));
             cudaGraph_t g = nullptr;
             SPSTD_CU(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
             for (int i = 0; i < kGraphSteps; ++i) {
@@ -678,6 +778,7 @@ spstd_status spstd_create(const spstd_config *cfg, void *d_workspace, size_t wor
     if (cudaMemsetAsync(ctx->ws, 0, ctx->L.total, ctx->stream) != cudaSuccess) return bail(SPSTD_ECUDA);
     st = set_dt(ctx, 0.0);
     if (st != SPSTD_OK) return bail(st);
+    setup_tma(ctx);
     *out = ctx;
     return SPSTD_OK;
 }
@@ -718,7 +819,7 @@ spstd_status download_field(spstd_ctx *ctx, const void *dev, double *host)
         SPSTD_CU(ctx, cudaMemcpyAsync(host, st, 8 * ctx->ntot, cudaMemcpyDeviceToHost, ctx->stream));
     }
     SPSTD_CU(ctx, cudaStreamSynchronize(ctx->stream));
-    return SPSTD_OK;
+    return check_device_status(ctx);
 }
 }  // namespace
 
@@ -781,6 +882,8 @@ spstd_status spstd_probe(spstd_ctx *ctx, int p, double *re, double *im, int64_t 
     SPSTD_CU(ctx, cudaMemcpyAsync(row.data(), (double2 *)ctx->ptr(ctx->L.ring) + (size_t)p * C, sizeof(double2) * C,
                                   cudaMemcpyDeviceToHost, ctx->stream));
     SPSTD_CU(ctx, cudaStreamSynchronize(ctx->stream));
+    spstd_status ds = check_device_status(ctx);
+    if (ds != SPSTD_OK) return ds;
     const int64_t nout = std::min(kept, cap);
     const int64_t first = ctx->steps_taken - nout;  // global index of the first sample returned
     for (int64_t i = 0; i < nout; ++i) {
@@ -825,6 +928,8 @@ spstd_status spstd_spectrum(spstd_ctx *ctx, int p, int64_t nfft, int max_peaks, 
     a.h_theta = th.data();
     a.h_amp = am.data();
     SPSTD_CU(ctx, launch_spectrum(a, ctx->stream));
+    spstd_status ds = check_device_status(ctx);
+    if (ds != SPSTD_OK) return ds;
     std::vector<std::pair<double, double>> res;
     for (int i = 0; i < np; ++i) {
         double e = ctx->cfg.hbar * th[i] / ctx->dt;
@@ -859,17 +964,19 @@ spstd_status energy_norm_impl(spstd_ctx *ctx, double *norm, double *energy)
     SPSTD_CU(ctx, launch_sum_partials(part, nb, dout + 0, s));
     // sum psi_R H psi_R
     SPSTD_CU(ctx, cudaMemsetAsync(tmp, 0, sizeof(T) * ctx->ntot, s));
-    SPSTD_CU(ctx, enqueue_apply<T>(ctx, pr, tmp, tH, 1.0, 0, s));
+    SPSTD_CU(ctx, enqueue_apply<T>(ctx, 0, 2, tH, 1.0, 0, s));
     SPSTD_CU(ctx, Launch<T>::dot2(pr, tmp, nullptr, nullptr, ctx->ntot, part, nb, s));
     SPSTD_CU(ctx, launch_sum_partials(part, nb, dout + 1, s));
     // sum psi_I H psi_I
     SPSTD_CU(ctx, cudaMemsetAsync(tmp, 0, sizeof(T) * ctx->ntot, s));
-    SPSTD_CU(ctx, enqueue_apply<T>(ctx, pi, tmp, tH, 1.0, 0, s));
+    SPSTD_CU(ctx, enqueue_apply<T>(ctx, 1, 2, tH, 1.0, 0, s));
     SPSTD_CU(ctx, Launch<T>::dot2(pi, tmp, nullptr, nullptr, ctx->ntot, part, nb, s));
     SPSTD_CU(ctx, launch_sum_partials(part, nb, dout + 2, s));
     double h[3];
     SPSTD_CU(ctx, cudaMemcpyAsync(h, dout, sizeof(h), cudaMemcpyDeviceToHost, s));
     SPSTD_CU(ctx, cudaStreamSynchronize(s));
+    spstd_status ds = check_device_status(ctx);
+    if (ds != SPSTD_OK) return ds;
     double dV = 1.0;
     for (int a = 0; a < ctx->cfg.dims; ++a) dV *= (ctx->cfg.hi[a] - ctx->cfg.lo[a]) / (double)ctx->cfg.n[a];
     *norm = dV * h[0];
@@ -884,7 +991,8 @@ spstd_status apply_h_impl(spstd_ctx *ctx, int which, double *out)
     T *src = (T *)ctx->ptr(ctx->L.psi[which]);
     T *tmp = (T *)ctx->ptr(ctx->L.tmp);
     SPSTD_CU(ctx, cudaMemsetAsync(tmp, 0, sizeof(T) * ctx->ntot, ctx->stream));
-    SPSTD_CU(ctx, enqueue_apply<T>(ctx, src, tmp, 2 * ctx->m, 1.0, 0, ctx->stream));
+    (void)src;
+    SPSTD_CU(ctx, enqueue_apply<T>(ctx, which, 2, 2 * ctx->m, 1.0, 0, ctx->stream));
     return download_field<T>(ctx, tmp, out);
 }
 }  // namespace
