@@ -32,6 +32,18 @@ cudaError_t persistent_grid(int threads, size_t smem, int *grid)
     return cudaSuccess;
 }
 
+// Complex points per thread of the pipelined x and strided passes.
+template <int N>
+constexpr int tma_e_x()
+{
+    return 16;
+}
+template <int N>
+constexpr int tma_e_s()
+{
+    return 16;
+}
+
 template <int N>
 cudaError_t pass_n(int axis, const CUtensorMap *ms, const CUtensorMap *md, const TmaPassArgs *a, cudaStream_t s)
 {
@@ -39,17 +51,19 @@ cudaError_t pass_n(int axis, const CUtensorMap *ms, const CUtensorMap *md, const
     int grid = 0;
     cudaError_t e;
     if (axis == 0) {
-        e = persistent_grid<xpass_tma_kernel<N>>(N, smem, &grid);
+        constexpr int E = tma_e_x<N>(), TT = N / E;
+        e = persistent_grid<xpass_tma_kernel<N, E>>(16 * TT, smem, &grid);
         if (e != cudaSuccess || !a) return e;
         if (a->n_tiles < grid) grid = a->n_tiles;
         if (grid <= 0) return cudaSuccess;
-        xpass_tma_kernel<N><<<grid, dim3(N / 16, 16), smem, s>>>(*ms, *md, *a);
+        xpass_tma_kernel<N, E><<<grid, dim3(TT, 16), smem, s>>>(*ms, *md, *a);
     } else {
-        e = persistent_grid<spass_tma_kernel<N>>(N, smem, &grid);
+        constexpr int E = tma_e_s<N>(), TT = N / E;
+        e = persistent_grid<spass_tma_kernel<N, E>>(16 * TT, smem, &grid);
         if (e != cudaSuccess || !a) return e;
         if (a->n_tiles < grid) grid = a->n_tiles;
         if (grid <= 0) return cudaSuccess;
-        spass_tma_kernel<N><<<grid, dim3(16, N / 16), smem, s>>>(*ms, *md, *a);
+        spass_tma_kernel<N, E><<<grid, dim3(16, TT), smem, s>>>(*ms, *md, *a);
     }
     return cudaGetLastError();
 }

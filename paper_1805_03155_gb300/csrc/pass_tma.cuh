@@ -10,9 +10,10 @@
 // store has one tile of slack before its stage is reloaded.
 //
 //   x pass:        tile = 32 contiguous rows of N points (16 complex line
-//                  pairs), block (N/16, 16); also adds bV V src.
+//                  pairs), block (N/E, 16); also adds bV V src.
 //   strided pass:  tile = N points along y or z x 32 adjacent x columns (16
-//                  column pairs), block (16, N/16).
+//                  column pairs), block (16, N/E).
+// E is the number of complex points a thread holds.
 // Waits are bounded: on a timeout the block records kStatusTimeout, lets its
 // stores drain and returns.
 #pragma once
@@ -112,17 +113,17 @@ __device__ __forceinline__ void tma_setup(const TmaSmem &m, const TmaPassArgs &a
 // ---------------------------------------------------------------------------
 // x pass
 // ---------------------------------------------------------------------------
-template <int N>
-__global__ void __launch_bounds__(N, 1)
+template <int N, int E>
+__global__ void __launch_bounds__(16 * (N / E), 1)
 xpass_tma_kernel(const __grid_constant__ CUtensorMap msrc, const __grid_constant__ CUtensorMap mdst,
                  const TmaPassArgs a)
 {
-    constexpr int E = 16, TT = N / E;
+    constexpr int TT = N / E;
     constexpr uint32_t kTileBytes = kTmaRows * N * sizeof(float);
     extern __shared__ unsigned char smem_raw[];
     const TmaSmem m = tma_carve<N>(smem_raw);
     const int t = threadIdx.x, l = threadIdx.y, tid = l * TT + t;
-    tma_setup<N>(m, a, tid, N);
+    tma_setup<N>(m, a, tid, 16 * TT);
 
     const int nk = (int)blockIdx.x < a.n_tiles ? (a.n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     auto tile_of = [&](int k) {
@@ -207,18 +208,18 @@ xpass_tma_kernel(const __grid_constant__ CUtensorMap msrc, const __grid_constant
 // ---------------------------------------------------------------------------
 // strided pass (y or z)
 // ---------------------------------------------------------------------------
-template <int N>
-__global__ void __launch_bounds__(N, 1)
+template <int N, int E>
+__global__ void __launch_bounds__(16 * (N / E), 1)
 spass_tma_kernel(const __grid_constant__ CUtensorMap msrc, const __grid_constant__ CUtensorMap mdst,
                  const TmaPassArgs a)
 {
-    constexpr int E = 16, TT = N / E;
+    constexpr int TT = N / E;
     constexpr uint32_t kTileBytes = kTmaCols * N * sizeof(float);
     extern __shared__ unsigned char smem_raw[];
     const TmaSmem m = tma_carve<N>(smem_raw);
     // block (16, TT): a warp covers the 16 column pairs of two rows
     const int p = threadIdx.x, t = threadIdx.y, tid = t * 16 + p;
-    tma_setup<N>(m, a, tid, N);
+    tma_setup<N>(m, a, tid, 16 * TT);
 
     const int nk = (int)blockIdx.x < a.n_tiles ? (a.n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     auto coords = [&](int k, int &x, int &y, int &z) {
