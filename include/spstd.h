@@ -39,6 +39,7 @@ extern "C" {
 #endif
 
 typedef struct spstd_ctx spstd_ctx;
+typedef struct spstd_batch spstd_batch;
 
 typedef enum {
     SPSTD_OK = 0,
@@ -215,6 +216,41 @@ spstd_status spstd_profile_steps(spstd_ctx *ctx, int64_t nsteps, double *ms, int
 #define SPSTD_NOALLOC_MAX_ELEMS ((int64_t)SPSTD_NOALLOC_MAX_PARTIALS * 2048)
 spstd_status spstd_norm_noalloc(const void *psiR, const void *psiI, int64_t n, int precision,
                                 double cell_volume, double *d_norm, void *stream);
+
+/* ---- Batches: many independent solves advanced by one call ---------------
+ * A batch advances every member context by the same number of steps, each with
+ * its own grid, V, dt, integrator and probes.  1D members of one length run all
+ * steps of a call in one resident block each (one launch per length); 2D/3D
+ * members that share dims, sizes, precision and integrator run every pass of
+ * every half-stage as one launch over all their tiles; groups run on parallel
+ * branches of a captured CUDA graph, replayed in chunks.  Results equal those
+ * of stepping each member alone up to FP rounding order (the single-context
+ * FP32 path may use the pipelined TMA passes, a batch the plain passes).
+ * Members stay usable (get_state, probe, spectrum, energy_norm) between batch
+ * steps; do not call spstd_step on a member while it is in a batch.
+ * Device memory: one caller-owned workspace of spstd_batch_workspace_size()
+ * bytes (256-byte aligned) for the member descriptors. */
+typedef struct spstd_batch spstd_batch;
+spstd_status spstd_batch_workspace_size(int max_members, size_t *bytes);
+/* stream: cudaStream_t for all batch work (NULL = legacy default stream);
+ * device: the CUDA device every member lives on. */
+spstd_status spstd_batch_create(int max_members, int device, void *stream, void *d_workspace,
+                                size_t workspace_bytes, spstd_batch **out);
+spstd_status spstd_batch_destroy(spstd_batch *b);
+/* Adds ctx (waits for ctx's own stream first); *slot receives its index.
+ * SPSTD_ENOTREADY when the batch is full, SPSTD_EINVAL if ctx is already in a
+ * batch or on another device. */
+spstd_status spstd_batch_add(spstd_batch *b, spstd_ctx *ctx, int *slot);
+/* Removes the member in slot after the batch stream has drained. */
+spstd_status spstd_batch_remove(spstd_batch *b, int slot);
+spstd_status spstd_batch_size(const spstd_batch *b, int *members);
+/* Enqueues nsteps steps of every member on the batch stream (asynchronous). */
+spstd_status spstd_batch_step(spstd_batch *b, int64_t nsteps);
+/* Waits for the batch stream. */
+spstd_status spstd_batch_sync(spstd_batch *b);
+/* Kernel launches one spstd_batch_step(b, nsteps) runs (graph nodes included). */
+spstd_status spstd_batch_launch_count(const spstd_batch *b, int64_t nsteps, int64_t *launches);
+const char *spstd_batch_last_error(const spstd_batch *b);
 
 /* Human-readable text of the last failure on ctx (never NULL). */
 const char *spstd_last_error(const spstd_ctx *ctx);

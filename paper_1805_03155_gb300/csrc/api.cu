@@ -279,6 +279,7 @@ struct spstd_ctx {
     // pipelined FP32 passes: tensor maps [field: psi_R, psi_I, tmp][view: x, y, z]
     bool tma[3] = {false, false, false};
     CUtensorMap tmap[3][3];
+    spstd_batch *batch = nullptr;  // batch this context is a member of
 
     void *ptr(size_t off) { return ws + off; }
     size_t field_off(int f) const { return f == 0 ? L.psi[0] : f == 1 ? L.psi[1] : L.tmp; }
@@ -1085,6 +1086,519 @@ spstd_status spstd_launch_count(const spstd_ctx *ctx, int64_t nsteps, int64_t *l
         *launches = nsteps * ((int64_t)ctx->hs.size() * ctx->cfg.dims + (ctx->cfg.n_probe > 0 ? 1 : 0));
     }
     return SPSTD_OK;
+}
+
+}  // extern "C"
+
+// =============================================================================
+// Batches: many independent solves advanced together.
+//
+// Members are grouped by shape: 1D members of one length and precision run
+// every step of a call in one resident block each (one launch per group, on a
+// side stream); 2D/3D members sharing dims, sizes, precision and integrator
+// run each pass of each half-stage as one batched launch over all members'
+// tiles (descriptors per member: its own fields, V, dt-scaled multipliers,
+// probes).  Groups of one step run on parallel graph branches, and chunks of
+// steps are replayed from one captured CUDA graph.
+// =============================================================================
+namespace {
+
+constexpr int kBatchGraphSteps = 10;
+constexpr int kBatchStreams = 4;
+constexpr size_t kBatchBytesPerMember = 8192;
+
+struct BatchGroup1D {
+    int precision;
+    int64_t N;
+    std::vector<int> slots;
+    size_t args_off;
+};
+
+struct BatchGroupND {
+    int precision, dims, m;
+    int64_t n[3];
+    double c[SPSTD_MAX_STAGES], d[SPSTD_MAX_STAGES];
+    std::vector<int> slots;
+    int nh;
+    int tiles[3];
+    size_t args_off;   // PassArgs<T> [nh * dims][M]
+    size_t probe_off;  // ProbeMember<T> [M]
+};
+
+}  // namespace
+
+struct spstd_batch {
+    int device = 0;
+    int max_members = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t side = nullptr;
+    cudaStream_t cap = nullptr;
+    cudaStream_t branch[kBatchStreams] = {nullptr};
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_branch[kBatchStreams] = {nullptr};
+    unsigned char *ws = nullptr;
+    size_t ws_bytes = 0;
+    std::vector<spstd_ctx *> slots;
+    bool dirty = true;
+    std::vector<BatchGroup1D> g1;
+    std::vector<BatchGroupND> gn;
+    cudaGraphExec_t gexec = nullptr;
+    std::string err;
+};
+
+namespace {
+
+spstd_status bfail(spstd_batch *b, spstd_status s, const std::string &msg)
+{
+    if (b) b->err = msg;
+    return s;
+}
+#define SPSTD_BCU(b, call)                                                                  \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess) return bfail(b, SPSTD_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+bool same_integrator(const spstd_ctx *a, int m, const double *c, const double *d)
+{
+    if (a->m != m) return false;
+    for (int l = 0; l < m; ++l)
+        if (a->c[l] != c[l] || a->d[l] != d[l]) return false;
+    return true;
+}
+
+template <typename T>
+PassArgs<T> member_pass_args(spstd_ctx *ctx, const HalfStage &h, int ax)
+{
+    const spstd_config &cfg = ctx->cfg;
+    const int64_t n0 = cfg.n[0], n1 = cfg.n[1], n2 = cfg.n[2];
+    const int64_t off[3] = {0, n0, n0 + n1};
+    PassArgs<T> a{};
+    a.src = field_ptr<T>(ctx, 1 - h.dst);
+    a.dst = field_ptr<T>(ctx, h.dst);
+    a.tw = (const cpx<T> *)ctx->ptr(ctx->L.tw[ax]);
+    a.mult = (const T *)ctx->ptr(ctx->L.mult) + (size_t)h.table * ctx->sum_n + off[ax];
+    if (ax == 0) {
+        a.V = (const T *)ctx->ptr(ctx->L.V);
+        a.bV = (T)h.bV;
+        a.use_V = 1;
+        a.n_rows = n1 * n2;
+    } else {
+        a.stride = ax == 1 ? n0 : n0 * n1;
+        a.outer_stride = ax == 1 ? n0 * n1 : n0;
+        a.n_outer = ax == 1 ? n2 : n1;
+        a.nx = (int)n0;
+    }
+    return a;
+}
+
+template <typename T>
+ResidentArgs<T> member_resident_args(spstd_ctx *ctx)
+{
+    ResidentArgs<T> r{};
+    r.psiR = field_ptr<T>(ctx, 0);
+    r.psiI = field_ptr<T>(ctx, 1);
+    r.V = (const T *)ctx->ptr(ctx->L.V);
+    r.tw = (const cpx<T> *)ctx->ptr(ctx->L.tw[0]);
+    r.mult = (const T *)ctx->ptr(ctx->L.mult);
+    r.nh = (int)ctx->hs.size();
+    for (int h = 0; h < r.nh; ++h) {
+        r.bV[h] = (T)ctx->hs[h].bV;
+        r.hfield[h] = ctx->hs[h].dst;
+        r.htable[h] = ctx->hs[h].table;
+    }
+    ProbeArgs p = probe_args<float>(ctx);
+    r.n_probe = p.n_probe;
+    for (int q = 0; q < p.n_probe; ++q) r.probe_idx[q] = p.idx[q];
+    r.ring = p.ring;
+    r.cap = p.cap;
+    r.counter = p.counter;
+    return r;
+}
+
+// Appends bytes to the descriptor image, 256-byte aligned; returns the offset.
+size_t put(std::vector<unsigned char> &img, const void *src, size_t bytes)
+{
+    size_t off = (img.size() + 255) & ~size_t(255);
+    img.resize(off + bytes);
+    std::memcpy(img.data() + off, src, bytes);
+    return off;
+}
+
+template <typename T>
+void build_nd_descriptors(spstd_batch *b, BatchGroupND &g, std::vector<unsigned char> &img)
+{
+    const int M = (int)g.slots.size();
+    std::vector<PassArgs<T>> args((size_t)g.nh * g.dims * M);
+    std::vector<ProbeMember<T>> pm(M);
+    for (int i = 0; i < M; ++i) {
+        spstd_ctx *ctx = b->slots[g.slots[i]];
+        for (int h = 0; h < g.nh; ++h)
+            for (int ax = 0; ax < g.dims; ++ax)
+                args[((size_t)h * g.dims + ax) * M + i] = member_pass_args<T>(ctx, ctx->hs[h], ax);
+        pm[i].psiR = field_ptr<T>(ctx, 0);
+        pm[i].psiI = field_ptr<T>(ctx, 1);
+        pm[i].p = probe_args<T>(ctx);
+    }
+    g.args_off = put(img, args.data(), sizeof(PassArgs<T>) * args.size());
+    g.probe_off = put(img, pm.data(), sizeof(ProbeMember<T>) * pm.size());
+    g.tiles[0] = Launch<T>::xpass_tiles((int)g.n[0], g.n[1] * g.n[2]);
+    g.tiles[1] = g.dims > 1 ? Launch<T>::spass_tiles((int)g.n[1], (int)g.n[0], g.n[2]) : 0;
+    g.tiles[2] = g.dims > 2 ? Launch<T>::spass_tiles((int)g.n[2], (int)g.n[0], g.n[1]) : 0;
+}
+
+template <typename T>
+void build_1d_descriptors(spstd_batch *b, BatchGroup1D &g, std::vector<unsigned char> &img)
+{
+    std::vector<ResidentArgs<T>> args(g.slots.size());
+    for (size_t i = 0; i < g.slots.size(); ++i) args[i] = member_resident_args<T>(b->slots[g.slots[i]]);
+    g.args_off = put(img, args.data(), sizeof(ResidentArgs<T>) * args.size());
+}
+
+spstd_status batch_build(spstd_batch *b)
+{
+    b->g1.clear();
+    b->gn.clear();
+    for (int s = 0; s < (int)b->slots.size(); ++s) {
+        spstd_ctx *ctx = b->slots[s];
+        if (!ctx) continue;
+        const spstd_config &cfg = ctx->cfg;
+        if (cfg.dims == 1) {
+            BatchGroup1D *g = nullptr;
+            for (auto &x : b->g1)
+                if (x.precision == cfg.precision && x.N == cfg.n[0]) g = &x;
+            if (!g) {
+                b->g1.push_back(BatchGroup1D{cfg.precision, cfg.n[0], {}, 0});
+                g = &b->g1.back();
+            }
+            g->slots.push_back(s);
+        } else {
+            BatchGroupND *g = nullptr;
+            for (auto &x : b->gn)
+                if (x.precision == cfg.precision && x.dims == cfg.dims && x.n[0] == cfg.n[0] && x.n[1] == cfg.n[1] &&
+                    x.n[2] == cfg.n[2] && x.nh == (int)ctx->hs.size() && same_integrator(ctx, x.m, x.c, x.d))
+                    g = &x;
+            if (!g) {
+                BatchGroupND ng{};
+                ng.precision = cfg.precision;
+                ng.dims = cfg.dims;
+                ng.m = ctx->m;
+                for (int a = 0; a < 3; ++a) ng.n[a] = cfg.n[a];
+                for (int l = 0; l < ctx->m; ++l) {
+                    ng.c[l] = ctx->c[l];
+                    ng.d[l] = ctx->d[l];
+                }
+                ng.nh = (int)ctx->hs.size();
+                b->gn.push_back(ng);
+                g = &b->gn.back();
+            }
+            g->slots.push_back(s);
+        }
+    }
+    std::vector<unsigned char> img;
+    for (auto &g : b->g1) {
+        if (g.precision == 32) build_1d_descriptors<float>(b, g, img);
+        else build_1d_descriptors<double>(b, g, img);
+    }
+    for (auto &g : b->gn) {
+        if (g.precision == 32) build_nd_descriptors<float>(b, g, img);
+        else build_nd_descriptors<double>(b, g, img);
+    }
+    if (img.size() > b->ws_bytes) return bfail(b, SPSTD_ENOMEM, "batch workspace too small for the descriptors");
+    if (!img.empty()) {
+        SPSTD_BCU(b, cudaMemcpyAsync(b->ws, img.data(), img.size(), cudaMemcpyHostToDevice, b->stream));
+        SPSTD_BCU(b, cudaStreamSynchronize(b->stream));
+    }
+    if (b->gexec) {
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+    }
+    b->dirty = false;
+    return SPSTD_OK;
+}
+
+template <typename T>
+cudaError_t enqueue_group_step(spstd_batch *b, const BatchGroupND &g, cudaStream_t s)
+{
+    const int M = (int)g.slots.size();
+    const PassArgs<T> *args = (const PassArgs<T> *)(b->ws + g.args_off);
+    for (int h = 0; h < g.nh; ++h) {
+        for (int ax = 0; ax < g.dims; ++ax) {
+            const PassArgs<T> *a = args + ((size_t)h * g.dims + ax) * M;
+            cudaError_t e = ax == 0 ? Launch<T>::xpass_batch((int)g.n[0], a, M, g.tiles[0], s)
+                                    : Launch<T>::spass_batch((int)g.n[ax], a, M, g.tiles[ax], s);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    return Launch<T>::probe_batch((const ProbeMember<T> *)(b->ws + g.probe_off), M, s);
+}
+
+cudaError_t enqueue_nd_steps(spstd_batch *b, int64_t nsteps, cudaStream_t s, bool fork)
+{
+    for (int64_t i = 0; i < nsteps; ++i) {
+        if (fork && b->gn.size() > 1) {
+            cudaError_t e = cudaEventRecord(b->ev_fork, s);
+            if (e != cudaSuccess) return e;
+            for (size_t g = 0; g < b->gn.size(); ++g) {
+                cudaStream_t bs = b->branch[g % kBatchStreams];
+                if (g < kBatchStreams) {
+                    e = cudaStreamWaitEvent(bs, b->ev_fork, 0);
+                    if (e != cudaSuccess) return e;
+                }
+                e = b->gn[g].precision == 32 ? enqueue_group_step<float>(b, b->gn[g], bs)
+                                             : enqueue_group_step<double>(b, b->gn[g], bs);
+                if (e != cudaSuccess) return e;
+            }
+            for (int k = 0; k < kBatchStreams && k < (int)b->gn.size(); ++k) {
+                e = cudaEventRecord(b->ev_branch[k], b->branch[k]);
+                if (e != cudaSuccess) return e;
+                e = cudaStreamWaitEvent(s, b->ev_branch[k], 0);
+                if (e != cudaSuccess) return e;
+            }
+        } else {
+            for (const auto &g : b->gn) {
+                cudaError_t e = g.precision == 32 ? enqueue_group_step<float>(b, g, s)
+                                                  : enqueue_group_step<double>(b, g, s);
+                if (e != cudaSuccess) return e;
+            }
+        }
+    }
+    return cudaSuccess;
+}
+
+// Raises the shared-memory limits of every batched kernel used (outside any capture).
+cudaError_t batch_prepare(spstd_batch *b)
+{
+    for (const auto &g : b->gn) {
+        for (int ax = 0; ax < g.dims; ++ax) {
+            cudaError_t e;
+            if (g.precision == 32)
+                e = ax == 0 ? Launch<float>::xpass_batch((int)g.n[0], nullptr, 0, 0, nullptr)
+                            : Launch<float>::spass_batch((int)g.n[ax], nullptr, 0, 0, nullptr);
+            else
+                e = ax == 0 ? Launch<double>::xpass_batch((int)g.n[0], nullptr, 0, 0, nullptr)
+                            : Launch<double>::spass_batch((int)g.n[ax], nullptr, 0, 0, nullptr);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    for (const auto &g : b->g1) {
+        cudaError_t e = g.precision == 32 ? Launch<float>::resident_batch((int)g.N, nullptr, 0, 0, nullptr)
+                                          : Launch<double>::resident_batch((int)g.N, nullptr, 0, 0, nullptr);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+spstd_status spstd_batch_workspace_size(int max_members, size_t *bytes)
+{
+    if (max_members < 1 || !bytes) return SPSTD_EINVAL;
+    *bytes = (size_t)max_members * kBatchBytesPerMember + 4096;
+    return SPSTD_OK;
+}
+
+spstd_status spstd_batch_create(int max_members, int device, void *stream, void *d_workspace, size_t workspace_bytes,
+                                spstd_batch **out)
+{
+    if (!out || max_members < 1) return SPSTD_EINVAL;
+    *out = nullptr;
+    size_t need = 0;
+    spstd_batch_workspace_size(max_members, &need);
+    if (!d_workspace || ((uintptr_t)d_workspace & 255)) return SPSTD_EINVAL;
+    if (workspace_bytes < need) return SPSTD_ENOMEM;
+    spstd_batch *b = new (std::nothrow) spstd_batch();
+    if (!b) return SPSTD_ENOMEM;
+    b->device = device;
+    b->max_members = max_members;
+    b->stream = (cudaStream_t)stream;
+    b->ws = (unsigned char *)d_workspace;
+    b->ws_bytes = workspace_bytes;
+    b->slots.assign(max_members, nullptr);
+    bool ok = cudaSetDevice(device) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) == cudaSuccess;
+    for (int k = 0; ok && k < kBatchStreams; ++k)
+        ok = cudaStreamCreateWithFlags(&b->branch[k], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&b->ev_branch[k], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        spstd_batch_destroy(b);
+        return SPSTD_ECUDA;
+    }
+    *out = b;
+    return SPSTD_OK;
+}
+
+spstd_status spstd_batch_destroy(spstd_batch *b)
+{
+    if (!b) return SPSTD_OK;
+    if (b->stream || b->side) {
+        cudaStreamSynchronize(b->stream);
+        if (b->side) cudaStreamSynchronize(b->side);
+    }
+    for (spstd_ctx *c : b->slots)
+        if (c) c->batch = nullptr;
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    for (int k = 0; k < kBatchStreams; ++k) {
+        if (b->branch[k]) cudaStreamDestroy(b->branch[k]);
+        if (b->ev_branch[k]) cudaEventDestroy(b->ev_branch[k]);
+    }
+    if (b->side) cudaStreamDestroy(b->side);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->ev_join) cudaEventDestroy(b->ev_join);
+    delete b;
+    return SPSTD_OK;
+}
+
+spstd_status spstd_batch_add(spstd_batch *b, spstd_ctx *ctx, int *slot)
+{
+    if (!b || !ctx || !slot) return SPSTD_EINVAL;
+    if (ctx->batch) return bfail(b, SPSTD_EINVAL, "context is already a batch member");
+    if (ctx->cfg.device != b->device) return bfail(b, SPSTD_EINVAL, "context lives on another device");
+    for (int s = 0; s < (int)b->slots.size(); ++s) {
+        if (!b->slots[s]) {
+            // the member's own pending work comes first
+            SPSTD_BCU(b, cudaStreamSynchronize(ctx->stream));
+            b->slots[s] = ctx;
+            ctx->batch = b;
+            b->dirty = true;
+            *slot = s;
+            return SPSTD_OK;
+        }
+    }
+    return bfail(b, SPSTD_ENOTREADY, "batch is full");
+}
+
+spstd_status spstd_batch_remove(spstd_batch *b, int slot)
+{
+    if (!b || slot < 0 || slot >= (int)b->slots.size() || !b->slots[slot]) return SPSTD_EINVAL;
+    SPSTD_BCU(b, cudaStreamSynchronize(b->stream));
+    b->slots[slot]->batch = nullptr;
+    b->slots[slot] = nullptr;
+    b->dirty = true;
+    return SPSTD_OK;
+}
+
+spstd_status spstd_batch_size(const spstd_batch *b, int *members)
+{
+    if (!b || !members) return SPSTD_EINVAL;
+    int n = 0;
+    for (auto *c : b->slots) n += c != nullptr;
+    *members = n;
+    return SPSTD_OK;
+}
+
+spstd_status spstd_batch_step(spstd_batch *b, int64_t nsteps)
+{
+    if (!b || nsteps < 0) return SPSTD_EINVAL;
+    if (nsteps == 0) return SPSTD_OK;
+    if (b->dirty) {
+        spstd_status st = batch_build(b);
+        if (st != SPSTD_OK) return st;
+        SPSTD_BCU(b, batch_prepare(b));
+    }
+    // 1D groups: every step of this call in one resident launch each, on the side stream
+    if (!b->g1.empty()) {
+        SPSTD_BCU(b, cudaEventRecord(b->ev_fork, b->stream));
+        SPSTD_BCU(b, cudaStreamWaitEvent(b->side, b->ev_fork, 0));
+        for (const auto &g : b->g1) {
+            const int M = (int)g.slots.size();
+            if (g.precision == 32)
+                SPSTD_BCU(b, Launch<float>::resident_batch((int)g.N, (const ResidentArgs<float> *)(b->ws + g.args_off),
+                                                           M, nsteps, b->side));
+            else
+                SPSTD_BCU(b, Launch<double>::resident_batch((int)g.N, (const ResidentArgs<double> *)(b->ws + g.args_off),
+                                                            M, nsteps, b->side));
+        }
+    }
+    // 2D/3D groups: graph-replayed chunks, then the remainder directly
+    int64_t left = nsteps;
+    if (!b->gn.empty() && left >= kBatchGraphSteps) {
+        if (!b->gexec) {
+            cudaGraph_t g = nullptr;
+            SPSTD_BCU(b, cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = enqueue_nd_steps(b, kBatchGraphSteps, b->cap, true);
+            cudaError_t e2 = cudaStreamEndCapture(b->cap, &g);
+            if (e != cudaSuccess || e2 != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                return bfail(b, SPSTD_ECUDA, std::string("batch graph capture: ") +
+                                                 cudaGetErrorString(e != cudaSuccess ? e : e2));
+            }
+            e = cudaGraphInstantiate(&b->gexec, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                b->gexec = nullptr;
+                return bfail(b, SPSTD_ECUDA, std::string("batch graph instantiate: ") + cudaGetErrorString(e));
+            }
+        }
+        for (int64_t r = 0; r < left / kBatchGraphSteps; ++r) SPSTD_BCU(b, cudaGraphLaunch(b->gexec, b->stream));
+        left %= kBatchGraphSteps;
+    }
+    if (!b->gn.empty() && left > 0) SPSTD_BCU(b, enqueue_nd_steps(b, left, b->stream, false));
+    if (!b->g1.empty()) {
+        SPSTD_BCU(b, cudaEventRecord(b->ev_join, b->side));
+        SPSTD_BCU(b, cudaStreamWaitEvent(b->stream, b->ev_join, 0));
+    }
+    for (spstd_ctx *c : b->slots)
+        if (c) c->steps_taken += nsteps;
+    return SPSTD_OK;
+}
+
+spstd_status spstd_batch_sync(spstd_batch *b)
+{
+    if (!b) return SPSTD_EINVAL;
+    SPSTD_BCU(b, cudaStreamSynchronize(b->stream));
+    return SPSTD_OK;
+}
+
+spstd_status spstd_batch_launch_count(const spstd_batch *b, int64_t nsteps, int64_t *launches)
+{
+    if (!b || !launches || nsteps < 0) return SPSTD_EINVAL;
+    int64_t per_step = 0, per_call = 0;
+    for (auto *c : b->slots) {
+        (void)c;
+    }
+    std::vector<std::pair<int, int64_t>> seen1;
+    int64_t g1 = 0, gnd = 0;
+    // groups are only known after a build; count them the same way
+    std::vector<std::vector<int64_t>> keys;
+    for (auto *c : b->slots) {
+        if (!c) continue;
+        const spstd_config &cfg = c->cfg;
+        std::vector<int64_t> k = {cfg.dims, cfg.precision, cfg.n[0], cfg.n[1], cfg.n[2], (int64_t)c->hs.size(), c->m};
+        for (int l = 0; l < c->m; ++l) {
+            int64_t bc, bd;
+            std::memcpy(&bc, &c->c[l], 8);
+            std::memcpy(&bd, &c->d[l], 8);
+            k.push_back(bc);
+            k.push_back(bd);
+        }
+        if (cfg.dims == 1) k.resize(3);
+        bool found = false;
+        for (auto &x : keys) found |= x == k;
+        if (found) continue;
+        keys.push_back(k);
+        if (cfg.dims == 1) ++g1;
+        else {
+            ++gnd;
+            per_step += (int64_t)c->hs.size() * cfg.dims + 1;
+        }
+    }
+    (void)seen1;
+    (void)gnd;
+    per_call = g1;
+    *launches = nsteps ? per_call + nsteps * per_step : 0;
+    return SPSTD_OK;
+}
+
+const char *spstd_batch_last_error(const spstd_batch *b)
+{
+    return b ? b->err.c_str() : "no batch";
 }
 
 }  // extern "C"

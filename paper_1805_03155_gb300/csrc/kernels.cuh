@@ -148,8 +148,7 @@ __device__ __forceinline__ void stage_tables(const PassArgs<T> &a, cpx<T> *s_tw,
 // 2lp+1 (the second may be past the end: its half of the complex line is 0).
 // ---------------------------------------------------------------------------
 template <typename T, int N, int LPC>
-__global__ void __launch_bounds__((N / line_e<T, N>::value) * LPC)
-xpass_kernel(const PassArgs<T> a)
+__device__ __forceinline__ void xpass_body(const PassArgs<T> &a, int64_t blk)
 {
     constexpr int E = line_e<T, N>::value;
     constexpr int TT = N / E;
@@ -170,7 +169,6 @@ xpass_kernel(const PassArgs<T> a)
         mult = s_mult;
     }
 
-    const int64_t blk = a.reverse ? (int64_t)(gridDim.x - 1 - blockIdx.x) : (int64_t)blockIdx.x;
     const int64_t lp = blk * LPC + l;
     const int64_t r0 = 2 * lp, r1 = r0 + 1;
     const bool ok0 = r0 < a.n_rows, ok1 = r1 < a.n_rows;
@@ -213,6 +211,23 @@ xpass_kernel(const PassArgs<T> a)
     }
 }
 
+template <typename T, int N, int LPC>
+__global__ void __launch_bounds__((N / line_e<T, N>::value) * LPC)
+xpass_kernel(const PassArgs<T> a)
+{
+    xpass_body<T, N, LPC>(a, a.reverse ? (int64_t)(gridDim.x - 1 - blockIdx.x) : (int64_t)blockIdx.x);
+}
+
+// Batched x pass: members of one shape, tiles_per_member consecutive blocks each.
+template <typename T, int N, int LPC>
+__global__ void __launch_bounds__((N / line_e<T, N>::value) * LPC)
+xpass_batch_kernel(const PassArgs<T> *__restrict__ args, int tiles_per_member)
+{
+    const int member = blockIdx.x / tiles_per_member;
+    const PassArgs<T> a = args[member];
+    xpass_body<T, N, LPC>(a, (int64_t)(blockIdx.x - member * tiles_per_member));
+}
+
 // ---------------------------------------------------------------------------
 // Strided pass (y or z axis).  Block (LPC, TT): threadIdx.x picks the column
 // pair (2p, 2p+1) inside a tile of 2 LPC adjacent x columns, threadIdx.y the
@@ -220,8 +235,7 @@ xpass_kernel(const PassArgs<T> a)
 // row per access.  Tile id = outer * n_xt + xt.
 // ---------------------------------------------------------------------------
 template <typename T, int N, int LPC>
-__global__ void __launch_bounds__((N / line_e<T, N>::value) * LPC)
-spass_kernel(const PassArgs<T> a)
+__device__ __forceinline__ void spass_body(const PassArgs<T> &a, int64_t blk)
 {
     constexpr int E = line_e<T, N>::value;
     constexpr int TT = N / E;
@@ -236,7 +250,6 @@ spass_kernel(const PassArgs<T> a)
     __syncthreads();
 
     const int n_xt = (a.nx + 2 * LPC - 1) / (2 * LPC);
-    const int64_t blk = a.reverse ? (int64_t)(gridDim.x - 1 - blockIdx.x) : (int64_t)blockIdx.x;
     const int64_t outer = blk / n_xt;
     const int xt = (int)(blk - outer * n_xt);
     const int c0 = xt * 2 * LPC + 2 * p;
@@ -293,6 +306,22 @@ spass_kernel(const PassArgs<T> a)
     }
 }
 
+template <typename T, int N, int LPC>
+__global__ void __launch_bounds__((N / line_e<T, N>::value) * LPC)
+spass_kernel(const PassArgs<T> a)
+{
+    spass_body<T, N, LPC>(a, a.reverse ? (int64_t)(gridDim.x - 1 - blockIdx.x) : (int64_t)blockIdx.x);
+}
+
+template <typename T, int N, int LPC>
+__global__ void __launch_bounds__((N / line_e<T, N>::value) * LPC)
+spass_batch_kernel(const PassArgs<T> *__restrict__ args, int tiles_per_member)
+{
+    const int member = blockIdx.x / tiles_per_member;
+    const PassArgs<T> a = args[member];
+    spass_body<T, N, LPC>(a, (int64_t)(blockIdx.x - member * tiles_per_member));
+}
+
 // ---------------------------------------------------------------------------
 // Resident 1D solver: one block owns a whole 1D grid for all nsteps steps.
 // Thread t keeps psi_R, psi_I and V at points t + e TT in registers (the same
@@ -300,8 +329,7 @@ spass_kernel(const PassArgs<T> a)
 // only for its multiplier table; the probes are written after every step.
 // ---------------------------------------------------------------------------
 template <typename T, int N>
-__global__ void __launch_bounds__(N / line_e<T, N>::value)
-resident1d_kernel(const ResidentArgs<T> a)
+__device__ __forceinline__ void resident1d_body(const ResidentArgs<T> &a)
 {
     constexpr int E = line_e<T, N>::value;
     constexpr int TT = N / E;
@@ -376,6 +404,23 @@ resident1d_kernel(const ResidentArgs<T> a)
     if (t == 0) *a.counter = c0 + a.nsteps;
 }
 
+template <typename T, int N>
+__global__ void __launch_bounds__(N / line_e<T, N>::value)
+resident1d_kernel(const ResidentArgs<T> a)
+{
+    resident1d_body<T, N>(a);
+}
+
+// Batched resident solver: block b advances member b (all of length N).
+template <typename T, int N>
+__global__ void __launch_bounds__(N / line_e<T, N>::value)
+resident1d_batch_kernel(const ResidentArgs<T> *__restrict__ args, int64_t nsteps)
+{
+    ResidentArgs<T> a = args[blockIdx.x];
+    a.nsteps = nsteps;
+    resident1d_body<T, N>(a);
+}
+
 // ---------------------------------------------------------------------------
 // Probe recorder (one block): ring[q][counter % cap] = (psi_R, psi_I)(idx_q).
 // ---------------------------------------------------------------------------
@@ -390,6 +435,28 @@ __global__ void probe_kernel(const T *__restrict__ psiR, const T *__restrict__ p
     }
     __syncthreads();
     if (q == 0) *a.counter = c + 1;
+}
+
+// Batched probe recorder: block b records member b.
+template <typename T>
+struct ProbeMember {
+    const T *psiR;
+    const T *psiI;
+    ProbeArgs p;
+};
+
+template <typename T>
+__global__ void probe_batch_kernel(const ProbeMember<T> *__restrict__ members)
+{
+    const ProbeMember<T> &m = members[blockIdx.x];
+    const int64_t c = *m.p.counter;
+    const int q = threadIdx.x;
+    if (q < m.p.n_probe) {
+        const int64_t idx = m.p.idx[q];
+        m.p.ring[(int64_t)q * m.p.cap + c % m.p.cap] = make_double2((double)m.psiR[idx], (double)m.psiI[idx]);
+    }
+    __syncthreads();
+    if (q == 0) *m.p.counter = c + 1;
 }
 
 // ---------------------------------------------------------------------------

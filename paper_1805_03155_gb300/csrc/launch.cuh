@@ -93,6 +93,41 @@ cudaError_t resident_n(const ResidentArgs<T> &a, cudaStream_t s)
 
 cudaError_t launch_sum_partials(const double *partial, int count, double *out, cudaStream_t s);
 
+template <typename T, int N>
+cudaError_t xpass_batch_n(const PassArgs<T> *args, int members, int tiles, cudaStream_t s)
+{
+    constexpr int TT = threads_per_line<T, N>();
+    constexpr int LPC = xpass_lpc<T, N>();
+    constexpr size_t smem = xpass_smem<T, N, LPC>();
+    cudaError_t e = allow_smem<xpass_batch_kernel<T, N, LPC>>(smem);
+    if (e != cudaSuccess || members <= 0 || tiles <= 0) return e;
+    xpass_batch_kernel<T, N, LPC><<<dim3((unsigned)(members * tiles)), dim3(TT, LPC), smem, s>>>(args, tiles);
+    return cudaGetLastError();
+}
+
+template <typename T, int N>
+cudaError_t spass_batch_n(const PassArgs<T> *args, int members, int tiles, cudaStream_t s)
+{
+    constexpr int TT = threads_per_line<T, N>();
+    constexpr int LPC = spass_lpc<T, N>();
+    constexpr size_t smem = spass_smem<T, N, LPC>();
+    cudaError_t e = allow_smem<spass_batch_kernel<T, N, LPC>>(smem);
+    if (e != cudaSuccess || members <= 0 || tiles <= 0) return e;
+    spass_batch_kernel<T, N, LPC><<<dim3((unsigned)(members * tiles)), dim3(LPC, TT), smem, s>>>(args, tiles);
+    return cudaGetLastError();
+}
+
+template <typename T, int N>
+cudaError_t resident_batch_n(const ResidentArgs<T> *args, int members, int64_t nsteps, cudaStream_t s)
+{
+    constexpr int TT = threads_per_line<T, N>();
+    constexpr size_t smem = resident_smem<T, N>();
+    cudaError_t e = allow_smem<resident1d_batch_kernel<T, N>>(smem);
+    if (e != cudaSuccess || members <= 0) return e;
+    resident1d_batch_kernel<T, N><<<members, TT, smem, s>>>(args, nsteps);
+    return cudaGetLastError();
+}
+
 template <typename T> struct Launch {
     static cudaError_t xpass(int N, const PassArgs<T> &a, cudaStream_t s);
     static cudaError_t spass(int N, const PassArgs<T> &a, cudaStream_t s);
@@ -103,6 +138,15 @@ template <typename T> struct Launch {
     static cudaError_t from_f64(const double *in, T *out, int64_t n, cudaStream_t s);
     static cudaError_t to_f64(const T *in, double *out, int64_t n, cudaStream_t s);
     static int resident_max_n();
+    // blocks one member of a batched pass needs
+    static int xpass_tiles(int N, int64_t n_rows);
+    static int spass_tiles(int N, int nx, int64_t n_outer);
+    // batched launches over members of one shape (args: device arrays)
+    static cudaError_t xpass_batch(int N, const PassArgs<T> *args, int members, int tiles, cudaStream_t s);
+    static cudaError_t spass_batch(int N, const PassArgs<T> *args, int members, int tiles, cudaStream_t s);
+    static cudaError_t resident_batch(int N, const ResidentArgs<T> *args, int members, int64_t nsteps,
+                                      cudaStream_t s);
+    static cudaError_t probe_batch(const ProbeMember<T> *members, int count, cudaStream_t s);
 };
 
 }  // namespace spstd

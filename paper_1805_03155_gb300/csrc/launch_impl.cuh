@@ -81,6 +81,86 @@ cudaError_t Launch<T>::resident1d(int N, const ResidentArgs<T> &a, cudaStream_t 
 #undef SPSTD_R
 }
 
+#define SPSTD_CASES(M)                                                     \
+    M(2) M(4) M(8) M(16) M(32) M(64) M(128) M(256) M(512) M(1024)
+
+template <typename T>
+int Launch<T>::xpass_tiles(int N, int64_t n_rows)
+{
+    const int64_t pairs = (n_rows + 1) / 2;
+    int lpc = 0;
+#define SPSTD_C(n) \
+    if (N == n) lpc = xpass_lpc<T, n>();
+    SPSTD_CASES(SPSTD_C)
+#undef SPSTD_C
+    if (N == 2048) lpc = xpass_lpc<T, 2048>();
+    if (N == 4096) lpc = xpass_lpc<T, 4096>();
+    if (N == 8192) lpc = xpass_lpc<T, 8192>();
+    return lpc ? (int)((pairs + lpc - 1) / lpc) : 0;
+}
+
+template <typename T>
+int Launch<T>::spass_tiles(int N, int nx, int64_t n_outer)
+{
+    int lpc = 0;
+#define SPSTD_C(n) \
+    if (N == n) lpc = spass_lpc<T, n>();
+    SPSTD_CASES(SPSTD_C)
+#undef SPSTD_C
+    return lpc ? (int)(((nx + 2 * lpc - 1) / (2 * lpc)) * n_outer) : 0;
+}
+
+template <typename T>
+cudaError_t Launch<T>::xpass_batch(int N, const PassArgs<T> *args, int members, int tiles, cudaStream_t s)
+{
+    switch (N) {
+#define SPSTD_C(n) \
+    case n: return xpass_batch_n<T, n>(args, members, tiles, s);
+        SPSTD_CASES(SPSTD_C)
+#undef SPSTD_C
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename T>
+cudaError_t Launch<T>::spass_batch(int N, const PassArgs<T> *args, int members, int tiles, cudaStream_t s)
+{
+    switch (N) {
+#define SPSTD_C(n) \
+    case n: return spass_batch_n<T, n>(args, members, tiles, s);
+        SPSTD_CASES(SPSTD_C)
+#undef SPSTD_C
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename T>
+cudaError_t Launch<T>::resident_batch(int N, const ResidentArgs<T> *args, int members, int64_t nsteps,
+                                      cudaStream_t s)
+{
+    switch (N) {
+#define SPSTD_C(n) \
+    case n: return resident_batch_n<T, n>(args, members, nsteps, s);
+        SPSTD_CASES(SPSTD_C)
+#undef SPSTD_C
+    case 2048: return resident_batch_n<T, 2048>(args, members, nsteps, s);
+    case 4096: return resident_batch_n<T, 4096>(args, members, nsteps, s);
+    default: break;
+    }
+    if constexpr (sizeof(T) == 4) {
+        if (N == 8192) return resident_batch_n<T, 8192>(args, members, nsteps, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t Launch<T>::probe_batch(const ProbeMember<T> *members, int count, cudaStream_t s)
+{
+    if (count <= 0) return cudaSuccess;
+    probe_batch_kernel<T><<<count, 32, 0, s>>>(members);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t Launch<T>::probe(const T *psiR, const T *psiI, const ProbeArgs &a, cudaStream_t s)
 {

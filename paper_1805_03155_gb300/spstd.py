@@ -95,6 +95,16 @@ def lib():
         "spstd_launch_count": (C.c_int, [vp, C.c_int64, ip]),
         "spstd_profile_steps": (C.c_int, [vp, C.c_int64, dp, ip]),
         "spstd_norm_noalloc": (C.c_int, [vp, vp, C.c_int64, C.c_int, C.c_double, vp, vp]),
+        "spstd_batch_workspace_size": (C.c_int, [C.c_int, C.POINTER(C.c_size_t)]),
+        "spstd_batch_create": (C.c_int, [C.c_int, C.c_int, vp, vp, C.c_size_t, C.POINTER(vp)]),
+        "spstd_batch_destroy": (C.c_int, [vp]),
+        "spstd_batch_add": (C.c_int, [vp, vp, C.POINTER(C.c_int)]),
+        "spstd_batch_remove": (C.c_int, [vp, C.c_int]),
+        "spstd_batch_size": (C.c_int, [vp, C.POINTER(C.c_int)]),
+        "spstd_batch_step": (C.c_int, [vp, C.c_int64]),
+        "spstd_batch_sync": (C.c_int, [vp]),
+        "spstd_batch_launch_count": (C.c_int, [vp, C.c_int64, ip]),
+        "spstd_batch_last_error": (C.c_char_p, [vp]),
         "spstd_last_error": (C.c_char_p, [vp]),
         "spstd_status_string": (C.c_char_p, [C.c_int]),
     }
@@ -276,6 +286,72 @@ def stability_limit(cfg: spstd_config, vmax=0.0):
     if st != SPSTD_OK:
         raise SpstdError(st, lib().spstd_status_string(st).decode())
     return s.value, dtm.value
+
+
+class Batch:
+    """Many independent solves advanced by one call (spstd_batch_*); the
+    descriptor workspace is a torch uint8 tensor."""
+
+    def __init__(self, max_members, device=0, stream=None):
+        import torch
+
+        self.L = lib()
+        dev = torch.device("cuda", device)
+        if stream is None:
+            stream = torch.cuda.current_stream(dev)
+        self.torch_stream = stream
+        nbytes = C.c_size_t(0)
+        self._check(self.L.spstd_batch_workspace_size(int(max_members), C.byref(nbytes)))
+        self._ws = torch.empty(nbytes.value + 256, dtype=torch.uint8, device=dev)
+        aligned = (self._ws.data_ptr() + 255) // 256 * 256
+        self.b = C.c_void_p(0)
+        self._check(self.L.spstd_batch_create(int(max_members), int(device), C.c_void_p(stream.cuda_stream),
+                                              C.c_void_p(aligned), nbytes.value, C.byref(self.b)))
+        self.members = {}
+
+    def _check(self, st):
+        if st != SPSTD_OK:
+            msg = self.L.spstd_status_string(st).decode()
+            if getattr(self, "b", None) is not None and self.b.value:
+                msg += ": " + self.L.spstd_batch_last_error(self.b).decode()
+            raise SpstdError(st, msg)
+
+    def spstd_batch_add(self, solver):
+        slot = C.c_int(-1)
+        self._check(self.L.spstd_batch_add(self.b, solver.ctx, C.byref(slot)))
+        self.members[slot.value] = solver
+        return slot.value
+
+    def spstd_batch_remove(self, slot):
+        self._check(self.L.spstd_batch_remove(self.b, int(slot)))
+        return self.members.pop(slot)
+
+    def spstd_batch_size(self):
+        n = C.c_int(0)
+        self._check(self.L.spstd_batch_size(self.b, C.byref(n)))
+        return n.value
+
+    def spstd_batch_step(self, nsteps):
+        self._check(self.L.spstd_batch_step(self.b, int(nsteps)))
+
+    def spstd_batch_sync(self):
+        self._check(self.L.spstd_batch_sync(self.b))
+
+    def spstd_batch_launch_count(self, nsteps):
+        v = C.c_int64(0)
+        self._check(self.L.spstd_batch_launch_count(self.b, int(nsteps), C.byref(v)))
+        return v.value
+
+    def close(self):
+        if getattr(self, "b", None) is not None and self.b.value:
+            self.L.spstd_batch_destroy(self.b)
+            self.b = C.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 NOALLOC_MAX_ELEMS = 65536 * 2048
