@@ -163,6 +163,127 @@ def cpu_baseline(problem, budget_s=20.0):
                       f"{t:.2f} s each, scaled by {h} half-stages per step; single thread, FP64"}
 
 
+def batched_vs_plain(count=512, steps=20, precision=32, local=0):
+    """The mixed 512-solve workload (1D wells 128..8192, 2D oscillators
+    64^2..512^2, 3D oscillators 32^3 and 64^3; FP32 fields, FP64 reductions,
+    FR4): `steps` steps of every member through one batch (graph-replayed
+    chunks, 1D members resident) vs the same members stepped one after another
+    with spstd_step on one stream (plain).  Device-resident inputs; CUDA-event
+    time on the batch stream; solves/s is extrapolated to 5000-step solves."""
+    import torch
+    from paper_1805_03155_gb300 import inputs, spstd
+
+    probs = inputs.batch_mix(count, steps=steps)
+    stream = torch.cuda.current_stream(local)
+    solvers = [spstd.solver_for(p, precision=precision, probe_capacity=4 * steps + 8, stream=stream,
+                                device=local) for p in probs]
+    pts = sum(p.n_total for p in probs)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    # plain: one member after another (warm-up captures each member's graph)
+    for s in solvers:
+        s.spstd_step(steps)
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for s in solvers:
+        s.spstd_step(steps)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    plain_ms = ev[0].elapsed_time(ev[1])
+    plain_launches = sum(s.spstd_launch_count(steps) for s in solvers)
+    # batched
+    b = spstd.Batch(count + 1, device=local, stream=stream)
+    for s in solvers:
+        b.spstd_batch_add(s)
+    b.spstd_batch_step(steps)
+    torch.cuda.synchronize()
+    ev[2].record(stream)
+    b.spstd_batch_step(steps)
+    ev[3].record(stream)
+    torch.cuda.synchronize()
+    batch_ms = ev[2].elapsed_time(ev[3])
+    launches = b.spstd_batch_launch_count(steps)
+    norms = [s.spstd_energy_norm()[0] for s in solvers[:: max(1, count // 16)]]
+    b.close()
+    for s in solvers:
+        s.close()
+    return {
+        "workload": f"batch_mix_{count}",
+        "members": count,
+        "grid_points": pts,
+        "steps": steps,
+        "batched": {"value": pts * steps / (batch_ms * 1e-3), "ms": batch_ms,
+                    "solves_per_s_5000_steps": count / (batch_ms * 1e-3 * 5000 / steps), "gpu_launches": launches},
+        "plain": {"value": pts * steps / (plain_ms * 1e-3), "ms": plain_ms,
+                  "solves_per_s_5000_steps": count / (plain_ms * 1e-3 * 5000 / steps), "gpu_launches": plain_launches},
+        "speedup": plain_ms / batch_ms,
+        "unit": "grid-point-steps/s",
+        "norm_drift_max": float(max(abs(n - 1.0) for n in norms)),
+    }
+
+
+def serving(rate=200.0, duration=1.0, steps=1000, chunk=500, precision=32, seed=9, local=0, hbm_cap=150e9):
+    """Poisson arrivals (rate/s for `duration` s) of solves drawn from the
+    mixed workload plus 128^3 oscillators, each `steps` steps, served by
+    continuous batching in `chunk`-step rounds under an HBM cap; p50/p99
+    latency from arrival to retirement.  Compared with serving the same
+    requests one at a time (plain: each solved alone, in arrival order)."""
+    import torch
+    from paper_1805_03155_gb300 import inputs, serve, spstd
+
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate, size=int(rate * duration * 3) + 8)
+    t_arr = np.cumsum(gaps)
+    t_arr = t_arr[t_arr < duration]
+    n = len(t_arr)
+    mix = inputs.batch_mix(max(n, 3), seed=seed, steps=steps)
+    probs = []
+    for i in range(n):
+        if i % 10 == 9:
+            p = inputs.gaussian_problem((128, 128, 128), (-8.0,) * 3, (8.0,) * 3, seed=seed * 7 + i,
+                                        integrator="FR4", dt=0.0, steps=steps, n_probe=2)
+        else:
+            p = mix[i]
+        probs.append(p)
+    srv = serve.Server(hbm_cap_bytes=hbm_cap, max_slots=n + 1, chunk_steps=chunk, precision=precision,
+                       device=local, spectrum=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for p, ta in zip(probs, t_arr):
+        srv.submit(p, steps, arrival=t0 + ta)
+    srv.run()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    lat = srv.latencies()
+    pts = sum(p.n_total for p in probs) * steps
+    chunks = srv.chunks
+    srv.close()
+    # plain: the same requests one at a time, each stepped alone
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    plain_lat = []
+    for p, ta in zip(probs, t_arr):
+        now = time.perf_counter() - t1
+        if now < ta:
+            time.sleep(ta - now)
+        s = spstd.solver_for(p, precision=precision, probe_capacity=steps, device=local)
+        s.spstd_step(steps)
+        s.spstd_energy_norm()
+        s.close()
+        plain_lat.append(time.perf_counter() - t1 - ta)
+    plain_wall = time.perf_counter() - t1
+    plain_lat = np.array(plain_lat)
+    return {
+        "workload": f"serve_poisson_{int(rate)}_per_s",
+        "requests": n, "steps_per_request": steps, "chunk_steps": chunk, "hbm_cap_bytes": hbm_cap,
+        "batched": {"solves_per_s": n / wall, "grid_point_steps_per_s": pts / wall,
+                    "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                    "wall_s": wall, "chunks": chunks},
+        "plain": {"solves_per_s": n / plain_wall, "grid_point_steps_per_s": pts / plain_wall,
+                  "p50_s": float(np.percentile(plain_lat, 50)), "p99_s": float(np.percentile(plain_lat, 99)),
+                  "wall_s": plain_wall},
+    }
+
+
 def run_reference(args):
     """The oracle as it stands, on the host cores, same metric and workload.
     Each step is a bounded sample of one half-stage: the oracle's spectral
@@ -227,6 +348,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="aniso_ho_3d_256", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-plain and serving legs")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -385,6 +507,9 @@ def main():
             },
             "check": {"norm_after": nv, "energy_after": ev},
         }
+        if not args.no_batch:
+            out["batched_vs_plain"] = batched_vs_plain(local=local)
+            out["serving"] = serving(local=local)
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(problem)
         print(json.dumps(out))

@@ -245,3 +245,39 @@ def gaussian_problem(n, lo=None, hi=None, seed: int = 7, omega=None, integrator=
     probes = [int(i) for i in rng.integers(n_probe, 0, len(psiR))] if n_probe else []
     return Problem(f"gauss_{'x'.join(map(str, n))}", dims, nn, lo, hi, V, psiR, psiI, probes,
                    integrator, dt, steps, 0)
+
+
+def batch_mix(count: int = 512, seed: int = 4, steps: int = 5000, sizes3d=(32, 64)) -> List[Problem]:
+    """Seeded mix of uneven solves, one third each of:
+
+    * 1D finite wells: N a uniform power of two in 128..8192 on [-20, 20],
+      half-width 2, V0 ~ U(1, 10);
+    * 2D isotropic oscillators: n^2 with n uniform in {64, 128, 256, 512} on
+      [-8, 8]^2, omega = 1;
+    * 3D isotropic oscillators: n^3 with n uniform in ``sizes3d`` (powers of
+      two) on [-8, 8]^3, omega = 1.
+
+    Each gets the gaussian_problem start (psi_R and psi_I displaced Gaussians,
+    seeded per member), 2 probes, FR4, dt = 0 (half the stability limit, chosen
+    by the solver) and `steps` steps; kinds are interleaved."""
+    rng = SplitMix64(seed)
+    out = []
+    for i in range(count):
+        kind = i % 3
+        sub = seed * 1000003 + i
+        if kind == 0:
+            N = int(2 ** rng.integers(1, 7, 14)[0])
+            V0 = float(rng.uniform(1, 1.0, 10.0)[0])
+            p = gaussian_problem((N,), (-20.0,), (20.0,), seed=sub, integrator="FR4", dt=0.0, steps=steps,
+                                 n_probe=2, well=(V0, 2.0))
+        elif kind == 1:
+            n = int(2 ** rng.integers(1, 6, 10)[0])
+            p = gaussian_problem((n, n), (-8.0, -8.0), (8.0, 8.0), seed=sub, integrator="FR4", dt=0.0,
+                                 steps=steps, n_probe=2)
+        else:
+            n = int(sizes3d[int(rng.integers(1, 0, len(sizes3d))[0])])
+            p = gaussian_problem((n, n, n), (-8.0,) * 3, (8.0,) * 3, seed=sub, integrator="FR4", dt=0.0,
+                                 steps=steps, n_probe=2)
+        p.name = f"mix{i}_{p.name}"
+        out.append(p)
+    return out

@@ -1,0 +1,146 @@
+"""Continuous-batching request loop on top of the batch C ABI.
+
+Requests (an inputs.Problem plus a step count) arrive over time.  A request
+is admitted as soon as a batch slot is free and its device footprint (the
+context workspace) fits under the HBM cap; its state then stays on the device
+while the batch advances every member in chunks of `chunk_steps`.  A member
+whose steps are done is retired at the next chunk boundary: its energy, norm
+and probe spectrum are read back, its slot and memory are freed, and its
+latency (retire time minus arrival time) is recorded.  Requests that arrive
+while others run are admitted between chunks, so their work overlaps on the
+device with the running ones.
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass, field
+from typing import Dict, List, Optional
+
+import numpy as np
+
+from . import spstd
+
+
+@dataclass
+class Request:
+    rid: int
+    problem: object
+    steps: int
+    arrival: float
+    admitted: Optional[float] = None
+    finished: Optional[float] = None
+    done_steps: int = 0
+    slot: int = -1
+    solver: object = None
+    result: Dict = field(default_factory=dict)
+
+
+class Server:
+    def __init__(self, hbm_cap_bytes: float = 150e9, max_slots: int = 1024, chunk_steps: int = 500,
+                 precision: int = 32, device: int = 0, keep_state: bool = False, spectrum: bool = True):
+        self.batch = spstd.Batch(max_slots, device=device)
+        self.cap = hbm_cap_bytes
+        self.chunk = int(chunk_steps)
+        self.precision = precision
+        self.device = device
+        self.keep_state = keep_state
+        self.spectrum = spectrum
+        self.queue: List[Request] = []
+        self.running: Dict[int, Request] = {}
+        self.done: List[Request] = []
+        self.footprint = 0
+        self._next = 0
+        self.chunks = 0
+
+    def footprint_of(self, problem) -> int:
+        cfg = spstd.make_config(problem.dims, problem.n[: problem.dims], problem.lo[: problem.dims],
+                                problem.hi[: problem.dims], precision=self.precision,
+                                integrator=problem.integrator, dt=problem.dt, probes=problem.probes,
+                                probe_capacity=max(1, problem.steps))
+        import ctypes as C
+        n = C.c_size_t(0)
+        st = spstd.lib().spstd_workspace_size(C.byref(cfg), C.byref(n))
+        if st != spstd.SPSTD_OK:
+            raise spstd.SpstdError(st, "workspace size")
+        return int(n.value)
+
+    def submit(self, problem, steps: int, arrival: Optional[float] = None) -> int:
+        r = Request(self._next, problem, int(steps), time.perf_counter() if arrival is None else arrival)
+        r.need = self.footprint_of(problem)
+        self._next += 1
+        self.queue.append(r)
+        return r.rid
+
+    def _admit(self, now: float):
+        still = []
+        for r in self.queue:
+            if r.arrival > now or self.footprint + r.need > self.cap:
+                still.append(r)
+                continue
+            try:
+                r.solver = spstd.solver_for(r.problem, precision=self.precision, probe_capacity=max(1, r.steps),
+                                            device=self.device, stream=self.batch.torch_stream)
+                r.slot = self.batch.spstd_batch_add(r.solver)
+            except spstd.SpstdError as e:
+                if e.status == spstd.SPSTD_ENOTREADY:  # batch full: wait for a slot
+                    if r.solver is not None:
+                        r.solver.close()
+                        r.solver = None
+                    still.append(r)
+                    continue
+                raise
+            r.admitted = time.perf_counter()
+            self.footprint += r.need
+            self.running[r.rid] = r
+        self.queue = still
+
+    def _retire(self):
+        for rid in [rid for rid, r in self.running.items() if r.done_steps >= r.steps]:
+            r = self.running.pop(rid)
+            self.batch.spstd_batch_remove(r.slot)
+            s = r.solver
+            r.result["norm"], r.result["energy"] = s.spstd_energy_norm()
+            if self.spectrum and r.problem.probes and r.steps >= 2:
+                r.result["E"], r.result["amp"] = s.spstd_spectrum(-1, max_peaks=4)
+            if self.keep_state:
+                r.result["state"] = s.spstd_get_state()
+            s.close()
+            r.solver = None
+            r.finished = time.perf_counter()
+            self.footprint -= r.need
+            self.done.append(r)
+
+    def step(self):
+        """One scheduling round: admit, advance every member one chunk (or up
+        to the nearest finish), retire."""
+        now = time.perf_counter()
+        self._admit(now)
+        if not self.running:
+            return False
+        n = min(self.chunk, min(r.steps - r.done_steps for r in self.running.values()))
+        self.batch.spstd_batch_step(n)
+        self.batch.spstd_batch_sync()
+        self.chunks += 1
+        for r in self.running.values():
+            r.done_steps += n
+        self._retire()
+        return True
+
+    def run(self, until_empty=True, idle_sleep=1e-3):
+        while self.queue or self.running:
+            if not self.step():
+                if not self.queue:
+                    break
+                nxt = min(r.arrival for r in self.queue)
+                time.sleep(max(0.0, min(idle_sleep, nxt - time.perf_counter())))
+        return self.done
+
+    def latencies(self):
+        lat = np.array([r.finished - r.arrival for r in self.done])
+        return lat
+
+    def close(self):
+        for r in list(self.running.values()):
+            if r.solver is not None:
+                r.solver.close()
+        self.batch.close()
