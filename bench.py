@@ -42,6 +42,22 @@ def make_problem(name, steps):
     return inputs.ho_3d(steps=steps)
 
 
+def max_over_ranks(x, dist, device="cuda"):
+    """Largest value of x over all ranks (the job's time is its slowest rank)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(points_per_rank, steps, world, ms_max):
+    """Whole-job grid-point-steps/s: every rank's points and steps over the
+    slowest rank's time (weak scaling, independent replicas)."""
+    return points_per_rank * steps * world / (ms_max * 1e-3)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -399,11 +415,8 @@ def main():
     ms = ev0.elapsed_time(ev1)
     clk = clocks.stop()
     launches = s.spstd_launch_count(args.steps)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = N * args.steps * ws / (ms * 1e-3)
+    ms = max_over_ranks(ms, dist)
+    value = job_value(N, args.steps, ws, ms)
 
     # ---- per-kernel device times (event pair around each launch) ------------
     prof_steps = max(2, min(8, args.steps))
@@ -443,10 +456,7 @@ def main():
     s.spstd_get_state(out_r, out_i)
     torch.cuda.synchronize()
     t_e2e = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([t_e2e], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
+    t_e2e = max_over_ranks(t_e2e, dist)
     nv, ev = s.spstd_energy_norm()
     s.close()
 

@@ -96,3 +96,54 @@ def test_ho_64cubed_steps_match_oracle(precision, tol):
     oR, oI, opr = oracle_run(p)
     assert rel_l2(R, Im, oR, oI) <= tol
     assert np.max(np.abs(pr - opr)) <= tol * np.max(np.abs(opr))
+
+
+@pytest.mark.slow
+def test_well_1d_full_run_fp64():
+    """The 1D finite well at its full length (256 points, FR4, 20000 steps,
+    FP64): state and probe series to 1e-10 of the oracle, the device spectrum
+    to the oracle's, and the four bound levels within 5 % of the continuum well
+    (k tan(ka) = kappa, -k cot(ka) = kappa; the grid puts the wall between two
+    points, so the discrete levels differ by 1-4 %)."""
+    from helpers import gpu_solver, oracle_run, rel_l2
+
+    p = inputs.well_1d()
+    s = gpu_solver(p, 64, cap=p.steps)
+    s.spstd_step(p.steps)
+    R, Im = s.spstd_get_state()
+    z = np.array([s.spstd_probe(q) for q in range(len(p.probes))])
+    E, A = s.spstd_spectrum(-1, max_peaks=8, thresh=1e-3, phase_correct=True)
+    s.close()
+    oR, oI, opr = oracle_run(p)
+    assert rel_l2(R, Im, oR, oI) <= 1e-10
+    assert np.max(np.abs(z - opr)) <= 1e-10 * np.max(np.abs(opr))
+    c, d = oracle.preset(p.integrator)
+    th, _, oA = oracle.spectrum(opr.sum(axis=0), p.dt, max_peaks=8, thresh=1e-3)
+    oE = np.array([oracle.phase_correct(t, c, d) / p.dt for t in th])
+    assert len(E) == len(oE) and np.max(np.abs(E - oE) / oE) <= 1e-6
+    cont = np.array([0.229468, 0.911550, 2.023038, 3.500540])
+    for e in cont:
+        assert np.min(np.abs(E - e)) / e < 0.05
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_ho_3d_levels_vs_closed_form(precision):
+    """64^3 isotropic oscillator, FR4, the full 10000 steps on the device: the
+    strongest spectral peaks (dispersion-corrected) sit on omega (n + 3/2),
+    n = 0, 1, 2, ... (hbar = m = omega = 1).  Tolerance 2e-4 relative: at
+    T = 23.6 adjacent levels are 3.8 Hann bins apart, and their leakage biases
+    a refined peak by ~1e-3 of a bin."""
+    from paper_1805_03155_gb300 import spstd
+
+    p = inputs.ho_3d()
+    s = spstd.solver_for(p, precision=precision, probe_capacity=p.steps)
+    s.spstd_step(p.steps)
+    n0, e0 = s.spstd_energy_norm()
+    E, A = s.spstd_spectrum(-1, max_peaks=8, thresh=1e-3, phase_correct=True)
+    s.close()
+    strong = E[A > 0.05 * A.max()]
+    assert len(strong) >= 3
+    for e in strong:
+        n = np.round(e - 1.5)
+        assert abs(e - (n + 1.5)) / e < 2e-4, (e, E, A)
+    assert abs(n0 - 1.0) < 1e-5
