@@ -25,6 +25,7 @@ _lock = threading.Lock()
 _lib = None
 
 LEAPFROG, STRANG, PAPER3, FR4, SUZUKI6 = 0, 1, 2, 3, 4
+PERIODIC, DIRICHLET, NEUMANN = 0, 1, 2
 PRESETS = {"LEAPFROG": LEAPFROG, "STRANG": STRANG, "PAPER3": PAPER3, "FR4": FR4, "SUZUKI6": SUZUKI6}
 
 
@@ -37,6 +38,7 @@ class Grid(C.Structure):
         ("hbar", C.c_double),
         ("mass", C.c_double),
         ("nyquist_zero", C.c_int),
+        ("bc", C.c_int * 3),
     ]
 
 
@@ -91,7 +93,7 @@ def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
-def make_grid(dims, n, lo, hi, hbar=1.0, mass=1.0, nyquist_zero=False) -> Grid:
+def make_grid(dims, n, lo, hi, hbar=1.0, mass=1.0, nyquist_zero=False, bc=(0, 0, 0)) -> Grid:
     g = Grid()
     g.dims = int(dims)
     nn = list(n) + [1] * (3 - len(n))
@@ -104,6 +106,9 @@ def make_grid(dims, n, lo, hi, hbar=1.0, mass=1.0, nyquist_zero=False) -> Grid:
     g.hbar = float(hbar)
     g.mass = float(mass)
     g.nyquist_zero = int(bool(nyquist_zero))
+    bb = list(bc) + [0] * (3 - len(bc))
+    for i in range(3):
+        g.bc[i] = int(bb[i])
     return g
 
 

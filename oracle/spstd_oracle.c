@@ -180,18 +180,26 @@ static double k2_of(int64_t j, int64_t n, double L, int nyquist_zero)
 
 /* out = L_axis f = Re F^{-1}[ k^2 F f ] along one axis, i.e. -d^2 f/dx_axis^2
  * (Eq. 10 with the two multiplies by iK folded into one by -K^2).  Every line
- * is transformed on its own, as a complex line with zero imaginary part. */
+ * is transformed on its own, as a complex line with zero imaginary part.
+ * Walls (Section 2.2) use the same periodic transform on the line's odd
+ * (Dirichlet: the DST) or even (Neumann: the DCT) extension over a period of
+ * twice the box, read back on the original points. */
 int orc_laplacian_axis(const double *f, double *out, const orc_grid *g, int axis)
 {
     if (!f || !out || !g || axis < 0 || axis >= g->dims) return -1;
+    const int bc = g->bc[axis];
     int64_t n = g->n[axis];
     int64_t stride = 1, outer = 1;
     for (int b = 0; b < axis; ++b) stride *= g->n[b];
     for (int b = axis + 1; b < 3; ++b) outer *= g->n[b];
     double L = g->hi[axis] - g->lo[axis];
-    double complex *x = (double complex *)malloc(sizeof(double complex) * (size_t)n);
-    double complex *t = (double complex *)malloc(sizeof(double complex) * (size_t)n);
-    double complex *W = twiddles(n);
+    if (bc == ORC_NEUMANN && n < 2) return -1;
+    /* length and period of the line the transform sees */
+    int64_t P = bc == ORC_DIRICHLET ? 2 * (n + 1) : bc == ORC_NEUMANN ? 2 * (n - 1) : n;
+    double Lp = bc == ORC_PERIODIC ? L : 2.0 * L;
+    double complex *x = (double complex *)malloc(sizeof(double complex) * (size_t)P);
+    double complex *t = (double complex *)malloc(sizeof(double complex) * (size_t)P);
+    double complex *W = twiddles(P);
     if (!x || !t || !W) {
         free(x); free(t); free(W);
         return -1;
@@ -199,11 +207,29 @@ int orc_laplacian_axis(const double *f, double *out, const orc_grid *g, int axis
     for (int64_t o = 0; o < outer; ++o) {
         for (int64_t i = 0; i < stride; ++i) {
             int64_t base = o * n * stride + i;
-            for (int64_t j = 0; j < n; ++j) x[j] = f[base + j * stride];
-            fft_with(x, t, n, W, -1);
-            for (int64_t j = 0; j < n; ++j) x[j] *= k2_of(j, n, L, g->nyquist_zero);
-            fft_with(x, t, n, W, +1);
-            for (int64_t j = 0; j < n; ++j) out[base + j * stride] = creal(x[j]) / (double)n;
+            if (bc == ORC_DIRICHLET) {
+                /* 0, f_0..f_{n-1}, 0, -f_{n-1}..-f_0 */
+                x[0] = 0.0;
+                x[n + 1] = 0.0;
+                for (int64_t j = 0; j < n; ++j) {
+                    x[j + 1] = f[base + j * stride];
+                    x[P - 1 - j] = -f[base + j * stride];
+                }
+            } else if (bc == ORC_NEUMANN) {
+                /* f_0..f_{n-1}, f_{n-2}..f_1 */
+                for (int64_t j = 0; j < n; ++j) x[j] = f[base + j * stride];
+                for (int64_t j = 1; j < n - 1; ++j) x[P - j] = f[base + j * stride];
+            } else {
+                for (int64_t j = 0; j < n; ++j) x[j] = f[base + j * stride];
+            }
+            fft_with(x, t, P, W, -1);
+            for (int64_t j = 0; j < P; ++j)
+                x[j] *= k2_of(j, P, Lp, bc == ORC_PERIODIC ? g->nyquist_zero : 0);
+            fft_with(x, t, P, W, +1);
+            for (int64_t j = 0; j < n; ++j) {
+                int64_t src = bc == ORC_DIRICHLET ? j + 1 : j;
+                out[base + j * stride] = creal(x[src]) / (double)P;
+            }
         }
     }
     free(x); free(t); free(W);
@@ -483,13 +509,17 @@ int orc_spectrum(const double *re, const double *im, int64_t M, int64_t nfft, in
 /* ------------------------------------------------------------------------ */
 
 /* norm = dV sum (psi_R^2 + psi_I^2); energy = dV sum (psi_R H psi_R +
- * psi_I H psi_I) with H = hbar K the Hamiltonian of Eq. 1. */
+ * psi_I H psi_I) with H = hbar K the Hamiltonian of Eq. 1.  dV is the grid
+ * spacing product (L/n periodic, L/(n+1) Dirichlet, L/(n-1) Neumann). */
 int orc_norm_energy(const double *psiR, const double *psiI, const double *V,
                     const orc_grid *g, double *norm, double *energy)
 {
     int64_t nt = n_total(g);
     double dV = 1.0;
-    for (int b = 0; b < g->dims; ++b) dV *= (g->hi[b] - g->lo[b]) / (double)g->n[b];
+    for (int b = 0; b < g->dims; ++b) {
+        int64_t cells = g->bc[b] == ORC_DIRICHLET ? g->n[b] + 1 : g->bc[b] == ORC_NEUMANN ? g->n[b] - 1 : g->n[b];
+        dV *= (g->hi[b] - g->lo[b]) / (double)cells;
+    }
     double *h = (double *)malloc(sizeof(double) * (size_t)nt);
     if (!h) return -1;
     double sn = 0.0, se = 0.0;

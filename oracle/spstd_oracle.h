@@ -28,7 +28,16 @@ typedef struct {
     double lo[3], hi[3]; /* periodic box per axis */
     double hbar, mass;   /* hbar and effective mass m* */
     int nyquist_zero;    /* 0: keep k_Nyq^2 = (pi/dx)^2, 1: zero the Nyquist mode */
+    int bc[3];           /* per axis: ORC_PERIODIC, ORC_DIRICHLET or ORC_NEUMANN */
 } orc_grid;
+
+/* Boundary conditions (Section 2.2): the DFT for periodic or decaying fields,
+ * the DST for Dirichlet walls (infinite well), the DCT for Neumann walls.
+ *  ORC_PERIODIC  n points x_j = lo + j L/n, right end excluded;
+ *  ORC_DIRICHLET n interior points x_j = lo + (j+1) L/(n+1), psi = 0 at lo, hi;
+ *  ORC_NEUMANN   n points x_j = lo + j L/(n-1) including both walls, where
+ *                d psi/dx = 0. */
+enum { ORC_PERIODIC = 0, ORC_DIRICHLET = 1, ORC_NEUMANN = 2 };
 
 /* Integrator presets (ids shared by value only with the CUDA library). */
 enum { ORC_LEAPFROG = 0, ORC_STRANG = 1, ORC_PAPER3 = 2, ORC_FR4 = 3, ORC_SUZUKI6 = 4 };
