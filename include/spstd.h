@@ -82,7 +82,8 @@ typedef struct {
     int dims;             /* 1, 2 or 3 */
     int64_t n[3];         /* points per axis, x first.  Each used axis: a power
                              of two, 2 <= n <= 8192 for dims == 1 and
-                             2 <= n <= 1024 otherwise; unused axes: 1 */
+                             2 <= n <= 1024 otherwise, or any 2 <= n <= 256 (see
+                             bc below); unused axes: 1 */
     double lo[3], hi[3];  /* periodic box per axis, hi > lo */
     double hbar, mass;    /* hbar and effective mass m* (> 0) */
     int precision;        /* 32 or 64: type of the fields and of the FFTs;
@@ -100,7 +101,20 @@ typedef struct {
                              1: Nyquist mode zeroed (literal Eq. 10) */
     int device;           /* CUDA device ordinal the workspace lives on */
     void *stream;         /* cudaStream_t for all work; NULL = legacy default */
+    int bc[3];            /* per axis boundary (Section 2.2): SPSTD_PERIODIC (DFT),
+                             SPSTD_DIRICHLET (DST, n interior points between walls
+                             at lo and hi) or SPSTD_NEUMANN (DCT, n points including
+                             both walls) */
 } spstd_config;
+
+/* Boundary conditions (Section 2.2).  Periodic axes whose length is a power of
+ * two use the FFT passes; wall axes, and periodic axes of any other length
+ * 2 <= n <= 256, apply the same spectral operator as a dense n x n matrix
+ * (FP64-built, rounded once), which for such short lines costs no more than the
+ * transforms.  Grid points: periodic x_j = lo + j L/n; Dirichlet
+ * x_j = lo + (j+1) L/(n+1); Neumann x_j = lo + j L/(n-1). */
+enum { SPSTD_PERIODIC = 0, SPSTD_DIRICHLET = 1, SPSTD_NEUMANN = 2 };
+#define SPSTD_MAX_DENSE_N 256
 
 /* Fills cfg with defaults: dims 1, n = (256, 1, 1), box [0, 1), hbar = m* = 1,
  * precision 64, SPSTD_FR4, dt = 0 (auto), no probes, capacity 1024. */

@@ -36,11 +36,31 @@ struct HalfStage {
     int table;    // multiplier table index
     double a;     // s coef dt hbar/2m*
     double bV;    // s coef dt/hbar
+    double scale; // s coef dt (multiplies a dense operator that carries hbar/2m*)
 };
 
 struct Layout {
-    size_t psi[2], V, tmp, staging, ring, counter, status, partial, dout, tw[3], mult, spec, total;
+    size_t psi[2], V, tmp, staging, ring, counter, status, partial, dout, tw[3], mult, dense[3], spec, total;
 };
+
+// An axis uses the FFT passes when it is periodic with a power-of-two length
+// within the FFT limits; otherwise the dense operator (n <= SPSTD_MAX_DENSE_N).
+bool axis_is_fft(const spstd_config &cfg, int a)
+{
+    const int64_t n = cfg.n[a];
+    if (cfg.bc[a] != SPSTD_PERIODIC || (n & (n - 1)) != 0) return false;
+    const int64_t lim = cfg.dims == 1 ? (cfg.precision == 32 ? 8192 : 4096) : 1024;
+    return n >= 2 && n <= lim;
+}
+
+// Points per cell length: periodic L/n, Dirichlet L/(n+1), Neumann L/(n-1).
+double axis_spacing(const spstd_config &cfg, int a)
+{
+    const double L = cfg.hi[a] - cfg.lo[a];
+    const int64_t n = cfg.n[a];
+    return cfg.bc[a] == SPSTD_DIRICHLET ? L / (double)(n + 1) : cfg.bc[a] == SPSTD_NEUMANN ? L / (double)(n - 1)
+                                                                                           : L / (double)n;
+}
 
 bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
 int64_t next_pow2(int64_t v)
@@ -161,10 +181,13 @@ double dispersion_inverse(int m, const double *c, const double *d, double s_star
 
 double w_max_of(const spstd_config &cfg, double vmax)
 {
+    // largest |k| per axis: pi n/L (periodic: the Nyquist mode; Dirichlet: the
+    // n-th sine), pi (n-1)/L (Neumann: the (n-1)-th cosine)
     double w = 0.0;
     for (int a = 0; a < cfg.dims; ++a) {
-        const double dx = (cfg.hi[a] - cfg.lo[a]) / (double)cfg.n[a];
-        w += (kPi / dx) * (kPi / dx);
+        const double L = cfg.hi[a] - cfg.lo[a];
+        const double kmax = kPi * (double)(cfg.bc[a] == SPSTD_NEUMANN ? cfg.n[a] - 1 : cfg.n[a]) / L;
+        w += kmax * kmax;
     }
     return cfg.hbar / (2.0 * cfg.mass) * w + std::max(vmax, 0.0) / cfg.hbar;
 }
@@ -181,17 +204,18 @@ spstd_status validate(const spstd_config *cfg, std::string *why, int *m, double 
     if (cfg->precision != 32 && cfg->precision != 64) return bad("precision must be 32 or 64");
     for (int a = 0; a < 3; ++a) {
         if (a < cfg->dims) {
-            if (!is_pow2(cfg->n[a]) || cfg->n[a] < 2) return bad("each used axis needs a power-of-two size >= 2");
+            if (cfg->bc[a] < SPSTD_PERIODIC || cfg->bc[a] > SPSTD_NEUMANN) return bad("unknown boundary condition");
+            if (cfg->n[a] < 2) return bad("each used axis needs n >= 2");
             if (!(cfg->hi[a] > cfg->lo[a]) || !std::isfinite(cfg->hi[a] - cfg->lo[a])) return bad("box needs hi > lo");
         } else if (cfg->n[a] != 1) {
             return bad("unused axes must have n = 1");
         }
     }
-    const int64_t max1 = cfg->precision == 32 ? Launch<float>::resident_max_n() : Launch<double>::resident_max_n();
     for (int a = 0; a < cfg->dims; ++a) {
-        const int64_t lim = cfg->dims == 1 ? max1 : 1024;
-        if (cfg->n[a] > lim) {
-            if (why) *why = "axis longer than this build supports (1D: 8192 FP32 / 4096 FP64; 2D/3D: 1024)";
+        if (!axis_is_fft(*cfg, a) && cfg->n[a] > SPSTD_MAX_DENSE_N) {
+            if (why)
+                *why = "axis not supported: FFT axes are periodic powers of two (1D <= 8192 FP32 / 4096 FP64, "
+                       "2D/3D <= 1024); other axes need n <= 256";
             return SPSTD_EUNSUPPORTED;
         }
     }
@@ -254,6 +278,8 @@ Layout make_layout(const spstd_config &cfg, int m)
         if (a < cfg.dims) sum_n += cfg.n[a];
     }
     L.mult = take(es * (size_t)(2 * m + 1) * sum_n);
+    for (int a = 0; a < 3; ++a)
+        L.dense[a] = take(a < cfg.dims && !axis_is_fft(cfg, a) ? es * (size_t)cfg.n[a] * cfg.n[a] : 0);
     L.spec = take(spectrum_scratch_bytes(effective_max_nfft(cfg), cfg.probe_capacity));
     L.total = off;
     return L;
@@ -280,6 +306,7 @@ struct spstd_ctx {
     bool tma[3] = {false, false, false};
     CUtensorMap tmap[3][3];
     spstd_batch *batch = nullptr;  // batch this context is a member of
+    bool dense[3] = {false, false, false};  // axis applies the dense operator
 
     void *ptr(size_t off) { return ws + off; }
     size_t field_off(int f) const { return f == 0 ? L.psi[0] : f == 1 ? L.psi[1] : L.tmp; }
@@ -325,10 +352,53 @@ void drop_graph(spstd_ctx *ctx)
 // k^2 of DFT index j on an n-point axis of period L (wrapped index, Eq. 8).
 double k2_of(int64_t j, int64_t n, double L, int nyquist_zero)
 {
-    if (nyquist_zero && j == n / 2) return 0.0;
+    if (nyquist_zero && n % 2 == 0 && j == n / 2) return 0.0;
     const int64_t w = (j <= n / 2) ? j : j - n;
     const double k = 2.0 * kPi * (double)w / L;
     return k * k;
+}
+
+// Spectral second-derivative operator of one axis as a dense n x n matrix
+// (row-major; symmetric except for Neumann walls, whose DCT-I weights the wall
+// points by one half), in FP64: the periodic operator F^-1 k^2 F of the
+// line's extension (itself for periodic axes; the odd extension over twice
+// the box for Dirichlet walls, the even one for Neumann walls, Section 2.2)
+// folded back onto the n grid points.  A[r] = (1/P) sum_q k_q^2 cos(2 pi q r/P)
+// is the circulant of the extended line of P points and period Lp.
+std::vector<double> dense_operator(const spstd_config &cfg, int axis)
+{
+    const int64_t n = cfg.n[axis];
+    const int bc = cfg.bc[axis];
+    const double L = cfg.hi[axis] - cfg.lo[axis];
+    const int64_t P = bc == SPSTD_DIRICHLET ? 2 * (n + 1) : bc == SPSTD_NEUMANN ? 2 * (n - 1) : n;
+    const double Lp = bc == SPSTD_PERIODIC ? L : 2.0 * L;
+    std::vector<double> A(P, 0.0);
+    for (int64_t r = 0; r < P; ++r) {
+        double acc = 0.0;
+        for (int64_t q = 0; q < P; ++q)
+            acc += k2_of(q, P, Lp, bc == SPSTD_PERIODIC ? cfg.nyquist_zero : 0) *
+                   std::cos(2.0 * kPi * (double)((q * r) % P) / (double)P);
+        A[r] = acc / (double)P;
+    }
+    auto circ = [&](int64_t d) { return A[((d % P) + P) % P]; };
+    std::vector<double> D((size_t)n * n, 0.0);
+    for (int64_t i = 0; i < n; ++i) {
+        for (int64_t j = 0; j < n; ++j) {
+            double v;
+            if (bc == SPSTD_DIRICHLET) {
+                // f_j sits at p = j+1 (+) and p = P-1-j (-); output i at p = i+1
+                v = circ((i + 1) - (j + 1)) - circ((i + 1) - (P - 1 - j));
+            } else if (bc == SPSTD_NEUMANN) {
+                // f_j sits at p = j and, for interior j, also at p = P-j
+                v = circ(i - j);
+                if (j > 0 && j < n - 1) v += circ(i - (P - j));
+            } else {
+                v = circ(i - j);
+            }
+            D[(size_t)i * n + j] = v;
+        }
+    }
+    return D;
 }
 
 template <typename T>
@@ -368,6 +438,21 @@ spstd_status upload_tables(spstd_ctx *ctx)
     }
     SPSTD_CU(ctx, cudaMemcpyAsync(ctx->ptr(ctx->L.mult), mult.data(), sizeof(T) * mult.size(),
                                   cudaMemcpyHostToDevice, ctx->stream));
+    // dense operators of the non-FFT axes, times hbar/2m*
+    std::vector<std::vector<T>> dense(3);
+    for (int a = 0; a < cfg.dims; ++a) {
+        if (!ctx->dense[a]) continue;
+        // stored transposed (column-major), so that the threads of a line, one
+        // output point each, read consecutive entries
+        std::vector<double> D = dense_operator(cfg, a);
+        const int64_t n = cfg.n[a];
+        dense[a].resize(D.size());
+        for (int64_t i = 0; i < n; ++i)
+            for (int64_t j = 0; j < n; ++j)
+                dense[a][(size_t)j * n + i] = (T)(cfg.hbar / (2.0 * cfg.mass) * D[(size_t)i * n + j]);
+        SPSTD_CU(ctx, cudaMemcpyAsync(ctx->ptr(ctx->L.dense[a]), dense[a].data(), sizeof(T) * dense[a].size(),
+                                      cudaMemcpyHostToDevice, ctx->stream));
+    }
     // the host vectors die here: wait until the copies have read them
     SPSTD_CU(ctx, cudaStreamSynchronize(ctx->stream));
     return SPSTD_OK;
@@ -411,7 +496,8 @@ void setup_tma(spstd_ctx *ctx)
     if (cfg.precision != 32 || cfg.dims < 2) return;
     const uint64_t n0 = cfg.n[0], n1 = cfg.n[1], n2 = cfg.n[2];
     auto eligible = [](int64_t n) { return n == 64 || n == 128 || n == 256; };
-    bool want[3] = {eligible(cfg.n[0]), eligible(cfg.n[1]), cfg.dims == 3 && eligible(cfg.n[2])};
+    bool want[3] = {eligible(cfg.n[0]) && !ctx->dense[0], eligible(cfg.n[1]) && !ctx->dense[1],
+                    cfg.dims == 3 && eligible(cfg.n[2]) && !ctx->dense[2]};
     for (int v = 0; v < 3; ++v) {
         if (!want[v]) continue;
         bool ok = true;
@@ -440,8 +526,10 @@ spstd_status set_dt(spstd_ctx *ctx, double vmax)
     ctx->hs.clear();
     for (int l = 0; l < ctx->m; ++l) {
         const double k = ctx->cfg.hbar / (2.0 * ctx->cfg.mass);
-        if (ctx->c[l] != 0.0) ctx->hs.push_back({0, 2 * l, ctx->c[l] * dt * k, ctx->c[l] * dt / ctx->cfg.hbar});
-        if (ctx->d[l] != 0.0) ctx->hs.push_back({1, 2 * l + 1, -ctx->d[l] * dt * k, -ctx->d[l] * dt / ctx->cfg.hbar});
+        if (ctx->c[l] != 0.0)
+            ctx->hs.push_back({0, 2 * l, ctx->c[l] * dt * k, ctx->c[l] * dt / ctx->cfg.hbar, ctx->c[l] * dt});
+        if (ctx->d[l] != 0.0)
+            ctx->hs.push_back({1, 2 * l + 1, -ctx->d[l] * dt * k, -ctx->d[l] * dt / ctx->cfg.hbar, -ctx->d[l] * dt});
     }
     if (changed || ctx->gexec == nullptr) {
         drop_graph(ctx);
@@ -495,6 +583,15 @@ T *field_ptr(spstd_ctx *ctx, int f)
     return (T *)ctx->ptr(ctx->field_off(f));
 }
 
+// Factor of a dense operator (which carries hbar/2m*) for multiplier set
+// `table`: s coef dt for a half-stage, hbar for H (row 2m).
+double table_scale(const spstd_ctx *ctx, int table)
+{
+    if (table >= 2 * ctx->m) return ctx->cfg.hbar;
+    const int l = table / 2;
+    return (table & 1) ? -ctx->d[l] * ctx->dt : ctx->c[l] * ctx->dt;
+}
+
 // dst += a sum_d L_d src + bV V src for fields fsrc -> fdst (0 psi_R, 1 psi_I,
 // 2 scratch), multiplier set `table`; the V term rides on the x pass.
 template <typename T>
@@ -511,6 +608,35 @@ cudaError_t enqueue_apply(spstd_ctx *ctx, int fsrc, int fdst, int table, double 
     for (int ax = 0; ax < cfg.dims; ++ax) {
         const int rev = ax == 1 ? !reverse : reverse;
         const int64_t N = cfg.n[ax];
+        if (ctx->dense[ax]) {
+            DenseArgs<T> da{};
+            da.src = src;
+            da.dst = dst;
+            da.V = (const T *)ctx->ptr(ctx->L.V);
+            da.D = (const T *)ctx->ptr(ctx->L.dense[ax]);
+            da.a = (T)table_scale(ctx, table);
+            da.bV = (T)bV;
+            da.use_V = ax == 0;
+            da.n = (int)N;
+            if (ax == 0) {
+                da.stride = 1;
+                da.inner = 1;
+                da.outer_stride = n0;
+                da.n_lines = n1 * n2;
+            } else if (ax == 1) {
+                da.stride = n0;
+                da.inner = n0;
+                da.outer_stride = n0 * n1;
+                da.n_lines = n0 * n2;
+            } else {
+                da.stride = n0 * n1;
+                da.inner = n0 * n1;
+                da.outer_stride = 0;
+                da.n_lines = n0 * n1;
+            }
+            SPSTD_TIMED(timer, s, ax, Launch<T>::dense_pass(da, s));
+            continue;
+        }
         const cpx<T> *tw = (const cpx<T> *)ctx->ptr(ctx->L.tw[ax]);
         if constexpr (sizeof(T) == 4) {
             if (ctx->tma[ax]) {
@@ -586,9 +712,36 @@ cudaError_t enqueue_one_step(spstd_ctx *ctx, cudaStream_t s, LaunchTimer *timer 
 }
 
 template <typename T>
+cudaError_t launch_dense_resident(spstd_ctx *ctx, int64_t nsteps, LaunchTimer *timer)
+{
+    DenseResidentArgs<T> r{};
+    r.psiR = field_ptr<T>(ctx, 0);
+    r.psiI = field_ptr<T>(ctx, 1);
+    r.V = (const T *)ctx->ptr(ctx->L.V);
+    r.D = (const T *)ctx->ptr(ctx->L.dense[0]);
+    r.nh = (int)ctx->hs.size();
+    for (int h = 0; h < r.nh; ++h) {
+        r.a[h] = (T)ctx->hs[h].scale;
+        r.bV[h] = (T)ctx->hs[h].bV;
+        r.hfield[h] = ctx->hs[h].dst;
+    }
+    r.n = (int)ctx->cfg.n[0];
+    r.nsteps = nsteps;
+    ProbeArgs p = probe_args<T>(ctx);
+    r.n_probe = p.n_probe;
+    for (int q = 0; q < p.n_probe; ++q) r.probe_idx[q] = p.idx[q];
+    r.ring = p.ring;
+    r.cap = p.cap;
+    r.counter = p.counter;
+    SPSTD_TIMED(timer, ctx->stream, 4, Launch<T>::dense_resident1d(r, ctx->stream));
+    return cudaSuccess;
+}
+
+template <typename T>
 cudaError_t launch_resident(spstd_ctx *ctx, int64_t nsteps, LaunchTimer *timer)
 {
     const spstd_config &cfg = ctx->cfg;
+    if (ctx->dense[0]) return launch_dense_resident<T>(ctx, nsteps, timer);
     ResidentArgs<T> r{};
     r.psiR = (T *)ctx->ptr(ctx->L.psi[0]);
     r.psiI = (T *)ctx->ptr(ctx->L.psi[1]);
@@ -628,10 +781,10 @@ spstd_status step_impl(spstd_ctx *ctx, int64_t nsteps)
         if (!ctx->gexec) {
             // raise the shared-memory limits of the kernels once, outside the capture
             PassArgs<T> none{};
-            SPSTD_CU(ctx, Launch<T>::xpass((int)cfg.n[0], none, ctx->stream));
+            if (!ctx->dense[0]) SPSTD_CU(ctx, Launch<T>::xpass((int)cfg.n[0], none, ctx->stream));
             none.nx = (int)cfg.n[0];
-            SPSTD_CU(ctx, Launch<T>::spass((int)cfg.n[1], none, ctx->stream));
-            if (cfg.dims == 3) SPSTD_CU(ctx, Launch<T>::spass((int)cfg.n[2], none, ctx->stream));
+            if (!ctx->dense[1]) SPSTD_CU(ctx, Launch<T>::spass((int)cfg.n[1], none, ctx->stream));
+            if (cfg.dims == 3 && !ctx->dense[2]) SPSTD_CU(ctx, Launch<T>::spass((int)cfg.n[2], none, ctx->stream));
             for (int ax = 0; ax < cfg.dims; ++ax)
                 if (ctx->tma[ax]) SPSTD_CU(ctx, prepare_pass_tma(ax, (int)cfg.n[ax]));
             cudaGraph_t g = nullptr;
@@ -766,6 +919,7 @@ spstd_status spstd_create(const spstd_config *cfg, void *d_workspace, size_t wor
     ctx->ntot = cfg->n[0] * cfg->n[1] * cfg->n[2];
     for (int a = 0; a < cfg->dims; ++a) ctx->sum_n += cfg->n[a];
     ctx->stream = (cudaStream_t)cfg->stream;
+    for (int a = 0; a < cfg->dims; ++a) ctx->dense[a] = !axis_is_fft(*cfg, a);
     ctx->s_star = stability_s_star(ctx->m, ctx->c, ctx->d);
     ctx->dt_auto = !(cfg->dt > 0);
     ctx->dt = -1.0;  // forces the first table upload
@@ -979,7 +1133,7 @@ spstd_status energy_norm_impl(spstd_ctx *ctx, double *norm, double *energy)
     spstd_status ds = check_device_status(ctx);
     if (ds != SPSTD_OK) return ds;
     double dV = 1.0;
-    for (int a = 0; a < ctx->cfg.dims; ++a) dV *= (ctx->cfg.hi[a] - ctx->cfg.lo[a]) / (double)ctx->cfg.n[a];
+    for (int a = 0; a < ctx->cfg.dims; ++a) dV *= axis_spacing(ctx->cfg, a);
     *norm = dV * h[0];
     *energy = dV * (h[1] + h[2]);
     if (!std::isfinite(*norm) || !std::isfinite(*energy)) return fail(ctx, SPSTD_EDIVERGED, "norm or energy is not finite");
@@ -1460,6 +1614,9 @@ spstd_status spstd_batch_add(spstd_batch *b, spstd_ctx *ctx, int *slot)
     if (!b || !ctx || !slot) return SPSTD_EINVAL;
     if (ctx->batch) return bfail(b, SPSTD_EINVAL, "context is already a batch member");
     if (ctx->cfg.device != b->device) return bfail(b, SPSTD_EINVAL, "context lives on another device");
+    for (int a = 0; a < ctx->cfg.dims; ++a)
+        if (ctx->dense[a])
+            return bfail(b, SPSTD_EUNSUPPORTED, "batches take FFT axes only (periodic, power-of-two lengths)");
     for (int s = 0; s < (int)b->slots.size(); ++s) {
         if (!b->slots[s]) {
             // the member's own pending work comes first

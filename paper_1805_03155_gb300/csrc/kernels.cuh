@@ -422,6 +422,117 @@ resident1d_batch_kernel(const ResidentArgs<T> *__restrict__ args, int64_t nsteps
 }
 
 // ---------------------------------------------------------------------------
+// Dense line operator (wall boundaries and lengths that are not powers of two):
+// along one axis, dst += a * (D src) + bV V src with D the n x n spectral
+// second-derivative matrix of that axis (times hbar/2m*), stored transposed
+// (entry (i, j) at j n + i) so that consecutive threads read consecutive
+// entries.  Line l
+// starts at (l / inner) * outer_stride + (l % inner) and steps by stride.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct DenseArgs {
+    const T *src;
+    T *dst;
+    const T *V;      // used when use_V
+    const T *D;      // [n][n], transposed: D(i, j) at j * n + i
+    T a, bV;
+    int use_V;
+    int n;
+    int64_t stride, inner, outer_stride, n_lines;
+};
+
+constexpr int kDenseThreads = 128;
+
+template <typename T>
+__global__ void __launch_bounds__(kDenseThreads) dense_pass_kernel(const DenseArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    T *lines = reinterpret_cast<T *>(smem);
+    const int n = a.n;
+    const int lb = kDenseThreads / n > 0 ? kDenseThreads / n : 1;  // lines per block
+    const int64_t l0 = (int64_t)blockIdx.x * lb;
+    // stage the block's lines
+    for (int k = threadIdx.x; k < lb * n; k += blockDim.x) {
+        const int64_t l = l0 + k / n;
+        if (l < a.n_lines) {
+            const int64_t base = (l / a.inner) * a.outer_stride + (l % a.inner);
+            lines[k] = a.src[base + (int64_t)(k % n) * a.stride];
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < lb * n; k += blockDim.x) {
+        const int64_t l = l0 + k / n;
+        if (l >= a.n_lines) continue;
+        const int i = k % n;
+        const T *line = lines + (k / n) * n;
+        T acc = T(0);
+        for (int j = 0; j < n; ++j) acc = fma(__ldg(a.D + (int64_t)j * n + i), line[j], acc);
+        const int64_t off = (l / a.inner) * a.outer_stride + (l % a.inner) + (int64_t)i * a.stride;
+        T r = a.dst[off] + a.a * acc;
+        if (a.use_V) r = fma(a.bV * a.V[off], line[i], r);
+        a.dst[off] = r;
+    }
+}
+
+// Whole 1D grid of n points in one block (thread i owns point i), all steps of
+// a call, with the dense operator of the axis: one barrier per half-stage.
+template <typename T>
+struct DenseResidentArgs {
+    T *psiR, *psiI;
+    const T *V, *D;
+    T a[kMaxHalfStages], bV[kMaxHalfStages];
+    int hfield[kMaxHalfStages];
+    int nh, n;
+    int64_t nsteps;
+    int n_probe;
+    int64_t probe_idx[kMaxProbes];
+    double2 *ring;
+    int64_t cap;
+    int64_t *counter;
+};
+
+template <typename T>
+__global__ void dense_resident1d_kernel(const DenseResidentArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    T *f[2] = {reinterpret_cast<T *>(smem), reinterpret_cast<T *>(smem) + a.n};
+    const int i = threadIdx.x;
+    const bool own = i < a.n;
+    T Vi = T(0);
+    if (own) {
+        f[0][i] = a.psiR[i];
+        f[1][i] = a.psiI[i];
+        Vi = a.V[i];
+    }
+    const int64_t c0 = *a.counter;
+    __syncthreads();
+    for (int64_t step = 0; step < a.nsteps; ++step) {
+        for (int h = 0; h < a.nh; ++h) {
+            const int d = a.hfield[h];       // updated field
+            const T *src = f[1 - d];
+            if (own) {
+                T acc = T(0);
+                for (int j = 0; j < a.n; ++j) acc = fma(__ldg(a.D + (int64_t)j * a.n + i), src[j], acc);
+                f[d][i] = fma(a.bV[h] * Vi, src[i], f[d][i] + a.a[h] * acc);
+            }
+            __syncthreads();
+        }
+        const int64_t slot = (c0 + step) % a.cap;
+        if (i < a.n_probe) {
+            const int64_t idx = a.probe_idx[i];
+            a.ring[(int64_t)i * a.cap + slot] = make_double2((double)f[0][idx], (double)f[1][idx]);
+        }
+        __syncthreads();  // the probes read other threads' points
+    }
+    if (own) {
+        a.psiR[i] = f[0][i];
+        a.psiI[i] = f[1][i];
+    }
+    __syncthreads();
+    if (i == 0) *a.counter = c0 + a.nsteps;
+}
+
+// ---------------------------------------------------------------------------
 // Probe recorder (one block): ring[q][counter % cap] = (psi_R, psi_I)(idx_q).
 // ---------------------------------------------------------------------------
 template <typename T>

@@ -147,6 +147,8 @@ template <typename T> struct Launch {
     static cudaError_t resident_batch(int N, const ResidentArgs<T> *args, int members, int64_t nsteps,
                                       cudaStream_t s);
     static cudaError_t probe_batch(const ProbeMember<T> *members, int count, cudaStream_t s);
+    static cudaError_t dense_pass(const DenseArgs<T> &a, cudaStream_t s);
+    static cudaError_t dense_resident1d(const DenseResidentArgs<T> &a, cudaStream_t s);
 };
 
 }  // namespace spstd

@@ -162,6 +162,25 @@ cudaError_t Launch<T>::probe_batch(const ProbeMember<T> *members, int count, cud
 }
 
 template <typename T>
+cudaError_t Launch<T>::dense_pass(const DenseArgs<T> &a, cudaStream_t s)
+{
+    if (a.n_lines <= 0) return cudaSuccess;
+    const int lb = kDenseThreads / a.n > 0 ? kDenseThreads / a.n : 1;
+    const int64_t blocks = (a.n_lines + lb - 1) / lb;
+    const size_t smem = sizeof(T) * (size_t)lb * a.n;
+    dense_pass_kernel<T><<<(unsigned)blocks, kDenseThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::dense_resident1d(const DenseResidentArgs<T> &a, cudaStream_t s)
+{
+    const int threads = ((a.n > a.n_probe ? a.n : a.n_probe) + 31) / 32 * 32;
+    dense_resident1d_kernel<T><<<1, threads, 2 * sizeof(T) * a.n, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t Launch<T>::probe(const T *psiR, const T *psiI, const ProbeArgs &a, cudaStream_t s)
 {
     probe_kernel<T><<<1, 32, 0, s>>>(psiR, psiI, a);

@@ -95,27 +95,42 @@ class Problem:
     nfft: int = 0
     hbar: float = 1.0
     mass: float = 1.0
+    bc: Tuple[int, int, int] = (0, 0, 0)   # per axis: 0 periodic, 1 Dirichlet, 2 Neumann
 
     @property
     def n_total(self) -> int:
         return int(self.n[0] * self.n[1] * self.n[2])
 
     def coords(self):
-        """Per-axis coordinate vectors x_j = lo + j (hi - lo)/n (Eq. 5/6)."""
-        return [self.lo[a] + np.arange(self.n[a]) * (self.hi[a] - self.lo[a]) / self.n[a]
-                for a in range(3)]
+        """Per-axis coordinate vectors (Eq. 5/6): periodic x_j = lo + j L/n,
+        Dirichlet x_j = lo + (j+1) L/(n+1), Neumann x_j = lo + j L/(n-1)."""
+        return [_axis_coords(self.n[a], self.lo[a], self.hi[a], self.bc[a]) for a in range(3)]
 
 
-def _mesh(n, lo, hi):
-    xs = [lo[a] + np.arange(n[a]) * (hi[a] - lo[a]) / n[a] for a in range(3)]
+def _axis_coords(n, lo, hi, bc=0):
+    L = hi - lo
+    if bc == 1:
+        return lo + np.arange(1, n + 1) * L / (n + 1)
+    if bc == 2:
+        return lo + np.arange(n) * L / max(n - 1, 1)
+    return lo + np.arange(n) * L / n
+
+
+def _mesh(n, lo, hi, bc=(0, 0, 0)):
+    xs = [_axis_coords(n[a], lo[a], hi[a], bc[a]) for a in range(3)]
     Z, Y, X = np.meshgrid(xs[2], xs[1], xs[0], indexing="ij")
     return X.ravel(), Y.ravel(), Z.ravel()
 
 
-def _normalise(psiR, psiI, n, lo, hi, dims):
+def _spacing(n, lo, hi, bc):
+    cells = n + 1 if bc == 1 else (n - 1 if bc == 2 else n)
+    return (hi - lo) / cells
+
+
+def _normalise(psiR, psiI, n, lo, hi, dims, bc=(0, 0, 0)):
     cell = 1.0
     for a in range(dims):
-        cell *= (hi[a] - lo[a]) / n[a]
+        cell *= _spacing(n[a], lo[a], hi[a], bc[a])
     s = np.sqrt(cell * np.sum(psiR * psiR + psiI * psiI))
     return psiR / s, psiI / s
 
@@ -203,7 +218,7 @@ def aniso_ho_3d(seed: int = 3, N: int = 256, steps: int = 50000,
 
 
 def gaussian_problem(n, lo=None, hi=None, seed: int = 7, omega=None, integrator="FR4",
-                     dt=1e-3, steps=10, n_probe=4, noise=0.0, well=None) -> Problem:
+                     dt=1e-3, steps=10, n_probe=4, noise=0.0, well=None, bc=(0, 0, 0)) -> Problem:
     """A seeded test problem on an arbitrary grid.
 
     n: points per axis (x first), 1 to 3 entries.  Potential: harmonic with the
@@ -216,7 +231,8 @@ def gaussian_problem(n, lo=None, hi=None, seed: int = 7, omega=None, integrator=
     lo = tuple(list(lo if lo is not None else [-4.0] * dims) + [0.0] * (3 - dims))
     hi = tuple(list(hi if hi is not None else [4.0] * dims) + [1.0] * (3 - dims))
     rng = SplitMix64(seed)
-    X, Y, Z = _mesh(nn, lo, hi)
+    bcc = tuple(list(bc) + [0] * (3 - len(bc)))
+    X, Y, Z = _mesh(nn, lo, hi, bcc)
     R = [X, Y, Z]
     if well is not None:
         V0, hw = well
@@ -241,10 +257,10 @@ def gaussian_problem(n, lo=None, hi=None, seed: int = 7, omega=None, integrator=
     psiI = 0.3 * np.exp(-e2)
     if noise:
         psiR = psiR + noise * rng.normal(len(psiR))
-    psiR, psiI = _normalise(psiR, psiI, nn, lo, hi, dims)
+    psiR, psiI = _normalise(psiR, psiI, nn, lo, hi, dims, bcc)
     probes = [int(i) for i in rng.integers(n_probe, 0, len(psiR))] if n_probe else []
     return Problem(f"gauss_{'x'.join(map(str, n))}", dims, nn, lo, hi, V, psiR, psiI, probes,
-                   integrator, dt, steps, 0)
+                   integrator, dt, steps, 0, bc=bcc)
 
 
 def batch_mix(count: int = 512, seed: int = 4, steps: int = 5000, sizes3d=(32, 64)) -> List[Problem]:

@@ -20,6 +20,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "spstd.h")
 SPSTD_OK, SPSTD_EINVAL, SPSTD_ENOMEM, SPSTD_ECUDA, SPSTD_EUNSTABLE = 0, 1, 2, 3, 4
 SPSTD_EDIVERGED, SPSTD_ETIMEOUT, SPSTD_ENOTREADY, SPSTD_EUNSUPPORTED = 5, 6, 7, 8
 PRESETS = {"CUSTOM": -1, "LEAPFROG": 0, "STRANG": 1, "PAPER3": 2, "FR4": 3, "SUZUKI6": 4}
+PERIODIC, DIRICHLET, NEUMANN = 0, 1, 2
 MAX_STAGES = 8
 MAX_PROBES = 16
 
@@ -51,6 +52,7 @@ class spstd_config(C.Structure):
         ("nyquist_zero", C.c_int),
         ("device", C.c_int),
         ("stream", C.c_void_p),
+        ("bc", C.c_int * 3),
     ]
 
 
@@ -121,7 +123,8 @@ def _dp(a):
 
 
 def make_config(dims, n, lo, hi, precision=64, integrator="FR4", dt=0.0, probes=(), probe_capacity=1024,
-                max_nfft=0, hbar=1.0, mass=1.0, nyquist_zero=False, c=None, d=None, device=0, stream=None):
+                max_nfft=0, hbar=1.0, mass=1.0, nyquist_zero=False, c=None, d=None, device=0, stream=None,
+                bc=(0, 0, 0)):
     cfg = spstd_config()
     lib().spstd_config_init(C.byref(cfg))
     cfg.dims = int(dims)
@@ -152,6 +155,9 @@ def make_config(dims, n, lo, hi, precision=64, integrator="FR4", dt=0.0, probes=
     cfg.nyquist_zero = int(bool(nyquist_zero))
     cfg.device = int(device)
     cfg.stream = stream
+    bb = list(bc) + [0] * (3 - len(bc))
+    for a in range(3):
+        cfg.bc[a] = int(bb[a])
     return cfg
 
 
@@ -372,7 +378,7 @@ def solver_for(problem, precision=64, probe_capacity=None, stream=None, device=0
                       problem.hi[: problem.dims], precision=precision, integrator=problem.integrator,
                       dt=problem.dt if dt is None else dt, probes=problem.probes, probe_capacity=cap,
                       max_nfft=problem.nfft if problem.nfft else 0, hbar=problem.hbar, mass=problem.mass,
-                      device=device)
+                      device=device, bc=getattr(problem, "bc", (0, 0, 0)))
     s = Solver(cfg, stream=stream)
     s.spstd_set_potential(problem.V)
     s.spstd_set_state(problem.psiR, problem.psiI)

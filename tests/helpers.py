@@ -8,7 +8,7 @@ from paper_1805_03155_gb300 import inputs
 
 def oracle_grid(p: inputs.Problem, nyquist_zero=False):
     return oracle.make_grid(p.dims, p.n[: p.dims], p.lo[: p.dims], p.hi[: p.dims], p.hbar, p.mass,
-                            nyquist_zero)
+                            nyquist_zero, bc=p.bc[: p.dims])
 
 
 def oracle_run(p: inputs.Problem, steps=None, psiR=None, psiI=None, c=None, d=None, dt=None):

@@ -63,7 +63,8 @@ def test_validation_codes(L):
     assert st == spstd.SPSTD_OK and nbytes > 16 * 32 * 8 * 4 * 4
     bad = [
         spstd.make_config(4, (16,), (0,), (1,)),                       # dims
-        spstd.make_config(1, (12,), (0,), (1,)),                       # not a power of two
+        spstd.make_config(1, (1,), (0,), (1,)),                        # n < 2
+        spstd.make_config(1, (16,), (0,), (1,), bc=(7,)),              # unknown boundary
         spstd.make_config(1, (16,), (1,), (0,)),                       # hi < lo
         spstd.make_config(1, (16,), (0,), (1,), precision=16),         # precision
         spstd.make_config(1, (16,), (0,), (1,), probes=[16]),          # probe outside
@@ -75,6 +76,10 @@ def test_validation_codes(L):
         assert _status(cfg)[0] == spstd.SPSTD_EINVAL
     too_long = spstd.make_config(2, (2048, 16), (0, 0), (1, 1))
     assert _status(too_long)[0] == spstd.SPSTD_EUNSUPPORTED
+    odd_long = spstd.make_config(1, (300,), (0,), (1,))          # not a power of two, > 256
+    assert _status(odd_long)[0] == spstd.SPSTD_EUNSUPPORTED
+    walls = spstd.make_config(3, (9, 12, 100), (0,) * 3, (1,) * 3, bc=(1, 2, 0))
+    assert _status(walls)[0] == spstd.SPSTD_OK
     unstable = spstd.make_config(1, (256,), (-20,), (20,), dt=1.0)
     assert _status(unstable)[0] == spstd.SPSTD_EUNSTABLE
 
