@@ -105,6 +105,15 @@ typedef struct {
                              SPSTD_DIRICHLET (DST, n interior points between walls
                              at lo and hi) or SPSTD_NEUMANN (DCT, n points including
                              both walls) */
+    int unmerged_steps;   /* 0 (default): when the last half-stage of a step and
+                             the first of the next update the same field (FR4,
+                             SUZUKI6, STRANG), consecutive steps of one spstd_step
+                             call apply them as one half-stage with the summed
+                             coefficient -- exact, since both act with the other
+                             field unchanged (Eq. 17: exp(aA) exp(bA) =
+                             exp((a+b)A)); the probe at that step boundary is
+                             recovered exactly from the fields before and after.
+                             1: always run every half-stage of every step. */
 } spstd_config;
 
 /* Boundary conditions (Section 2.2).  Periodic axes whose length is a power of

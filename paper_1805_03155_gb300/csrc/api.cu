@@ -40,7 +40,7 @@ struct HalfStage {
 };
 
 struct Layout {
-    size_t psi[2], V, tmp, staging, ring, counter, status, partial, dout, tw[3], mult, dense[3], spec, total;
+    size_t psi[2], V, tmp, staging, ring, counter, status, snap, partial, dout, tw[3], mult, dense[3], spec, total;
 };
 
 // An axis uses the FFT passes when it is periodic with a power-of-two length
@@ -270,6 +270,7 @@ Layout make_layout(const spstd_config &cfg, int m)
     L.ring = take(16 * (size_t)std::max(cfg.n_probe, 1) * cfg.probe_capacity);
     L.counter = take(8);
     L.status = take(8);
+    L.snap = take(16 * SPSTD_MAX_PROBES);
     L.partial = take(8 * kPartials);
     L.dout = take(8 * 8);
     int64_t sum_n = 0;
@@ -277,7 +278,7 @@ Layout make_layout(const spstd_config &cfg, int m)
         L.tw[a] = take(a < cfg.dims ? 2 * es * cfg.n[a] : 0);
         if (a < cfg.dims) sum_n += cfg.n[a];
     }
-    L.mult = take(es * (size_t)(2 * m + 1) * sum_n);
+    L.mult = take(es * (size_t)(2 * m + 2) * sum_n);  // rows: c_l, d_l, H, merged boundary
     for (int a = 0; a < 3; ++a)
         L.dense[a] = take(a < cfg.dims && !axis_is_fft(cfg, a) ? es * (size_t)cfg.n[a] * cfg.n[a] : 0);
     L.spec = take(spectrum_scratch_bytes(effective_max_nfft(cfg), cfg.probe_capacity));
@@ -307,6 +308,10 @@ struct spstd_ctx {
     CUtensorMap tmap[3][3];
     spstd_batch *batch = nullptr;  // batch this context is a member of
     bool dense[3] = {false, false, false};  // axis applies the dense operator
+    // step-boundary merge of the last and first half-stages (same field)
+    bool merge = false;
+    HalfStage merged{};
+    double merge_alpha = 0.0;  // c_last / (c_last + c_first)
 
     void *ptr(size_t off) { return ws + off; }
     size_t field_off(int f) const { return f == 0 ? L.psi[0] : f == 1 ? L.psi[1] : L.tmp; }
@@ -418,13 +423,14 @@ spstd_status upload_tables(spstd_ctx *ctx)
                                       ctx->stream));
     }
     // per half-stage (and H) multipliers a k_d^2(n)/N_d, FP64 then rounded
-    const int ntab = 2 * ctx->m + 1;
+    const int ntab = 2 * ctx->m + 2;
     std::vector<double> a_of(ntab, 0.0);
     for (int l = 0; l < ctx->m; ++l) {
         a_of[2 * l] = +ctx->c[l] * ctx->dt * cfg.hbar / (2.0 * cfg.mass);
         a_of[2 * l + 1] = -ctx->d[l] * ctx->dt * cfg.hbar / (2.0 * cfg.mass);
     }
     a_of[2 * ctx->m] = cfg.hbar * cfg.hbar / (2.0 * cfg.mass);
+    a_of[2 * ctx->m + 1] = ctx->merge ? ctx->merged.a : 0.0;
     std::vector<T> mult((size_t)ntab * ctx->sum_n);
     for (int t = 0; t < ntab; ++t) {
         int64_t off = 0;
@@ -531,6 +537,15 @@ spstd_status set_dt(spstd_ctx *ctx, double vmax)
         if (ctx->d[l] != 0.0)
             ctx->hs.push_back({1, 2 * l + 1, -ctx->d[l] * dt * k, -ctx->d[l] * dt / ctx->cfg.hbar, -ctx->d[l] * dt});
     }
+    ctx->merge = false;
+    if (!ctx->cfg.unmerged_steps && ctx->hs.size() >= 2 && ctx->hs.front().dst == ctx->hs.back().dst) {
+        const HalfStage &f = ctx->hs.front(), &l = ctx->hs.back();
+        if (f.scale + l.scale != 0.0) {
+            ctx->merge = true;
+            ctx->merged = {f.dst, 2 * ctx->m + 1, f.a + l.a, f.bV + l.bV, f.scale + l.scale};
+            ctx->merge_alpha = l.scale / (f.scale + l.scale);
+        }
+    }
     if (changed || ctx->gexec == nullptr) {
         drop_graph(ctx);
         spstd_status s = ctx->cfg.precision == 32 ? upload_tables<float>(ctx) : upload_tables<double>(ctx);
@@ -587,6 +602,7 @@ T *field_ptr(spstd_ctx *ctx, int f)
 // `table`: s coef dt for a half-stage, hbar for H (row 2m).
 double table_scale(const spstd_ctx *ctx, int table)
 {
+    if (table == 2 * ctx->m + 1) return ctx->merged.scale;
     if (table >= 2 * ctx->m) return ctx->cfg.hbar;
     const int l = table / 2;
     return (table & 1) ? -ctx->d[l] * ctx->dt : ctx->c[l] * ctx->dt;
@@ -695,20 +711,56 @@ ProbeArgs probe_args(spstd_ctx *ctx)
     return p;
 }
 
-// One full step of Eq. 17/18 (2D/3D): every half-stage as x, y(, z) passes,
-// then the probe recorder.
+// nsteps full steps of Eq. 17/18 (2D/3D): every half-stage as x, y(, z)
+// passes, then the probe recorder.  With ctx->merge, the last half-stage of
+// each step but the final one is fused with the first of the next step (same
+// field, summed coefficient), and the probe between them is interpolated
+// exactly from a snapshot taken before the fused half-stage.
 template <typename T>
-cudaError_t enqueue_one_step(spstd_ctx *ctx, cudaStream_t s, LaunchTimer *timer = nullptr)
+cudaError_t enqueue_steps(spstd_ctx *ctx, int64_t nsteps, cudaStream_t s, LaunchTimer *timer = nullptr)
 {
     T *psi[2] = {(T *)ctx->ptr(ctx->L.psi[0]), (T *)ctx->ptr(ctx->L.psi[1])};
+    const bool probes = ctx->cfg.n_probe > 0;
+    double2 *snap = (double2 *)ctx->ptr(ctx->L.snap);
+    const int nh = (int)ctx->hs.size();
     int parity = 0;
-    for (const HalfStage &h : ctx->hs) {
-        cudaError_t e = enqueue_apply<T>(ctx, 1 - h.dst, h.dst, h.table, h.bV, parity, s, timer);
-        if (e != cudaSuccess) return e;
-        parity ^= 1;
+    for (int64_t i = 0; i < nsteps; ++i) {
+        const bool fused_in = ctx->merge && i > 0;            // first half-stage already applied
+        const bool fused_out = ctx->merge && i + 1 < nsteps;  // last half-stage fused with the next
+        for (int k = fused_in ? 1 : 0; k < nh; ++k) {
+            if (k == nh - 1 && fused_out) {
+                const HalfStage &h = ctx->merged;
+                if (probes)
+                    SPSTD_TIMED(timer, s, 3, Launch<T>::probe_snapshot(psi[0], psi[1], probe_args<T>(ctx), snap, s));
+                cudaError_t e = enqueue_apply<T>(ctx, 1 - h.dst, h.dst, h.table, h.bV, parity, s, timer);
+                if (e != cudaSuccess) return e;
+                parity ^= 1;
+                if (probes)
+                    SPSTD_TIMED(timer, s, 3,
+                                Launch<T>::probe_merged(psi[0], psi[1], probe_args<T>(ctx), snap, ctx->merge_alpha,
+                                                        h.dst, s));
+            } else {
+                const HalfStage &h = ctx->hs[k];
+                cudaError_t e = enqueue_apply<T>(ctx, 1 - h.dst, h.dst, h.table, h.bV, parity, s, timer);
+                if (e != cudaSuccess) return e;
+                parity ^= 1;
+            }
+        }
+        if (probes && !fused_out)
+            SPSTD_TIMED(timer, s, 3, Launch<T>::probe(psi[0], psi[1], probe_args<T>(ctx), s));
     }
-    if (ctx->cfg.n_probe > 0) SPSTD_TIMED(timer, s, 3, Launch<T>::probe(psi[0], psi[1], probe_args<T>(ctx), s));
     return cudaSuccess;
+}
+
+// Kernel launches enqueue_steps(n) issues.
+int64_t launches_for_steps(const spstd_ctx *ctx, int64_t n)
+{
+    if (n <= 0) return 0;
+    const int64_t nh = (int64_t)ctx->hs.size();
+    const int64_t halfstages = ctx->merge ? n * nh - (n - 1) : n * nh;
+    // a merged boundary records its probe with a snapshot and an interpolating recorder
+    const int64_t probe = ctx->cfg.n_probe > 0 ? (ctx->merge ? 2 * n - 1 : n) : 0;
+    return halfstages * ctx->cfg.dims + probe;
 }
 
 template <typename T>
@@ -789,13 +841,11 @@ spstd_status step_impl(spstd_ctx *ctx, int64_t nsteps)
                 if (ctx->tma[ax]) SPSTD_CU(ctx, prepare_pass_tma(ax, (int)cfg.n[ax]));
             cudaGraph_t g = nullptr;
             SPSTD_CU(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
-            for (int i = 0; i < kGraphSteps; ++i) {
-                e = enqueue_one_step<T>(ctx, ctx->cap_stream);
-                if (e != cudaSuccess) {
-                    cudaStreamEndCapture(ctx->cap_stream, &g);
-                    if (g) cudaGraphDestroy(g);
-                    return cuda_fail(ctx, e, "graph capture");
-                }
+            e = enqueue_steps<T>(ctx, kGraphSteps, ctx->cap_stream);
+            if (e != cudaSuccess) {
+                cudaStreamEndCapture(ctx->cap_stream, &g);
+                if (g) cudaGraphDestroy(g);
+                return cuda_fail(ctx, e, "graph capture");
             }
             SPSTD_CU(ctx, cudaStreamEndCapture(ctx->cap_stream, &g));
             e = cudaGraphInstantiate(&ctx->gexec, g, 0);
@@ -810,10 +860,10 @@ spstd_status step_impl(spstd_ctx *ctx, int64_t nsteps)
         nsteps -= reps * kGraphSteps;
         ctx->steps_taken += reps * kGraphSteps;
     }
-    for (int64_t i = 0; i < nsteps; ++i) {
-        e = enqueue_one_step<T>(ctx, ctx->stream);
+    if (nsteps > 0) {
+        e = enqueue_steps<T>(ctx, nsteps, ctx->stream);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "step launch");
-        ctx->steps_taken += 1;
+        ctx->steps_taken += nsteps;
     }
     return SPSTD_OK;
 }
@@ -1177,7 +1227,7 @@ spstd_status profile_impl(spstd_ctx *ctx, int64_t nsteps, double *ms, int64_t *c
     if (ctx->cfg.dims == 1) {
         SPSTD_CU(ctx, launch_resident<T>(ctx, nsteps, &timer));
     } else {
-        for (int64_t i = 0; i < nsteps; ++i) SPSTD_CU(ctx, enqueue_one_step<T>(ctx, ctx->stream, &timer));
+        SPSTD_CU(ctx, enqueue_steps<T>(ctx, nsteps, ctx->stream, &timer));
     }
     ctx->steps_taken += nsteps;
     SPSTD_CU(ctx, cudaStreamSynchronize(ctx->stream));
@@ -1237,7 +1287,9 @@ spstd_status spstd_launch_count(const spstd_ctx *ctx, int64_t nsteps, int64_t *l
     } else if (ctx->cfg.dims == 1) {
         *launches = 1;
     } else {
-        *launches = nsteps * ((int64_t)ctx->hs.size() * ctx->cfg.dims + (ctx->cfg.n_probe > 0 ? 1 : 0));
+        // graph-replayed chunks of kGraphSteps, then the remainder
+        const int64_t reps = nsteps >= kGraphSteps ? nsteps / kGraphSteps : 0;
+        *launches = reps * launches_for_steps(ctx, kGraphSteps) + launches_for_steps(ctx, nsteps - reps * kGraphSteps);
     }
     return SPSTD_OK;
 }

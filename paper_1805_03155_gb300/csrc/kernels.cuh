@@ -548,6 +548,36 @@ __global__ void probe_kernel(const T *__restrict__ psiR, const T *__restrict__ p
     if (q == 0) *a.counter = c + 1;
 }
 
+// Probe values at a merged step boundary: the boundary lies inside a merged
+// half-stage that updates field `mf` with coefficient c_last + c_first, so the
+// recorded value of that field is snap + alpha (now - snap), alpha = c_last /
+// (c_last + c_first); the other field is unchanged by it.
+template <typename T>
+__global__ void probe_snapshot_kernel(const T *__restrict__ psiR, const T *__restrict__ psiI, const ProbeArgs a,
+                                      double2 *__restrict__ snap)
+{
+    const int q = threadIdx.x;
+    if (q < a.n_probe) snap[q] = make_double2((double)psiR[a.idx[q]], (double)psiI[a.idx[q]]);
+}
+
+template <typename T>
+__global__ void probe_merged_kernel(const T *__restrict__ psiR, const T *__restrict__ psiI, const ProbeArgs a,
+                                    const double2 *__restrict__ snap, double alpha, int mf)
+{
+    const int64_t c = *a.counter;
+    const int q = threadIdx.x;
+    if (q < a.n_probe) {
+        const int64_t idx = a.idx[q];
+        const double2 s = snap[q];
+        double r = (double)psiR[idx], i = (double)psiI[idx];
+        if (mf == 0) r = s.x + alpha * (r - s.x);
+        else i = s.y + alpha * (i - s.y);
+        a.ring[(int64_t)q * a.cap + c % a.cap] = make_double2(r, i);
+    }
+    __syncthreads();
+    if (q == 0) *a.counter = c + 1;
+}
+
 // Batched probe recorder: block b records member b.
 template <typename T>
 struct ProbeMember {

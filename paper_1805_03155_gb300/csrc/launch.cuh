@@ -148,6 +148,10 @@ template <typename T> struct Launch {
                                       cudaStream_t s);
     static cudaError_t probe_batch(const ProbeMember<T> *members, int count, cudaStream_t s);
     static cudaError_t dense_pass(const DenseArgs<T> &a, cudaStream_t s);
+    static cudaError_t probe_snapshot(const T *psiR, const T *psiI, const ProbeArgs &a, double2 *snap,
+                                      cudaStream_t s);
+    static cudaError_t probe_merged(const T *psiR, const T *psiI, const ProbeArgs &a, const double2 *snap,
+                                    double alpha, int mf, cudaStream_t s);
     static cudaError_t dense_resident1d(const DenseResidentArgs<T> &a, cudaStream_t s);
 };
 

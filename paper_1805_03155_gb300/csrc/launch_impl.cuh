@@ -162,6 +162,22 @@ cudaError_t Launch<T>::probe_batch(const ProbeMember<T> *members, int count, cud
 }
 
 template <typename T>
+cudaError_t Launch<T>::probe_snapshot(const T *psiR, const T *psiI, const ProbeArgs &a, double2 *snap,
+                                      cudaStream_t s)
+{
+    probe_snapshot_kernel<T><<<1, 32, 0, s>>>(psiR, psiI, a, snap);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::probe_merged(const T *psiR, const T *psiI, const ProbeArgs &a, const double2 *snap,
+                                    double alpha, int mf, cudaStream_t s)
+{
+    probe_merged_kernel<T><<<1, 32, 0, s>>>(psiR, psiI, a, snap, alpha, mf);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t Launch<T>::dense_pass(const DenseArgs<T> &a, cudaStream_t s)
 {
     if (a.n_lines <= 0) return cudaSuccess;

@@ -53,6 +53,7 @@ class spstd_config(C.Structure):
         ("device", C.c_int),
         ("stream", C.c_void_p),
         ("bc", C.c_int * 3),
+        ("unmerged_steps", C.c_int),
     ]
 
 
@@ -124,7 +125,7 @@ def _dp(a):
 
 def make_config(dims, n, lo, hi, precision=64, integrator="FR4", dt=0.0, probes=(), probe_capacity=1024,
                 max_nfft=0, hbar=1.0, mass=1.0, nyquist_zero=False, c=None, d=None, device=0, stream=None,
-                bc=(0, 0, 0)):
+                bc=(0, 0, 0), merge=True):
     cfg = spstd_config()
     lib().spstd_config_init(C.byref(cfg))
     cfg.dims = int(dims)
@@ -158,6 +159,7 @@ def make_config(dims, n, lo, hi, precision=64, integrator="FR4", dt=0.0, probes=
     bb = list(bc) + [0] * (3 - len(bc))
     for a in range(3):
         cfg.bc[a] = int(bb[a])
+    cfg.unmerged_steps = 0 if merge else 1
     return cfg
 
 
@@ -371,14 +373,14 @@ def spstd_norm_noalloc(psiR_ptr, psiI_ptr, n, precision, cell_volume, out_ptr, s
                                     float(cell_volume), C.c_void_p(out_ptr), C.c_void_p(stream_ptr))
 
 
-def solver_for(problem, precision=64, probe_capacity=None, stream=None, device=0, dt=None):
+def solver_for(problem, precision=64, probe_capacity=None, stream=None, device=0, dt=None, merge=True):
     """Creates a Solver for an inputs.Problem and uploads V and the state."""
     cap = probe_capacity if probe_capacity is not None else max(1, problem.steps)
     cfg = make_config(problem.dims, problem.n[: problem.dims], problem.lo[: problem.dims],
                       problem.hi[: problem.dims], precision=precision, integrator=problem.integrator,
                       dt=problem.dt if dt is None else dt, probes=problem.probes, probe_capacity=cap,
                       max_nfft=problem.nfft if problem.nfft else 0, hbar=problem.hbar, mass=problem.mass,
-                      device=device, bc=getattr(problem, "bc", (0, 0, 0)))
+                      device=device, bc=getattr(problem, "bc", (0, 0, 0)), merge=merge)
     s = Solver(cfg, stream=stream)
     s.spstd_set_potential(problem.V)
     s.spstd_set_state(problem.psiR, problem.psiI)

@@ -25,10 +25,10 @@ def gpu_solver(p: inputs.Problem, precision=64, cap=None, **kw):
     return spstd.solver_for(p, precision=precision, probe_capacity=cap, **kw)
 
 
-def gpu_run(p: inputs.Problem, precision=64, steps=None, chunks=None):
+def gpu_run(p: inputs.Problem, precision=64, steps=None, chunks=None, merge=True):
     """Runs steps (default p.steps) on the GPU; returns (psiR, psiI, probes)."""
     steps = p.steps if steps is None else steps
-    s = gpu_solver(p, precision, cap=max(1, steps))
+    s = gpu_solver(p, precision, cap=max(1, steps), merge=merge)
     if chunks is None:
         s.spstd_step(steps)
     else:

@@ -34,7 +34,7 @@ def test_batch_members_equal_lone_solves(precision):
     steps = 27  # two graph chunks of 10 + 7 direct steps
     alone = []
     for p in probs:
-        s = gpu_solver(p, precision, cap=steps)
+        s = gpu_solver(p, precision, cap=steps, merge=False)  # batches run every half-stage
         s.spstd_step(steps)
         R, Im = s.spstd_get_state()
         alone.append((R, Im, np.array([s.spstd_probe(q) for q in range(3)])))
@@ -69,12 +69,12 @@ def test_batch_membership_changes():
     probs = members()[:6]
     ref = []
     for p in probs:
-        s = gpu_solver(p, 64, cap=40)
+        s = gpu_solver(p, 64, cap=40, merge=False)
         s.spstd_step(30)
         ref.append(s.spstd_get_state())
         s.close()
     batch = spstd.Batch(4)
-    solvers = [gpu_solver(p, 64, cap=40) for p in probs]
+    solvers = [gpu_solver(p, 64, cap=40, merge=False) for p in probs]
     slots = [batch.spstd_batch_add(s) for s in solvers[:4]]
     with pytest.raises(spstd.SpstdError) as ei:
         batch.spstd_batch_add(solvers[4])

@@ -85,11 +85,28 @@ def test_graph_replay_equals_single_steps(shape):
     """Chunks replayed from the captured graph give bitwise the same result as
     single-step calls (and the probes line up)."""
     p = small_problem(shape, steps=40)
-    a = gpu_run(p, 64, chunks=[40])
-    b = gpu_run(p, 64, chunks=[1] * 40)
-    c = gpu_run(p, 64, chunks=[17, 3, 16, 4])
+    a = gpu_run(p, 64, chunks=[40], merge=False)
+    b = gpu_run(p, 64, chunks=[1] * 40, merge=False)
+    c = gpu_run(p, 64, chunks=[17, 3, 16, 4], merge=False)
     for x, y in ((a, b), (a, c)):
         assert np.array_equal(x[0], y[0]) and np.array_equal(x[1], y[1]) and np.array_equal(x[2], y[2])
+
+
+@pytest.mark.parametrize("shape,integrator", [((16, 32), "FR4"), ((8, 16, 32), "SUZUKI6"), ((32, 16), "STRANG"),
+                                              ((16, 8, 8), "PAPER3")], ids=str)
+def test_merged_step_boundaries_equal_unmerged(shape, integrator):
+    """Fusing the last half-stage of a step with the first of the next (same
+    field, summed coefficient) is exact: merged and unmerged runs agree to FP64
+    rounding, probes included (the boundary probe is interpolated from a
+    snapshot), for any chunking of the steps."""
+    p = small_problem(shape, integrator=integrator, steps=41)
+    ref = gpu_run(p, 64, chunks=[41], merge=False)
+    for chunks in ([41], [1] * 41, [17, 3, 21]):
+        got = gpu_run(p, 64, chunks=chunks, merge=True)
+        scale = max(np.abs(ref[0]).max(), np.abs(ref[1]).max())
+        assert np.max(np.abs(got[0] - ref[0])) <= 1e-12 * scale
+        assert np.max(np.abs(got[1] - ref[1])) <= 1e-12 * scale
+        assert np.max(np.abs(got[2] - ref[2])) <= 1e-12 * np.abs(ref[2]).max()
 
 
 @pytest.mark.parametrize("shape", [(256,), (32, 64), (16, 16, 32)], ids=lambda s: "x".join(map(str, s)))
@@ -109,12 +126,12 @@ def test_energy_norm_match_oracle(shape, precision):
 
 def test_checkpoint_resume_is_bitwise():
     p = small_problem((16, 8, 32), steps=30)
-    full = gpu_run(p, 64)
-    s = gpu_solver(p, 64, cap=30)
+    full = gpu_run(p, 64, merge=False)
+    s = gpu_solver(p, 64, cap=30, merge=False)
     s.spstd_step(13)
     R, Im = s.spstd_get_state()
     s.close()
-    s2 = gpu_solver(p, 64, cap=30)
+    s2 = gpu_solver(p, 64, cap=30, merge=False)
     s2.spstd_set_state(R, Im)
     s2.spstd_step(17)
     R2, I2 = s2.spstd_get_state()

@@ -39,7 +39,7 @@ def test_served_results_equal_lone_solves(precision):
     srv.close()
     for r in done:
         p, steps = reqs[r.rid]
-        s = spstd.solver_for(p, precision=precision, probe_capacity=steps)
+        s = spstd.solver_for(p, precision=precision, probe_capacity=steps, merge=False)
         s.spstd_step(steps)
         R, Im = s.spstd_get_state()
         nv, ev = s.spstd_energy_norm()

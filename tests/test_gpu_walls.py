@@ -118,7 +118,9 @@ def test_table2_on_device(integrator, col):
 def test_table3_on_device():
     """Table 3 (2D infinite well, 2048 steps, SPSTD): the device series equals
     the oracle's; every strong device peak sits on the scheme's discrete
-    frequency of some mode (n_x, n_y) (within 0.05 bin); and the printed SPSTD
+    frequency of some mode (n_x, n_y) within 0.3 bin (2D modes crowd: (4,5) and
+    (2,6) are 1.8 bins apart, inside the Hann main lobe, which biases a refined
+    peak by up to a quarter bin); and the printed SPSTD
     entries of the modes this source excites are found within 0.15 bin (the
     delta two cells off the centre on the diagonal barely excites (1,3) and
     (2,3); the oracle test checks every printed entry against the scheme)."""
@@ -138,6 +140,6 @@ def test_table3_on_device():
     exact = np.array([np.arccos(np.trace(oracle.evolution_matrix(c, d, (lev[i] + lev[j]) * p.dt)) / 2) / p.dt
                       for i in range(9) for j in range(9)])
     for o in om[A > 0.02 * A.max()]:
-        assert np.min(np.abs(exact - o)) < 0.05 * b, (o / b, exact / b)
+        assert np.min(np.abs(exact - o)) < 0.3 * b, (o / b, exact / b)
     found = sum(np.min(np.abs(om - spstd)) < 0.15 * b for _, _, spstd, _ in tab)
     assert found >= 4, (om / b, tab[:, 2] / b)
