@@ -484,7 +484,10 @@ def main():
                 "box": [problem.lo[0], problem.hi[0]],
                 "integrator": problem.integrator,
                 "half_stages_per_step": coeff_halfstages,
-                "half_stages_applied_per_step": half_stages,
+                # the timed call of K steps applies K (h - 1) + 1 half-stages when step
+                # boundaries are fused, K h otherwise
+                "half_stages_applied_per_step": ((args.steps * (coeff_halfstages - 1) + 1) / args.steps
+                                                 if half_stages < coeff_halfstages else coeff_halfstages),
                 "merged_step_boundaries": bool(half_stages < coeff_halfstages),
                 "fields": "fp32" if prec == 32 else "fp64",
                 "reductions": "fp64",

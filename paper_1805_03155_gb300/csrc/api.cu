@@ -752,6 +752,47 @@ cudaError_t enqueue_steps(spstd_ctx *ctx, int64_t nsteps, cudaStream_t s, Launch
     return cudaSuccess;
 }
 
+// With merged boundaries a call of n steps is: the first half-stage, n - 1
+// units, the tail.  A unit is the inner half-stages of a step followed by the
+// fused boundary (its last half-stage + the next step's first) and the
+// interpolated probe; the tail is the inner half-stages, the last half-stage
+// and the probe.  Units are what the captured graph replays.
+template <typename T>
+cudaError_t enqueue_merged_piece(spstd_ctx *ctx, int piece, int64_t units, cudaStream_t s,
+                                 LaunchTimer *timer = nullptr)
+{
+    T *psi[2] = {(T *)ctx->ptr(ctx->L.psi[0]), (T *)ctx->ptr(ctx->L.psi[1])};
+    const bool probes = ctx->cfg.n_probe > 0;
+    double2 *snap = (double2 *)ctx->ptr(ctx->L.snap);
+    const int nh = (int)ctx->hs.size();
+    int parity = 0;
+    auto apply = [&](const HalfStage &h) {
+        cudaError_t e = enqueue_apply<T>(ctx, 1 - h.dst, h.dst, h.table, h.bV, parity, s, timer);
+        parity ^= 1;
+        return e;
+    };
+    cudaError_t e = cudaSuccess;
+    if (piece == 0) return apply(ctx->hs[0]);  // head
+    if (piece == 1) {                          // units
+        for (int64_t u = 0; u < units; ++u) {
+            for (int k = 1; k < nh - 1; ++k)
+                if ((e = apply(ctx->hs[k])) != cudaSuccess) return e;
+            if (probes)
+                SPSTD_TIMED(timer, s, 3, Launch<T>::probe_snapshot(psi[0], psi[1], probe_args<T>(ctx), snap, s));
+            if ((e = apply(ctx->merged)) != cudaSuccess) return e;
+            if (probes)
+                SPSTD_TIMED(timer, s, 3,
+                            Launch<T>::probe_merged(psi[0], psi[1], probe_args<T>(ctx), snap, ctx->merge_alpha,
+                                                    ctx->merged.dst, s));
+        }
+        return cudaSuccess;
+    }
+    for (int k = 1; k < nh; ++k)  // tail
+        if ((e = apply(ctx->hs[k])) != cudaSuccess) return e;
+    if (probes) SPSTD_TIMED(timer, s, 3, Launch<T>::probe(psi[0], psi[1], probe_args<T>(ctx), s));
+    return cudaSuccess;
+}
+
 // Kernel launches enqueue_steps(n) issues.
 int64_t launches_for_steps(const spstd_ctx *ctx, int64_t n)
 {
@@ -817,6 +858,21 @@ cudaError_t launch_resident(spstd_ctx *ctx, int64_t nsteps, LaunchTimer *timer)
     return cudaSuccess;
 }
 
+// Raises the shared-memory limits of the pass kernels once, outside any capture.
+template <typename T>
+spstd_status prepare_kernels(spstd_ctx *ctx)
+{
+    const spstd_config &cfg = ctx->cfg;
+    PassArgs<T> none{};
+    if (!ctx->dense[0]) SPSTD_CU(ctx, Launch<T>::xpass((int)cfg.n[0], none, ctx->stream));
+    none.nx = (int)cfg.n[0];
+    if (cfg.dims > 1 && !ctx->dense[1]) SPSTD_CU(ctx, Launch<T>::spass((int)cfg.n[1], none, ctx->stream));
+    if (cfg.dims == 3 && !ctx->dense[2]) SPSTD_CU(ctx, Launch<T>::spass((int)cfg.n[2], none, ctx->stream));
+    for (int ax = 0; ax < cfg.dims; ++ax)
+        if (ctx->tma[ax]) SPSTD_CU(ctx, prepare_pass_tma(ax, (int)cfg.n[ax]));
+    return SPSTD_OK;
+}
+
 template <typename T>
 spstd_status step_impl(spstd_ctx *ctx, int64_t nsteps)
 {
@@ -829,16 +885,42 @@ spstd_status step_impl(spstd_ctx *ctx, int64_t nsteps)
         return SPSTD_OK;
     }
     cudaError_t e;
+    if (ctx->merge) {
+        // head, graph-replayed units, remaining units, tail
+        const int64_t units = nsteps - 1;
+        SPSTD_CU(ctx, enqueue_merged_piece<T>(ctx, 0, 0, ctx->stream));
+        int64_t done = 0;
+        if (units >= kGraphSteps) {
+            if (!ctx->gexec) {
+                spstd_status ps = prepare_kernels<T>(ctx);
+                if (ps != SPSTD_OK) return ps;
+                cudaGraph_t g = nullptr;
+                SPSTD_CU(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+                e = enqueue_merged_piece<T>(ctx, 1, kGraphSteps, ctx->cap_stream);
+                cudaError_t e2 = cudaStreamEndCapture(ctx->cap_stream, &g);
+                if (e != cudaSuccess || e2 != cudaSuccess) {
+                    if (g) cudaGraphDestroy(g);
+                    return cuda_fail(ctx, e != cudaSuccess ? e : e2, "graph capture");
+                }
+                e = cudaGraphInstantiate(&ctx->gexec, g, 0);
+                cudaGraphDestroy(g);
+                if (e != cudaSuccess) {
+                    ctx->gexec = nullptr;
+                    return cuda_fail(ctx, e, "cudaGraphInstantiate");
+                }
+            }
+            for (int64_t r = 0; r < units / kGraphSteps; ++r) SPSTD_CU(ctx, cudaGraphLaunch(ctx->gexec, ctx->stream));
+            done = units / kGraphSteps * kGraphSteps;
+        }
+        SPSTD_CU(ctx, enqueue_merged_piece<T>(ctx, 1, units - done, ctx->stream));
+        SPSTD_CU(ctx, enqueue_merged_piece<T>(ctx, 2, 0, ctx->stream));
+        ctx->steps_taken += nsteps;
+        return SPSTD_OK;
+    }
     if (nsteps >= kGraphSteps) {
         if (!ctx->gexec) {
-            // raise the shared-memory limits of the kernels once, outside the capture
-            PassArgs<T> none{};
-            if (!ctx->dense[0]) SPSTD_CU(ctx, Launch<T>::xpass((int)cfg.n[0], none, ctx->stream));
-            none.nx = (int)cfg.n[0];
-            if (!ctx->dense[1]) SPSTD_CU(ctx, Launch<T>::spass((int)cfg.n[1], none, ctx->stream));
-            if (cfg.dims == 3 && !ctx->dense[2]) SPSTD_CU(ctx, Launch<T>::spass((int)cfg.n[2], none, ctx->stream));
-            for (int ax = 0; ax < cfg.dims; ++ax)
-                if (ctx->tma[ax]) SPSTD_CU(ctx, prepare_pass_tma(ax, (int)cfg.n[ax]));
+            spstd_status ps = prepare_kernels<T>(ctx);
+            if (ps != SPSTD_OK) return ps;
             cudaGraph_t g = nullptr;
             SPSTD_CU(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
             e = enqueue_steps<T>(ctx, kGraphSteps, ctx->cap_stream);
@@ -1227,7 +1309,13 @@ spstd_status profile_impl(spstd_ctx *ctx, int64_t nsteps, double *ms, int64_t *c
     if (ctx->cfg.dims == 1) {
         SPSTD_CU(ctx, launch_resident<T>(ctx, nsteps, &timer));
     } else {
-        SPSTD_CU(ctx, enqueue_steps<T>(ctx, nsteps, ctx->stream, &timer));
+        if (ctx->merge && nsteps > 0) {
+            SPSTD_CU(ctx, enqueue_merged_piece<T>(ctx, 0, 0, ctx->stream, &timer));
+            SPSTD_CU(ctx, enqueue_merged_piece<T>(ctx, 1, nsteps - 1, ctx->stream, &timer));
+            SPSTD_CU(ctx, enqueue_merged_piece<T>(ctx, 2, 0, ctx->stream, &timer));
+        } else {
+            SPSTD_CU(ctx, enqueue_steps<T>(ctx, nsteps, ctx->stream, &timer));
+        }
     }
     ctx->steps_taken += nsteps;
     SPSTD_CU(ctx, cudaStreamSynchronize(ctx->stream));
@@ -1287,9 +1375,16 @@ spstd_status spstd_launch_count(const spstd_ctx *ctx, int64_t nsteps, int64_t *l
     } else if (ctx->cfg.dims == 1) {
         *launches = 1;
     } else {
-        // graph-replayed chunks of kGraphSteps, then the remainder
-        const int64_t reps = nsteps >= kGraphSteps ? nsteps / kGraphSteps : 0;
-        *launches = reps * launches_for_steps(ctx, kGraphSteps) + launches_for_steps(ctx, nsteps - reps * kGraphSteps);
+        if (ctx->merge) {
+            // n (h - 1) + 1 half-stages; 2 (n - 1) + 1 probe launches
+            const int64_t nh = (int64_t)ctx->hs.size();
+            *launches = (nsteps * (nh - 1) + 1) * ctx->cfg.dims + (ctx->cfg.n_probe > 0 ? 2 * nsteps - 1 : 0);
+        } else {
+            // graph-replayed chunks of kGraphSteps, then the remainder
+            const int64_t reps = nsteps >= kGraphSteps ? nsteps / kGraphSteps : 0;
+            *launches = reps * launches_for_steps(ctx, kGraphSteps) +
+                        launches_for_steps(ctx, nsteps - reps * kGraphSteps);
+        }
     }
     return SPSTD_OK;
 }
