@@ -77,6 +77,7 @@ enum {
 
 #define SPSTD_MAX_STAGES 8
 #define SPSTD_MAX_PROBES 16
+#define SPSTD_MAX_EIGENSTATES 4
 
 typedef struct {
     int dims;             /* 1, 2 or 3 */
@@ -105,6 +106,8 @@ typedef struct {
                              SPSTD_DIRICHLET (DST, n interior points between walls
                              at lo and hi) or SPSTD_NEUMANN (DCT, n points including
                              both walls) */
+    int max_eigenstates;  /* 0..4: eigenstate accumulators to reserve (FP64 complex,
+                             16 B per grid point each) */
     int unmerged_steps;   /* 0 (default): when the last half-stage of a step and
                              the first of the next update the same field (FR4,
                              SUZUKI6, STRANG), consecutive steps of one spstd_step
@@ -239,6 +242,21 @@ spstd_status spstd_profile_steps(spstd_ctx *ctx, int64_t nsteps, double *ms, int
 #define SPSTD_NOALLOC_MAX_ELEMS ((int64_t)SPSTD_NOALLOC_MAX_PARTIALS * 2048)
 spstd_status spstd_norm_noalloc(const void *psiR, const void *psiI, int64_t n, int precision,
                                 double cell_volume, double *d_norm, void *stream);
+
+/* ---- Eigenstates (Figs. 1, 2, 4: the eigenstate of a spectral peak) -------
+ * spstd_eigenstates_begin opens an accumulation window: each of the next
+ * `window` steps adds, for every target energy E_k (k < n_target <=
+ * cfg.max_eigenstates), w_n psi^n exp(+i E_k t_n / hbar) to accumulator k at
+ * every grid point (FP64), with w_n the symmetric Hann window over the window
+ * and t_n the time after the n-th step of the window.  The result is the
+ * eigenstate at E_k up to normalisation and phase (components at other
+ * energies are suppressed by the window).  While a window is open steps run
+ * without fused boundaries or the resident 1D solver (every step ends at a
+ * full state).  spstd_eigenstate_get copies accumulator k (unnormalised) to
+ * the host and synchronises; spstd_eigenstates_end closes the window. */
+spstd_status spstd_eigenstates_begin(spstd_ctx *ctx, int n_target, const double *E, int64_t window);
+spstd_status spstd_eigenstate_get(spstd_ctx *ctx, int k, double *re, double *im, int64_t *samples);
+spstd_status spstd_eigenstates_end(spstd_ctx *ctx);
 
 /* ---- Batches: many independent solves advanced by one call ---------------
  * A batch advances every member context by the same number of steps, each with

@@ -81,6 +81,8 @@ def lib():
             L.orc_phase_correct.argtypes = [C.c_double, dp, dp, C.c_int]
             L.orc_phase_correct.restype = C.c_double
             L.orc_norm_energy.argtypes = [dp, dp, dp, gp, dp, dp]
+            L.orc_run_eigen.argtypes = [dp, dp, dp, gp, dp, dp, C.c_int, C.c_double, C.c_int64, C.c_int,
+                                        dp, dp, dp]
             _lib = L
     return _lib
 
@@ -223,3 +225,21 @@ def norm_energy(psiR, psiI, V, g: Grid):
     if lib().orc_norm_energy(_dp(pr), _dp(pi), _dp(V), C.byref(g), C.byref(nv), C.byref(ev)):
         raise ValueError("orc_norm_energy failed")
     return nv.value, ev.value
+
+
+def run_eigen(psiR, psiI, V, g: Grid, c, d, dt, nsteps, E):
+    """Advance copies by nsteps and return (psiR, psiI, acc) with acc complex
+    [len(E), n_total]: the Hann-windowed Fourier components at energies E."""
+    pr = _f64(psiR).copy()
+    pi = _f64(psiI).copy()
+    V = _f64(V) if V is not None else np.zeros_like(pr)
+    c = _f64(c)
+    d = _f64(d)
+    E = _f64(np.atleast_1d(E))
+    n = len(pr)
+    ar = np.zeros(len(E) * n)
+    ai = np.zeros(len(E) * n)
+    if lib().orc_run_eigen(_dp(pr), _dp(pi), _dp(V), C.byref(g), _dp(c), _dp(d), len(c), float(dt), int(nsteps),
+                           len(E), _dp(E), _dp(ar), _dp(ai)):
+        raise ValueError("orc_run_eigen failed")
+    return pr, pi, (ar + 1j * ai).reshape(len(E), n)

@@ -533,3 +533,36 @@ int orc_norm_energy(const double *psiR, const double *psiI, const double *V,
     *energy = dV * se;
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Eigenstates (Figs. 1, 2, 4: the eigenstate belonging to a spectral peak).  */
+/* ------------------------------------------------------------------------ */
+
+/* Advances the state by nsteps steps (as orc_run) and accumulates, for each
+ * target energy E_k, the windowed Fourier component of the field at every
+ * point: acc_k = sum_n w_n psi^n exp(+i E_k t_n / hbar), t_n = (n+1) dt the
+ * time after step n, w_n the symmetric Hann window over the nsteps samples
+ * (w = 1 if nsteps = 1).  A component exp(-i E t/hbar) of the evolution is
+ * kept where E = E_k and suppressed elsewhere by the window, so acc_k is the
+ * eigenstate at E_k up to normalisation and phase.  acc arrays: [n_target][n_total]. */
+int orc_run_eigen(double *psiR, double *psiI, const double *V, const orc_grid *g,
+                  const double *c, const double *d, int m, double dt, int64_t nsteps,
+                  int n_target, const double *E, double *acc_re, double *acc_im)
+{
+    int64_t nt = n_total(g);
+    for (int64_t p = 0; p < (int64_t)n_target * nt; ++p) acc_re[p] = acc_im[p] = 0.0;
+    for (int64_t s = 0; s < nsteps; ++s) {
+        if (orc_run(psiR, psiI, V, g, c, d, m, dt, 1, 0, NULL, NULL, NULL)) return -1;
+        double w = (nsteps == 1) ? 1.0 : 0.5 * (1.0 - cos(TWO_PI * (double)s / (double)(nsteps - 1)));
+        for (int k = 0; k < n_target; ++k) {
+            double ph = E[k] * (double)(s + 1) * dt / g->hbar;
+            double cr = w * cos(ph), ci = w * sin(ph);
+            for (int64_t p = 0; p < nt; ++p) {
+                /* (psiR + i psiI)(cr + i ci) */
+                acc_re[(int64_t)k * nt + p] += psiR[p] * cr - psiI[p] * ci;
+                acc_im[(int64_t)k * nt + p] += psiR[p] * ci + psiI[p] * cr;
+            }
+        }
+    }
+    return 0;
+}

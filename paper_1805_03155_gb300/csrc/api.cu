@@ -40,7 +40,8 @@ struct HalfStage {
 };
 
 struct Layout {
-    size_t psi[2], V, tmp, staging, ring, counter, status, snap, partial, dout, tw[3], mult, dense[3], spec, total;
+    size_t psi[2], V, tmp, staging, ring, counter, status, snap, partial, dout, tw[3], mult, dense[3], spec;
+    size_t eig_acc, eig_theta, eig_step, total;
 };
 
 // An axis uses the FFT passes when it is periodic with a power-of-two length
@@ -241,6 +242,7 @@ spstd_status validate(const spstd_config *cfg, std::string *why, int *m, double 
         if (cfg->probe_idx[q] < 0 || cfg->probe_idx[q] >= ntot) return bad("probe index outside the grid");
     if (cfg->probe_capacity < 1) return bad("probe_capacity must be >= 1");
     if (cfg->max_nfft > 0 && (!is_pow2(cfg->max_nfft) || cfg->max_nfft < 4)) return bad("max_nfft must be a power of two >= 4");
+    if (cfg->max_eigenstates < 0 || cfg->max_eigenstates > SPSTD_MAX_EIGENSTATES) return bad("max_eigenstates must be 0..4");
     if (!std::isfinite(cfg->dt)) return bad("dt is not finite");
     return SPSTD_OK;
 }
@@ -282,6 +284,9 @@ Layout make_layout(const spstd_config &cfg, int m)
     for (int a = 0; a < 3; ++a)
         L.dense[a] = take(a < cfg.dims && !axis_is_fft(cfg, a) ? es * (size_t)cfg.n[a] * cfg.n[a] : 0);
     L.spec = take(spectrum_scratch_bytes(effective_max_nfft(cfg), cfg.probe_capacity));
+    L.eig_acc = take(16 * (size_t)cfg.max_eigenstates * ntot);
+    L.eig_theta = take(8 * SPSTD_MAX_EIGENSTATES);
+    L.eig_step = take(16);  // int64 step, unsigned completion count
     L.total = off;
     return L;
 }
@@ -312,6 +317,10 @@ struct spstd_ctx {
     bool merge = false;
     HalfStage merged{};
     double merge_alpha = 0.0;  // c_last / (c_last + c_first)
+    // eigenstate accumulation window
+    bool eig_active = false;
+    int eig_n = 0;
+    int64_t eig_window = 0;
 
     void *ptr(size_t off) { return ws + off; }
     size_t field_off(int f) const { return f == 0 ? L.psi[0] : f == 1 ? L.psi[1] : L.tmp; }
@@ -873,12 +882,31 @@ spstd_status prepare_kernels(spstd_ctx *ctx)
     return SPSTD_OK;
 }
 
+// A step followed by the eigenstate accumulation (every step ends at a full state).
+template <typename T>
+cudaError_t enqueue_eigen_step(spstd_ctx *ctx, cudaStream_t s, LaunchTimer *timer = nullptr)
+{
+    cudaError_t e = enqueue_steps<T>(ctx, 1, s, timer);
+    if (e != cudaSuccess) return e;
+    int64_t *step = (int64_t *)ctx->ptr(ctx->L.eig_step);
+    SPSTD_TIMED(timer, s, 3,
+                Launch<T>::eigen_accum(field_ptr<T>(ctx, 0), field_ptr<T>(ctx, 1), (double2 *)ctx->ptr(ctx->L.eig_acc),
+                                       ctx->ntot, ctx->eig_n, (const double *)ctx->ptr(ctx->L.eig_theta),
+                                       ctx->eig_window, step, (unsigned *)(step + 1), s));
+    return cudaSuccess;
+}
+
 template <typename T>
 spstd_status step_impl(spstd_ctx *ctx, int64_t nsteps)
 {
     const spstd_config &cfg = ctx->cfg;
     T *psi0 = (T *)ctx->ptr(ctx->L.psi[0]);
     T *psi1 = (T *)ctx->ptr(ctx->L.psi[1]);
+    if (ctx->eig_active) {
+        for (int64_t i = 0; i < nsteps; ++i) SPSTD_CU(ctx, enqueue_eigen_step<T>(ctx, ctx->stream));
+        ctx->steps_taken += nsteps;
+        return SPSTD_OK;
+    }
     if (cfg.dims == 1) {
         SPSTD_CU(ctx, launch_resident<T>(ctx, nsteps, nullptr));
         ctx->steps_taken += nsteps;
@@ -1342,6 +1370,51 @@ spstd_status spstd_profile_steps(spstd_ctx *ctx, int64_t nsteps, double *ms, int
                                     : profile_impl<double>(ctx, nsteps, ms, cnt);
 }
 
+spstd_status spstd_eigenstates_begin(spstd_ctx *ctx, int n_target, const double *E, int64_t window)
+{
+    if (!ctx || !E || window < 1) return SPSTD_EINVAL;
+    if (n_target < 1 || n_target > ctx->cfg.max_eigenstates)
+        return fail(ctx, SPSTD_EINVAL, "n_target must be 1..max_eigenstates");
+    double theta[SPSTD_MAX_EIGENSTATES] = {0};
+    for (int k = 0; k < n_target; ++k) {
+        if (!std::isfinite(E[k])) return fail(ctx, SPSTD_EINVAL, "non-finite target energy");
+        theta[k] = E[k] * ctx->dt / ctx->cfg.hbar;
+    }
+    SPSTD_CU(ctx, cudaMemsetAsync(ctx->ptr(ctx->L.eig_acc), 0, 16 * (size_t)n_target * ctx->ntot, ctx->stream));
+    SPSTD_CU(ctx, cudaMemsetAsync(ctx->ptr(ctx->L.eig_step), 0, 16, ctx->stream));
+    SPSTD_CU(ctx, cudaMemcpyAsync(ctx->ptr(ctx->L.eig_theta), theta, sizeof(theta), cudaMemcpyHostToDevice,
+                                  ctx->stream));
+    SPSTD_CU(ctx, cudaStreamSynchronize(ctx->stream));  // theta lives on this stack
+    ctx->eig_active = true;
+    ctx->eig_n = n_target;
+    ctx->eig_window = window;
+    return SPSTD_OK;
+}
+
+spstd_status spstd_eigenstate_get(spstd_ctx *ctx, int k, double *re, double *im, int64_t *samples)
+{
+    if (!ctx || !re || !im || k < 0 || k >= ctx->eig_n) return SPSTD_EINVAL;
+    std::vector<double2> acc(ctx->ntot);
+    int64_t n = 0;
+    SPSTD_CU(ctx, cudaMemcpyAsync(acc.data(), (double2 *)ctx->ptr(ctx->L.eig_acc) + (size_t)k * ctx->ntot,
+                                  sizeof(double2) * ctx->ntot, cudaMemcpyDeviceToHost, ctx->stream));
+    SPSTD_CU(ctx, cudaMemcpyAsync(&n, ctx->ptr(ctx->L.eig_step), 8, cudaMemcpyDeviceToHost, ctx->stream));
+    SPSTD_CU(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int64_t p = 0; p < ctx->ntot; ++p) {
+        re[p] = acc[p].x;
+        im[p] = acc[p].y;
+    }
+    if (samples) *samples = n;
+    return SPSTD_OK;
+}
+
+spstd_status spstd_eigenstates_end(spstd_ctx *ctx)
+{
+    if (!ctx) return SPSTD_EINVAL;
+    ctx->eig_active = false;
+    return SPSTD_OK;
+}
+
 spstd_status spstd_get_dt(const spstd_ctx *ctx, double *dt)
 {
     if (!ctx || !dt) return SPSTD_EINVAL;
@@ -1372,6 +1445,8 @@ spstd_status spstd_launch_count(const spstd_ctx *ctx, int64_t nsteps, int64_t *l
     if (!ctx || !launches || nsteps < 0) return SPSTD_EINVAL;
     if (nsteps == 0) {
         *launches = 0;
+    } else if (ctx->eig_active) {
+        *launches = nsteps * ((int64_t)ctx->hs.size() * ctx->cfg.dims + (ctx->cfg.n_probe > 0 ? 1 : 0) + 1);
     } else if (ctx->cfg.dims == 1) {
         *launches = 1;
     } else {

@@ -578,6 +578,47 @@ __global__ void probe_merged_kernel(const T *__restrict__ psiR, const T *__restr
     if (q == 0) *a.counter = c + 1;
 }
 
+// Eigenstate accumulation after a step: acc[k][p] += w_n (psi_R + i psi_I)[p]
+// exp(+i theta_k (n + 1)), n = *step (samples taken so far), w_n the Hann
+// window over `window` samples; no-op once n >= window.  The last block to
+// finish advances *step (completion count in *done, reset for the next step).
+template <typename T>
+__global__ void eigen_accum_kernel(const T *__restrict__ psiR, const T *__restrict__ psiI,
+                                   double2 *__restrict__ acc, int64_t n, int n_target, const double *__restrict__ theta,
+                                   int64_t window, int64_t *step, unsigned *done)
+{
+    __shared__ double2 s_ph[4];
+    __shared__ bool s_last;
+    const int64_t k = *step;
+    if (k < window) {
+        if (threadIdx.x < n_target) {
+            const double w = window == 1 ? 1.0 : 0.5 * (1.0 - cospi(2.0 * (double)k / (double)(window - 1)));
+            double sn, cs;
+            sincos(theta[threadIdx.x] * (double)(k + 1), &sn, &cs);
+            s_ph[threadIdx.x] = make_double2(w * cs, w * sn);
+        }
+        __syncthreads();
+        for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+            const double zr = (double)psiR[p], zi = (double)psiI[p];
+            for (int t = 0; t < n_target; ++t) {
+                const double2 ph = s_ph[t];
+                double2 a = acc[(int64_t)t * n + p];
+                a.x += zr * ph.x - zi * ph.y;
+                a.y += zr * ph.y + zi * ph.x;
+                acc[(int64_t)t * n + p] = a;
+            }
+        }
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        *done = 0u;
+        if (k < window) *step = k + 1;
+    }
+}
+
 // Batched probe recorder: block b records member b.
 template <typename T>
 struct ProbeMember {

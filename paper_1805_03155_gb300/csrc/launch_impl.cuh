@@ -178,6 +178,18 @@ cudaError_t Launch<T>::probe_merged(const T *psiR, const T *psiI, const ProbeArg
 }
 
 template <typename T>
+cudaError_t Launch<T>::eigen_accum(const T *psiR, const T *psiI, double2 *acc, int64_t n, int n_target,
+                                   const double *theta, int64_t window, int64_t *step, unsigned *done,
+                                   cudaStream_t s)
+{
+    int64_t b = (n + 255) / 256;
+    if (b > 2048) b = 2048;
+    if (b < 1) b = 1;
+    eigen_accum_kernel<T><<<(unsigned)b, 256, 0, s>>>(psiR, psiI, acc, n, n_target, theta, window, step, done);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t Launch<T>::dense_pass(const DenseArgs<T> &a, cudaStream_t s)
 {
     if (a.n_lines <= 0) return cudaSuccess;

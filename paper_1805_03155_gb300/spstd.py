@@ -53,6 +53,7 @@ class spstd_config(C.Structure):
         ("device", C.c_int),
         ("stream", C.c_void_p),
         ("bc", C.c_int * 3),
+        ("max_eigenstates", C.c_int),
         ("unmerged_steps", C.c_int),
     ]
 
@@ -98,6 +99,9 @@ def lib():
         "spstd_launch_count": (C.c_int, [vp, C.c_int64, ip]),
         "spstd_profile_steps": (C.c_int, [vp, C.c_int64, dp, ip]),
         "spstd_norm_noalloc": (C.c_int, [vp, vp, C.c_int64, C.c_int, C.c_double, vp, vp]),
+        "spstd_eigenstates_begin": (C.c_int, [vp, C.c_int, dp, C.c_int64]),
+        "spstd_eigenstate_get": (C.c_int, [vp, C.c_int, dp, dp, ip]),
+        "spstd_eigenstates_end": (C.c_int, [vp]),
         "spstd_batch_workspace_size": (C.c_int, [C.c_int, C.POINTER(C.c_size_t)]),
         "spstd_batch_create": (C.c_int, [C.c_int, C.c_int, vp, vp, C.c_size_t, C.POINTER(vp)]),
         "spstd_batch_destroy": (C.c_int, [vp]),
@@ -125,7 +129,7 @@ def _dp(a):
 
 def make_config(dims, n, lo, hi, precision=64, integrator="FR4", dt=0.0, probes=(), probe_capacity=1024,
                 max_nfft=0, hbar=1.0, mass=1.0, nyquist_zero=False, c=None, d=None, device=0, stream=None,
-                bc=(0, 0, 0), merge=True):
+                bc=(0, 0, 0), merge=True, max_eigenstates=0):
     cfg = spstd_config()
     lib().spstd_config_init(C.byref(cfg))
     cfg.dims = int(dims)
@@ -160,6 +164,7 @@ def make_config(dims, n, lo, hi, precision=64, integrator="FR4", dt=0.0, probes=
     for a in range(3):
         cfg.bc[a] = int(bb[a])
     cfg.unmerged_steps = 0 if merge else 1
+    cfg.max_eigenstates = int(max_eigenstates)
     return cfg
 
 
@@ -271,6 +276,27 @@ class Solver:
         self._check(self.L.spstd_get_coefficients(self.ctx, C.byref(m), _dp(c), _dp(d)))
         return c[: m.value].copy(), d[: m.value].copy()
 
+    def spstd_eigenstates_begin(self, E, window):
+        E = np.ascontiguousarray(np.atleast_1d(E), dtype=np.float64)
+        self._check(self.L.spstd_eigenstates_begin(self.ctx, len(E), _dp(E), int(window)))
+
+    def spstd_eigenstate_get(self, k, normalise=True):
+        """Accumulator k as a complex array; normalised to sum |phi|^2 = 1 and
+        rotated so that its largest entry is real positive when normalise."""
+        re_ = np.empty(self.n_total)
+        im_ = np.empty(self.n_total)
+        n = C.c_int64(0)
+        self._check(self.L.spstd_eigenstate_get(self.ctx, int(k), _dp(re_), _dp(im_), C.byref(n)))
+        z = re_ + 1j * im_
+        if normalise and np.any(z):
+            z = z / np.linalg.norm(z)
+            j = np.argmax(np.abs(z))
+            z = z * np.exp(-1j * np.angle(z[j]))
+        return z
+
+    def spstd_eigenstates_end(self):
+        self._check(self.L.spstd_eigenstates_end(self.ctx))
+
     KERNEL_KINDS = ("x_pass", "y_pass", "z_pass", "probe", "resident_1d")
 
     def spstd_profile_steps(self, nsteps):
@@ -373,14 +399,16 @@ def spstd_norm_noalloc(psiR_ptr, psiI_ptr, n, precision, cell_volume, out_ptr, s
                                     float(cell_volume), C.c_void_p(out_ptr), C.c_void_p(stream_ptr))
 
 
-def solver_for(problem, precision=64, probe_capacity=None, stream=None, device=0, dt=None, merge=True):
+def solver_for(problem, precision=64, probe_capacity=None, stream=None, device=0, dt=None, merge=True,
+               max_eigenstates=0):
     """Creates a Solver for an inputs.Problem and uploads V and the state."""
     cap = probe_capacity if probe_capacity is not None else max(1, problem.steps)
     cfg = make_config(problem.dims, problem.n[: problem.dims], problem.lo[: problem.dims],
                       problem.hi[: problem.dims], precision=precision, integrator=problem.integrator,
                       dt=problem.dt if dt is None else dt, probes=problem.probes, probe_capacity=cap,
                       max_nfft=problem.nfft if problem.nfft else 0, hbar=problem.hbar, mass=problem.mass,
-                      device=device, bc=getattr(problem, "bc", (0, 0, 0)), merge=merge)
+                      device=device, bc=getattr(problem, "bc", (0, 0, 0)), merge=merge,
+                      max_eigenstates=max_eigenstates)
     s = Solver(cfg, stream=stream)
     s.spstd_set_potential(problem.V)
     s.spstd_set_state(problem.psiR, problem.psiI)
