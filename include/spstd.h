@@ -65,14 +65,18 @@ typedef enum {
  *  SPSTD_SUZUKI6   Suzuki five-fold Strang composition (order 4),
  *                  p = 1/(4 - 4^(1/3)): c = (p/2, p, (1-3p)/2, (1-3p)/2, p, p/2),
  *                  d = (p, p, 1-4p, p, p, 0).
- *  SPSTD_CUSTOM    use cfg.m, cfg.c, cfg.d as given (m <= 8). */
+ *  SPSTD_CUSTOM    use cfg.m, cfg.c, cfg.d as given (m <= 8).
+ *  SPSTD_RK4       not symplectic: the classical fourth-order Runge-Kutta
+ *                  scheme the paper compares against (Fig. 3), on the same
+ *                  kernels (8 K applications per step); stable for w dt <= 2 sqrt 2. */
 enum {
     SPSTD_CUSTOM = -1,
     SPSTD_LEAPFROG = 0,
     SPSTD_STRANG = 1,
     SPSTD_PAPER3 = 2,
     SPSTD_FR4 = 3,
-    SPSTD_SUZUKI6 = 4
+    SPSTD_SUZUKI6 = 4,
+    SPSTD_RK4 = 5
 };
 
 #define SPSTD_MAX_STAGES 8

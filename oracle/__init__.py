@@ -81,6 +81,7 @@ def lib():
             L.orc_phase_correct.argtypes = [C.c_double, dp, dp, C.c_int]
             L.orc_phase_correct.restype = C.c_double
             L.orc_norm_energy.argtypes = [dp, dp, dp, gp, dp, dp]
+            L.orc_run_rk4.argtypes = [dp, dp, dp, gp, C.c_double, C.c_int64, C.c_int, ip, dp, dp]
             L.orc_run_eigen.argtypes = [dp, dp, dp, gp, dp, dp, C.c_int, C.c_double, C.c_int64, C.c_int,
                                         dp, dp, dp]
             _lib = L
@@ -243,3 +244,19 @@ def run_eigen(psiR, psiI, V, g: Grid, c, d, dt, nsteps, E):
                            len(E), _dp(E), _dp(ar), _dp(ai)):
         raise ValueError("orc_run_eigen failed")
     return pr, pi, (ar + 1j * ai).reshape(len(E), n)
+
+
+def run_rk4(psiR, psiI, V, g: Grid, dt, nsteps, probe_idx=()):
+    """Classical RK4 (the non-symplectic comparison of Fig. 3); as run()."""
+    pr = _f64(psiR).copy()
+    pi = _f64(psiI).copy()
+    V = _f64(V) if V is not None else np.zeros_like(pr)
+    idx = np.ascontiguousarray(probe_idx, dtype=np.int64)
+    npb = len(idx)
+    bre = np.zeros(max(npb * int(nsteps), 1))
+    bim = np.zeros(max(npb * int(nsteps), 1))
+    if lib().orc_run_rk4(_dp(pr), _dp(pi), _dp(V), C.byref(g), float(dt), int(nsteps), npb,
+                         idx.ctypes.data_as(C.POINTER(C.c_int64)), _dp(bre), _dp(bim)):
+        raise ValueError("orc_run_rk4 failed")
+    probes = (bre[: npb * nsteps] + 1j * bim[: npb * nsteps]).reshape(npb, int(nsteps))
+    return pr, pi, probes

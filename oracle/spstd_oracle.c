@@ -566,3 +566,60 @@ int orc_run_eigen(double *psiR, double *psiI, const double *V, const orc_grid *g
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* The non-symplectic comparison scheme of Fig. 3: classical Runge-Kutta.     */
+/* ------------------------------------------------------------------------ */
+
+/* Classical fourth-order Runge-Kutta for d(psi_R, psi_I)/dt = (K psi_I,
+ * -K psi_R) (Eq. 3/4 with K of Eq. 16): k1 = f(y), k2 = f(y + dt/2 k1),
+ * k3 = f(y + dt/2 k2), k4 = f(y + dt k3), y += dt/6 (k1 + 2 k2 + 2 k3 + k4).
+ * Probes as orc_run. */
+int orc_run_rk4(double *psiR, double *psiI, const double *V, const orc_grid *g, double dt, int64_t nsteps,
+                int n_probe, const int64_t *probe_idx, double *probe_re, double *probe_im)
+{
+    int64_t nt = n_total(g);
+    double *tr = (double *)malloc(sizeof(double) * (size_t)nt);
+    double *ti = (double *)malloc(sizeof(double) * (size_t)nt);
+    double *kr = (double *)malloc(sizeof(double) * (size_t)nt);
+    double *ki = (double *)malloc(sizeof(double) * (size_t)nt);
+    double *ar = (double *)malloc(sizeof(double) * (size_t)nt);
+    double *ai = (double *)malloc(sizeof(double) * (size_t)nt);
+    if (!tr || !ti || !kr || !ki || !ar || !ai) {
+        free(tr); free(ti); free(kr); free(ki); free(ar); free(ai);
+        return -1;
+    }
+    const double b[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+    const double a[4] = {0.0, 0.5, 0.5, 1.0};
+    int rc = 0;
+    for (int64_t s = 0; s < nsteps && !rc; ++s) {
+        for (int64_t p = 0; p < nt; ++p) {
+            tr[p] = ar[p] = psiR[p];
+            ti[p] = ai[p] = psiI[p];
+        }
+        for (int j = 0; j < 4 && !rc; ++j) {
+            /* k = f(t): (K t_I, -K t_R) */
+            rc |= orc_apply_K(ti, V, kr, g);
+            rc |= orc_apply_K(tr, V, ki, g);
+            for (int64_t p = 0; p < nt; ++p) {
+                ki[p] = -ki[p];
+                ar[p] += b[j] * dt * kr[p];
+                ai[p] += b[j] * dt * ki[p];
+                if (j < 3) {
+                    tr[p] = psiR[p] + a[j + 1] * dt * kr[p];
+                    ti[p] = psiI[p] + a[j + 1] * dt * ki[p];
+                }
+            }
+        }
+        for (int64_t p = 0; p < nt; ++p) {
+            psiR[p] = ar[p];
+            psiI[p] = ai[p];
+        }
+        for (int q = 0; q < n_probe; ++q) {
+            probe_re[(int64_t)q * nsteps + s] = psiR[probe_idx[q]];
+            probe_im[(int64_t)q * nsteps + s] = psiI[probe_idx[q]];
+        }
+    }
+    free(tr); free(ti); free(kr); free(ki); free(ar); free(ai);
+    return rc ? -1 : 0;
+}

@@ -58,6 +58,8 @@ int    orc_spectrum(const double *re, const double *im, int64_t M, int64_t nfft,
 double orc_phase_correct(double theta, const double *c, const double *d, int m);
 int    orc_norm_energy(const double *psiR, const double *psiI, const double *V,
                        const orc_grid *g, double *norm, double *energy);
+int    orc_run_rk4(double *psiR, double *psiI, const double *V, const orc_grid *g, double dt, int64_t nsteps,
+                   int n_probe, const int64_t *probe_idx, double *probe_re, double *probe_im);
 int    orc_run_eigen(double *psiR, double *psiI, const double *V, const orc_grid *g,
                      const double *c, const double *d, int m, double dt, int64_t nsteps,
                      int n_target, const double *E, double *acc_re, double *acc_im);

@@ -41,7 +41,7 @@ struct HalfStage {
 
 struct Layout {
     size_t psi[2], V, tmp, staging, ring, counter, status, snap, partial, dout, tw[3], mult, dense[3], spec;
-    size_t eig_acc, eig_theta, eig_step, total;
+    size_t eig_acc, eig_theta, eig_step, rk[6], total;
 };
 
 // An axis uses the FFT passes when it is periodic with a power-of-two length
@@ -155,8 +155,21 @@ double stability_s_star(int m, const double *c, const double *d)
     return lo;
 }
 
+// Largest stable w dt of the configured scheme: the partitioned map's s*
+// (Eq. 25), or 2 sqrt 2 for RK4 (|1 - is - s^2/2 + is^3/6 + s^4/24| <= 1 iff
+// s^2 <= 8 on the imaginary axis).
+double scheme_s_star(int preset, int m, const double *c, const double *d)
+{
+    if (preset == SPSTD_RK4) return 2.0 * std::sqrt(2.0);
+    return stability_s_star(m, c, d);
+}
+
+// Phase advance per step of the mode with w dt = s. m = 0 is the classical
+// Runge-Kutta scheme: its factor R(-is) = 1 - is - s^2/2 + is^3/6 + s^4/24 is
+// not unimodular; the angle of exp(-i theta) is -arg R, taken in [0, pi].
 double map_angle(int m, const double *c, const double *d, double s)
 {
+    if (m == 0) return std::fabs(std::atan2(s - s * s * s / 6.0, 1.0 - 0.5 * s * s + s * s * s * s / 24.0));
     double t = 0.5 * step_trace(m, c, d, s);
     t = std::min(1.0, std::max(-1.0, t));
     return std::acos(t);
@@ -229,12 +242,14 @@ spstd_status validate(const spstd_config *cfg, std::string *why, int *m, double 
             c[l] = cfg->c[l];
             d[l] = cfg->d[l];
         }
+    } else if (cfg->preset == SPSTD_RK4) {
+        *m = 0;  // not a partitioned scheme: no c_l, d_l
     } else if (!preset_coefficients(cfg->preset, m, c, d)) {
         return bad("unknown integrator preset");
     }
     int nh = 0;
     for (int l = 0; l < *m; ++l) nh += (c[l] != 0.0) + (d[l] != 0.0);
-    if (nh == 0) return bad("all integrator coefficients are zero");
+    if (nh == 0 && cfg->preset != SPSTD_RK4) return bad("all integrator coefficients are zero");
     if (nh > kMaxHalfStages) return bad("too many nonzero coefficients");
     if (cfg->n_probe < 0 || cfg->n_probe > SPSTD_MAX_PROBES) return bad("n_probe must be 0..16");
     const int64_t ntot = cfg->n[0] * cfg->n[1] * cfg->n[2];
@@ -287,6 +302,7 @@ Layout make_layout(const spstd_config &cfg, int m)
     L.eig_acc = take(16 * (size_t)cfg.max_eigenstates * ntot);
     L.eig_theta = take(8 * SPSTD_MAX_EIGENSTATES);
     L.eig_step = take(16);  // int64 step, unsigned completion count
+    for (int k = 0; k < 6; ++k) L.rk[k] = take(cfg.preset == SPSTD_RK4 ? es * ntot : 0);  // t, h, acc (R, I)
     L.total = off;
     return L;
 }
@@ -318,12 +334,14 @@ struct spstd_ctx {
     HalfStage merged{};
     double merge_alpha = 0.0;  // c_last / (c_last + c_first)
     // eigenstate accumulation window
+    bool rk4 = false;  // classical Runge-Kutta comparison scheme
     bool eig_active = false;
     int eig_n = 0;
     int64_t eig_window = 0;
 
     void *ptr(size_t off) { return ws + off; }
-    size_t field_off(int f) const { return f == 0 ? L.psi[0] : f == 1 ? L.psi[1] : L.tmp; }
+    // fields: 0 psi_R, 1 psi_I, 2 scratch, 3..8 Runge-Kutta t_R, t_I, h_R, h_I, acc_R, acc_I
+    size_t field_off(int f) const { return f == 0 ? L.psi[0] : f == 1 ? L.psi[1] : f == 2 ? L.tmp : L.rk[f - 3]; }
 };
 
 namespace {
@@ -664,7 +682,7 @@ cudaError_t enqueue_apply(spstd_ctx *ctx, int fsrc, int fdst, int table, double 
         }
         const cpx<T> *tw = (const cpx<T> *)ctx->ptr(ctx->L.tw[ax]);
         if constexpr (sizeof(T) == 4) {
-            if (ctx->tma[ax]) {
+            if (ctx->tma[ax] && fsrc <= 2 && fdst <= 2) {
                 TmaPassArgs ta{};
                 ta.tw = (const float2 *)tw;
                 ta.mult = (const float *)(mult + off[ax]);
@@ -882,11 +900,46 @@ spstd_status prepare_kernels(spstd_ctx *ctx)
     return SPSTD_OK;
 }
 
+// One classical Runge-Kutta step (the comparison scheme of Fig. 3): four
+// stages, each H applied to the stage state's two fields by the pass kernels,
+// then the stage update; the state becomes the accumulated sum; then probes.
+template <typename T>
+cudaError_t enqueue_rk4_step(spstd_ctx *ctx, cudaStream_t s, LaunchTimer *timer = nullptr)
+{
+    const size_t bytes = sizeof(T) * ctx->ntot;
+    T *y[2] = {field_ptr<T>(ctx, 0), field_ptr<T>(ctx, 1)};
+    T *t[2] = {field_ptr<T>(ctx, 3), field_ptr<T>(ctx, 4)};
+    T *h[2] = {field_ptr<T>(ctx, 5), field_ptr<T>(ctx, 6)};
+    T *acc[2] = {field_ptr<T>(ctx, 7), field_ptr<T>(ctx, 8)};
+    const double b[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+    const double a[4] = {0.0, 0.5, 0.5, 1.0};
+    const double k = ctx->dt / ctx->cfg.hbar;
+    cudaError_t e;
+    for (int f = 0; f < 2; ++f) {
+        if ((e = cudaMemcpyAsync(t[f], y[f], bytes, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
+        if ((e = cudaMemcpyAsync(acc[f], y[f], bytes, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
+    }
+    const int tH = 2 * ctx->m;
+    for (int j = 0; j < 4; ++j) {
+        for (int f = 0; f < 2; ++f)
+            if ((e = cudaMemsetAsync(h[f], 0, bytes, s)) != cudaSuccess) return e;
+        if ((e = enqueue_apply<T>(ctx, 4, 5, tH, 1.0, 0, s, timer)) != cudaSuccess) return e;  // h_R = H t_I
+        if ((e = enqueue_apply<T>(ctx, 3, 6, tH, 1.0, 1, s, timer)) != cudaSuccess) return e;  // h_I = H t_R
+        e = Launch<T>::rk4_update(y[0], y[1], h[0], h[1], acc[0], acc[1], t[0], t[1], ctx->ntot, (T)(b[j] * k),
+                                  (T)(j < 3 ? a[j + 1] * k : 0.0), j == 3, s);
+        if (e != cudaSuccess) return e;
+    }
+    for (int f = 0; f < 2; ++f)
+        if ((e = cudaMemcpyAsync(y[f], acc[f], bytes, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
+    if (ctx->cfg.n_probe > 0) SPSTD_TIMED(timer, s, 3, Launch<T>::probe(y[0], y[1], probe_args<T>(ctx), s));
+    return cudaSuccess;
+}
+
 // A step followed by the eigenstate accumulation (every step ends at a full state).
 template <typename T>
 cudaError_t enqueue_eigen_step(spstd_ctx *ctx, cudaStream_t s, LaunchTimer *timer = nullptr)
 {
-    cudaError_t e = enqueue_steps<T>(ctx, 1, s, timer);
+    cudaError_t e = ctx->rk4 ? enqueue_rk4_step<T>(ctx, s, timer) : enqueue_steps<T>(ctx, 1, s, timer);
     if (e != cudaSuccess) return e;
     int64_t *step = (int64_t *)ctx->ptr(ctx->L.eig_step);
     SPSTD_TIMED(timer, s, 3,
@@ -902,6 +955,11 @@ spstd_status step_impl(spstd_ctx *ctx, int64_t nsteps)
     const spstd_config &cfg = ctx->cfg;
     T *psi0 = (T *)ctx->ptr(ctx->L.psi[0]);
     T *psi1 = (T *)ctx->ptr(ctx->L.psi[1]);
+    if (ctx->rk4 && !ctx->eig_active) {
+        for (int64_t i = 0; i < nsteps; ++i) SPSTD_CU(ctx, enqueue_rk4_step<T>(ctx, ctx->stream));
+        ctx->steps_taken += nsteps;
+        return SPSTD_OK;
+    }
     if (ctx->eig_active) {
         for (int64_t i = 0; i < nsteps; ++i) SPSTD_CU(ctx, enqueue_eigen_step<T>(ctx, ctx->stream));
         ctx->steps_taken += nsteps;
@@ -1034,7 +1092,7 @@ spstd_status spstd_workspace_size(const spstd_config *cfg, size_t *bytes)
     spstd_status s = validate(cfg, nullptr, &m, c, d);
     if (s != SPSTD_OK) return s;
     if (cfg->dt > 0) {
-        const double ss = stability_s_star(m, c, d);
+        const double ss = scheme_s_star(cfg->preset, m, c, d);
         if (cfg->dt > ss / w_max_of(*cfg, 0.0)) return SPSTD_EUNSTABLE;
     }
     *bytes = make_layout(*cfg, m).total;
@@ -1047,7 +1105,7 @@ spstd_status spstd_stability_limit(const spstd_config *cfg, double vmax, double 
     double c[SPSTD_MAX_STAGES], d[SPSTD_MAX_STAGES];
     spstd_status s = validate(cfg, nullptr, &m, c, d);
     if (s != SPSTD_OK) return s;
-    const double ss = stability_s_star(m, c, d);
+    const double ss = scheme_s_star(cfg->preset, m, c, d);
     if (s_star) *s_star = ss;
     if (dt_max) *dt_max = ss / w_max_of(*cfg, vmax);
     return SPSTD_OK;
@@ -1080,7 +1138,8 @@ spstd_status spstd_create(const spstd_config *cfg, void *d_workspace, size_t wor
     for (int a = 0; a < cfg->dims; ++a) ctx->sum_n += cfg->n[a];
     ctx->stream = (cudaStream_t)cfg->stream;
     for (int a = 0; a < cfg->dims; ++a) ctx->dense[a] = !axis_is_fft(*cfg, a);
-    ctx->s_star = stability_s_star(ctx->m, ctx->c, ctx->d);
+    ctx->s_star = scheme_s_star(cfg->preset, ctx->m, ctx->c, ctx->d);
+    ctx->rk4 = cfg->preset == SPSTD_RK4;
     ctx->dt_auto = !(cfg->dt > 0);
     ctx->dt = -1.0;  // forces the first table upload
     auto bail = [&](spstd_status s) {
@@ -1334,7 +1393,9 @@ template <typename T>
 spstd_status profile_impl(spstd_ctx *ctx, int64_t nsteps, double *ms, int64_t *cnt)
 {
     LaunchTimer timer;
-    if (ctx->cfg.dims == 1) {
+    if (ctx->rk4) {
+        for (int64_t i = 0; i < nsteps; ++i) SPSTD_CU(ctx, enqueue_rk4_step<T>(ctx, ctx->stream, &timer));
+    } else if (ctx->cfg.dims == 1) {
         SPSTD_CU(ctx, launch_resident<T>(ctx, nsteps, &timer));
     } else {
         if (ctx->merge && nsteps > 0) {
@@ -1445,6 +1506,8 @@ spstd_status spstd_launch_count(const spstd_ctx *ctx, int64_t nsteps, int64_t *l
     if (!ctx || !launches || nsteps < 0) return SPSTD_EINVAL;
     if (nsteps == 0) {
         *launches = 0;
+    } else if (ctx->rk4) {
+        *launches = nsteps * (8 * ctx->cfg.dims + 4 + (ctx->cfg.n_probe > 0 ? 1 : 0) + (ctx->eig_active ? 1 : 0));
     } else if (ctx->eig_active) {
         *launches = nsteps * ((int64_t)ctx->hs.size() * ctx->cfg.dims + (ctx->cfg.n_probe > 0 ? 1 : 0) + 1);
     } else if (ctx->cfg.dims == 1) {
@@ -1839,6 +1902,7 @@ spstd_status spstd_batch_add(spstd_batch *b, spstd_ctx *ctx, int *slot)
     for (int a = 0; a < ctx->cfg.dims; ++a)
         if (ctx->dense[a])
             return bfail(b, SPSTD_EUNSUPPORTED, "batches take FFT axes only (periodic, power-of-two lengths)");
+    if (ctx->rk4) return bfail(b, SPSTD_EUNSUPPORTED, "batches take the partitioned symplectic schemes only");
     for (int s = 0; s < (int)b->slots.size(); ++s) {
         if (!b->slots[s]) {
             // the member's own pending work comes first

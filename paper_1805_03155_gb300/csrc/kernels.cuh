@@ -619,6 +619,25 @@ __global__ void eigen_accum_kernel(const T *__restrict__ psiR, const T *__restri
     }
 }
 
+// One Runge-Kutta stage update (Fig. 3's comparison scheme) given hR = H t_I,
+// hI = H t_R:  a_R += cb hR, a_I -= cb hI;  and, unless last, the next stage
+// state t_R = y_R + ca hR, t_I = y_I - ca hI  (cb, ca = stage weight x dt/hbar).
+template <typename T>
+__global__ void rk4_update_kernel(const T *__restrict__ yR, const T *__restrict__ yI, const T *__restrict__ hR,
+                                  const T *__restrict__ hI, T *__restrict__ aR, T *__restrict__ aI,
+                                  T *__restrict__ tR, T *__restrict__ tI, int64_t n, T cb, T ca, int last)
+{
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        const T r = hR[p], i = hI[p];
+        aR[p] = fma(cb, r, aR[p]);
+        aI[p] = fma(-cb, i, aI[p]);
+        if (!last) {
+            tR[p] = fma(ca, r, yR[p]);
+            tI[p] = fma(-ca, i, yI[p]);
+        }
+    }
+}
+
 // Batched probe recorder: block b records member b.
 template <typename T>
 struct ProbeMember {

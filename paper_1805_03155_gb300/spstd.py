@@ -19,7 +19,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "spstd.h")
 
 SPSTD_OK, SPSTD_EINVAL, SPSTD_ENOMEM, SPSTD_ECUDA, SPSTD_EUNSTABLE = 0, 1, 2, 3, 4
 SPSTD_EDIVERGED, SPSTD_ETIMEOUT, SPSTD_ENOTREADY, SPSTD_EUNSUPPORTED = 5, 6, 7, 8
-PRESETS = {"CUSTOM": -1, "LEAPFROG": 0, "STRANG": 1, "PAPER3": 2, "FR4": 3, "SUZUKI6": 4}
+PRESETS = {"CUSTOM": -1, "LEAPFROG": 0, "STRANG": 1, "PAPER3": 2, "FR4": 3, "SUZUKI6": 4, "RK4": 5}
 PERIODIC, DIRICHLET, NEUMANN = 0, 1, 2
 MAX_STAGES = 8
 MAX_PROBES = 16
