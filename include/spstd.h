@@ -86,9 +86,12 @@ enum {
 typedef struct {
     int dims;             /* 1, 2 or 3 */
     int64_t n[3];         /* points per axis, x first.  Each used axis: a power
-                             of two, 2 <= n <= 8192 for dims == 1 and
-                             2 <= n <= 1024 otherwise, or any 2 <= n <= 256 (see
-                             bc below); unused axes: 1 */
+                             of two (periodic), 2 <= n <= 4194304 for x and
+                             2 <= n <= 1024 for y and z, or any 2 <= n <= 256
+                             (see bc below); unused axes: 1.  x lines longer
+                             than one block transforms (8192 FP32 / 4096 FP64
+                             in 1D, 1024 otherwise) take a four-step FFT
+                             through a scratch array in the workspace */
     double lo[3], hi[3];  /* periodic box per axis, hi > lo */
     double hbar, mass;    /* hbar and effective mass m* (> 0) */
     int precision;        /* 32 or 64: type of the fields and of the FFTs;

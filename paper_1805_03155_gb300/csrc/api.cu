@@ -20,6 +20,7 @@
 
 #include "../../include/spstd.h"
 #include "launch.cuh"
+#include "longline.h"
 #include "pass_tma_launch.h"
 #include "spectrum.h"
 
@@ -41,7 +42,7 @@ struct HalfStage {
 
 struct Layout {
     size_t psi[2], V, tmp, staging, ring, counter, status, snap, partial, dout, tw[3], mult, dense[3], spec;
-    size_t eig_acc, eig_theta, eig_step, rk[6], total;
+    size_t eig_acc, eig_theta, eig_step, rk[6], lscr, total;
 };
 
 // An axis uses the FFT passes when it is periodic with a power-of-two length
@@ -53,6 +54,18 @@ bool axis_is_fft(const spstd_config &cfg, int a)
     const int64_t lim = cfg.dims == 1 ? (cfg.precision == 32 ? 8192 : 4096) : 1024;
     return n >= 2 && n <= lim;
 }
+
+// The x axis of a periodic power-of-two length beyond the on-chip limit runs
+// the four-step pass (up to 2^22 points).
+bool axis_is_long(const spstd_config &cfg, int a)
+{
+    const int64_t n = cfg.n[a];
+    return a == 0 && cfg.bc[a] == SPSTD_PERIODIC && (n & (n - 1)) == 0 && !axis_is_fft(cfg, a) && n <= kMaxLongN;
+}
+
+// Entries of an axis in each multiplier row (the four-step pass computes its
+// multipliers from the wrapped index instead).
+int64_t table_len(const spstd_config &cfg, int a) { return a < cfg.dims && !axis_is_long(cfg, a) ? cfg.n[a] : 0; }
 
 // Points per cell length: periodic L/n, Dirichlet L/(n+1), Neumann L/(n-1).
 double axis_spacing(const spstd_config &cfg, int a)
@@ -226,10 +239,10 @@ spstd_status validate(const spstd_config *cfg, std::string *why, int *m, double 
         }
     }
     for (int a = 0; a < cfg->dims; ++a) {
-        if (!axis_is_fft(*cfg, a) && cfg->n[a] > SPSTD_MAX_DENSE_N) {
+        if (!axis_is_fft(*cfg, a) && !axis_is_long(*cfg, a) && cfg->n[a] > SPSTD_MAX_DENSE_N) {
             if (why)
-                *why = "axis not supported: FFT axes are periodic powers of two (1D <= 8192 FP32 / 4096 FP64, "
-                       "2D/3D <= 1024); other axes need n <= 256";
+                *why = "axis not supported: FFT axes are periodic powers of two (x <= 4194304; y, z <= 1024); "
+                       "other axes need n <= 256";
             return SPSTD_EUNSUPPORTED;
         }
     }
@@ -292,17 +305,26 @@ Layout make_layout(const spstd_config &cfg, int m)
     L.dout = take(8 * 8);
     int64_t sum_n = 0;
     for (int a = 0; a < 3; ++a) {
-        L.tw[a] = take(a < cfg.dims ? 2 * es * cfg.n[a] : 0);
-        if (a < cfg.dims) sum_n += cfg.n[a];
+        int64_t ntw = a < cfg.dims ? cfg.n[a] : 0;
+        if (a < cfg.dims && axis_is_long(cfg, a)) {
+            int N1, N2;
+            long_split(cfg.n[a], &N1, &N2);
+            ntw = N1 + 2 * (int64_t)N2;  // W_N1, W_N2, W_N[k < N2]
+        }
+        L.tw[a] = take(2 * es * ntw);
+        sum_n += table_len(cfg, a);
     }
     L.mult = take(es * (size_t)(2 * m + 2) * sum_n);  // rows: c_l, d_l, H, merged boundary
     for (int a = 0; a < 3; ++a)
-        L.dense[a] = take(a < cfg.dims && !axis_is_fft(cfg, a) ? es * (size_t)cfg.n[a] * cfg.n[a] : 0);
+        L.dense[a] = take(a < cfg.dims && !axis_is_fft(cfg, a) && !axis_is_long(cfg, a)
+                              ? es * (size_t)cfg.n[a] * cfg.n[a] : 0);
     L.spec = take(spectrum_scratch_bytes(effective_max_nfft(cfg), cfg.probe_capacity));
     L.eig_acc = take(16 * (size_t)cfg.max_eigenstates * ntot);
     L.eig_theta = take(8 * SPSTD_MAX_EIGENSTATES);
     L.eig_step = take(16);  // int64 step, unsigned completion count
     for (int k = 0; k < 6; ++k) L.rk[k] = take(cfg.preset == SPSTD_RK4 ? es * ntot : 0);  // t, h, acc (R, I)
+    // four-step scratch: one complex line per pair of x lines
+    L.lscr = take(axis_is_long(cfg, 0) ? 2 * es * (size_t)((cfg.n[1] * cfg.n[2] + 1) / 2) * cfg.n[0] : 0);
     L.total = off;
     return L;
 }
@@ -329,6 +351,9 @@ struct spstd_ctx {
     CUtensorMap tmap[3][3];
     spstd_batch *batch = nullptr;  // batch this context is a member of
     bool dense[3] = {false, false, false};  // axis applies the dense operator
+    bool long_x = false;                    // x axis runs the four-step pass
+    int N1 = 0, N2 = 0;                     // its split N = N1 N2
+    int64_t tab_off[3] = {0, 0, 0};         // axis offsets within a multiplier row
     // step-boundary merge of the last and first half-stages (same field)
     bool merge = false;
     HalfStage merged{};
@@ -433,40 +458,56 @@ std::vector<double> dense_operator(const spstd_config &cfg, int axis)
     return D;
 }
 
+// The factor a of multiplier row t (the row holds a k^2/N): c_l dt hbar/2m*
+// (row 2l), -d_l dt hbar/2m* (row 2l+1), hbar^2/2m* (H), merged boundary.
+double table_a(const spstd_ctx *ctx, int t)
+{
+    const spstd_config &cfg = ctx->cfg;
+    const int m = ctx->m;
+    if (t == 2 * m + 1) return ctx->merge ? ctx->merged.a : 0.0;
+    if (t == 2 * m) return cfg.hbar * cfg.hbar / (2.0 * cfg.mass);
+    return (t & 1) ? -ctx->d[t / 2] * ctx->dt * cfg.hbar / (2.0 * cfg.mass)
+                   : +ctx->c[t / 2] * ctx->dt * cfg.hbar / (2.0 * cfg.mass);
+}
+
 template <typename T>
 spstd_status upload_tables(spstd_ctx *ctx)
 {
     const spstd_config &cfg = ctx->cfg;
     // twiddles W_N[k] = exp(-2 pi i k/N), FP64 then rounded
+    std::vector<std::vector<T>> tws(3);
     for (int a = 0; a < cfg.dims; ++a) {
-        const int64_t n = cfg.n[a];
-        std::vector<T> tw(2 * n);
-        for (int64_t k = 0; k < n; ++k) {
-            const double ang = 2.0 * kPi * (double)k / (double)n;
-            tw[2 * k] = (T)std::cos(ang);
-            tw[2 * k + 1] = (T)(-std::sin(ang));
+        std::vector<T> &tw = tws[a];
+        // W_n[k] = exp(-2 pi i k/n), k < count, appended
+        auto append = [&](int64_t n, int64_t count) {
+            for (int64_t k = 0; k < count; ++k) {
+                const double ang = 2.0 * kPi * (double)k / (double)n;
+                tw.push_back((T)std::cos(ang));
+                tw.push_back((T)(-std::sin(ang)));
+            }
+        };
+        if (a == 0 && ctx->long_x) {
+            append(ctx->N1, ctx->N1);
+            append(ctx->N2, ctx->N2);
+            append(cfg.n[0], ctx->N2);
+        } else {
+            append(cfg.n[a], cfg.n[a]);
         }
-        SPSTD_CU(ctx, cudaMemcpyAsync(ctx->ptr(ctx->L.tw[a]), tw.data(), sizeof(T) * 2 * n, cudaMemcpyHostToDevice,
+        SPSTD_CU(ctx, cudaMemcpyAsync(ctx->ptr(ctx->L.tw[a]), tw.data(), sizeof(T) * tw.size(), cudaMemcpyHostToDevice,
                                       ctx->stream));
     }
     // per half-stage (and H) multipliers a k_d^2(n)/N_d, FP64 then rounded
     const int ntab = 2 * ctx->m + 2;
     std::vector<double> a_of(ntab, 0.0);
-    for (int l = 0; l < ctx->m; ++l) {
-        a_of[2 * l] = +ctx->c[l] * ctx->dt * cfg.hbar / (2.0 * cfg.mass);
-        a_of[2 * l + 1] = -ctx->d[l] * ctx->dt * cfg.hbar / (2.0 * cfg.mass);
-    }
-    a_of[2 * ctx->m] = cfg.hbar * cfg.hbar / (2.0 * cfg.mass);
-    a_of[2 * ctx->m + 1] = ctx->merge ? ctx->merged.a : 0.0;
+    for (int t = 0; t < ntab; ++t) a_of[t] = table_a(ctx, t);
     std::vector<T> mult((size_t)ntab * ctx->sum_n);
     for (int t = 0; t < ntab; ++t) {
-        int64_t off = 0;
         for (int a = 0; a < cfg.dims; ++a) {
-            const int64_t n = cfg.n[a];
+            const int64_t n = table_len(cfg, a);
             const double L = cfg.hi[a] - cfg.lo[a];
             for (int64_t j = 0; j < n; ++j)
-                mult[(size_t)t * ctx->sum_n + off + j] = (T)(a_of[t] * k2_of(j, n, L, cfg.nyquist_zero) / (double)n);
-            off += n;
+                mult[(size_t)t * ctx->sum_n + ctx->tab_off[a] + j] =
+                    (T)(a_of[t] * k2_of(j, n, L, cfg.nyquist_zero) / (double)n);
         }
     }
     SPSTD_CU(ctx, cudaMemcpyAsync(ctx->ptr(ctx->L.mult), mult.data(), sizeof(T) * mult.size(),
@@ -646,11 +687,31 @@ cudaError_t enqueue_apply(spstd_ctx *ctx, int fsrc, int fdst, int table, double 
     T *dst = field_ptr<T>(ctx, fdst);
     const T *mult = (const T *)ctx->ptr(ctx->L.mult) + (size_t)table * ctx->sum_n;
     const int64_t n0 = cfg.n[0], n1 = cfg.n[1], n2 = cfg.n[2];
-    const int64_t off[3] = {0, n0, n0 + n1};
+    const int64_t *off = ctx->tab_off;
     int *status = (int *)ctx->ptr(ctx->L.status);
     for (int ax = 0; ax < cfg.dims; ++ax) {
         const int rev = ax == 1 ? !reverse : reverse;
         const int64_t N = cfg.n[ax];
+        if (ax == 0 && ctx->long_x) {
+            LongArgs<T> la{};
+            la.src = src;
+            la.dst = dst;
+            la.V = (const T *)ctx->ptr(ctx->L.V);
+            la.C = (cpx<T> *)ctx->ptr(ctx->L.lscr);
+            la.tw1 = (const cpx<T> *)ctx->ptr(ctx->L.tw[0]);
+            la.tw2 = la.tw1 + ctx->N1;
+            la.twl = la.tw2 + ctx->N2;
+            const double L = cfg.hi[0] - cfg.lo[0];
+            la.scale = (T)(table_a(ctx, table) * (2.0 * kPi / L) * (2.0 * kPi / L) / (double)N);
+            la.bV = (T)bV;
+            la.nyquist_zero = cfg.nyquist_zero;
+            la.N1 = ctx->N1;
+            la.N2 = ctx->N2;
+            la.n_rows = n1 * n2;
+            la.n_pairs = (n1 * n2 + 1) / 2;
+            for (int k = 0; k < 3; ++k) SPSTD_TIMED(timer, s, 0, launch_long_x<T>(la, s, k));
+            continue;
+        }
         if (ctx->dense[ax]) {
             DenseArgs<T> da{};
             da.src = src;
@@ -821,6 +882,13 @@ cudaError_t enqueue_merged_piece(spstd_ctx *ctx, int piece, int64_t units, cudaS
 }
 
 // Kernel launches enqueue_steps(n) issues.
+// Kernel launches of one H-apply: one per axis, three for a four-step x axis.
+int64_t apply_launches(const spstd_ctx *ctx) { return ctx->cfg.dims + (ctx->long_x ? 2 : 0); }
+
+// A 1D grid runs all steps of a call in one resident launch unless its line
+// is too long for one block.
+bool resident_path(const spstd_ctx *ctx) { return ctx->cfg.dims == 1 && !ctx->long_x; }
+
 int64_t launches_for_steps(const spstd_ctx *ctx, int64_t n)
 {
     if (n <= 0) return 0;
@@ -828,7 +896,7 @@ int64_t launches_for_steps(const spstd_ctx *ctx, int64_t n)
     const int64_t halfstages = ctx->merge ? n * nh - (n - 1) : n * nh;
     // a merged boundary records its probe with a snapshot and an interpolating recorder
     const int64_t probe = ctx->cfg.n_probe > 0 ? (ctx->merge ? 2 * n - 1 : n) : 0;
-    return halfstages * ctx->cfg.dims + probe;
+    return halfstages * apply_launches(ctx) + probe;
 }
 
 template <typename T>
@@ -891,7 +959,8 @@ spstd_status prepare_kernels(spstd_ctx *ctx)
 {
     const spstd_config &cfg = ctx->cfg;
     PassArgs<T> none{};
-    if (!ctx->dense[0]) SPSTD_CU(ctx, Launch<T>::xpass((int)cfg.n[0], none, ctx->stream));
+    if (ctx->long_x) SPSTD_CU(ctx, prepare_long_x<T>(ctx->N1, ctx->N2));
+    else if (!ctx->dense[0]) SPSTD_CU(ctx, Launch<T>::xpass((int)cfg.n[0], none, ctx->stream));
     none.nx = (int)cfg.n[0];
     if (cfg.dims > 1 && !ctx->dense[1]) SPSTD_CU(ctx, Launch<T>::spass((int)cfg.n[1], none, ctx->stream));
     if (cfg.dims == 3 && !ctx->dense[2]) SPSTD_CU(ctx, Launch<T>::spass((int)cfg.n[2], none, ctx->stream));
@@ -965,7 +1034,7 @@ spstd_status step_impl(spstd_ctx *ctx, int64_t nsteps)
         ctx->steps_taken += nsteps;
         return SPSTD_OK;
     }
-    if (cfg.dims == 1) {
+    if (resident_path(ctx)) {
         SPSTD_CU(ctx, launch_resident<T>(ctx, nsteps, nullptr));
         ctx->steps_taken += nsteps;
         return SPSTD_OK;
@@ -1135,9 +1204,14 @@ spstd_status spstd_create(const spstd_config *cfg, void *d_workspace, size_t wor
     }
     ctx->ws = (unsigned char *)d_workspace;
     ctx->ntot = cfg->n[0] * cfg->n[1] * cfg->n[2];
-    for (int a = 0; a < cfg->dims; ++a) ctx->sum_n += cfg->n[a];
+    for (int a = 0; a < cfg->dims; ++a) {
+        ctx->tab_off[a] = ctx->sum_n;
+        ctx->sum_n += table_len(*cfg, a);
+    }
+    ctx->long_x = axis_is_long(*cfg, 0);
+    if (ctx->long_x) long_split(cfg->n[0], &ctx->N1, &ctx->N2);
     ctx->stream = (cudaStream_t)cfg->stream;
-    for (int a = 0; a < cfg->dims; ++a) ctx->dense[a] = !axis_is_fft(*cfg, a);
+    for (int a = 0; a < cfg->dims; ++a) ctx->dense[a] = !axis_is_fft(*cfg, a) && !axis_is_long(*cfg, a);
     ctx->s_star = scheme_s_star(cfg->preset, ctx->m, ctx->c, ctx->d);
     ctx->rk4 = cfg->preset == SPSTD_RK4;
     ctx->dt_auto = !(cfg->dt > 0);
@@ -1395,7 +1469,7 @@ spstd_status profile_impl(spstd_ctx *ctx, int64_t nsteps, double *ms, int64_t *c
     LaunchTimer timer;
     if (ctx->rk4) {
         for (int64_t i = 0; i < nsteps; ++i) SPSTD_CU(ctx, enqueue_rk4_step<T>(ctx, ctx->stream, &timer));
-    } else if (ctx->cfg.dims == 1) {
+    } else if (resident_path(ctx)) {
         SPSTD_CU(ctx, launch_resident<T>(ctx, nsteps, &timer));
     } else {
         if (ctx->merge && nsteps > 0) {
@@ -1507,16 +1581,16 @@ spstd_status spstd_launch_count(const spstd_ctx *ctx, int64_t nsteps, int64_t *l
     if (nsteps == 0) {
         *launches = 0;
     } else if (ctx->rk4) {
-        *launches = nsteps * (8 * ctx->cfg.dims + 4 + (ctx->cfg.n_probe > 0 ? 1 : 0) + (ctx->eig_active ? 1 : 0));
+        *launches = nsteps * (8 * apply_launches(ctx) + 4 + (ctx->cfg.n_probe > 0 ? 1 : 0) + (ctx->eig_active ? 1 : 0));
     } else if (ctx->eig_active) {
-        *launches = nsteps * ((int64_t)ctx->hs.size() * ctx->cfg.dims + (ctx->cfg.n_probe > 0 ? 1 : 0) + 1);
-    } else if (ctx->cfg.dims == 1) {
+        *launches = nsteps * ((int64_t)ctx->hs.size() * apply_launches(ctx) + (ctx->cfg.n_probe > 0 ? 1 : 0) + 1);
+    } else if (resident_path(ctx)) {
         *launches = 1;
     } else {
         if (ctx->merge) {
             // n (h - 1) + 1 half-stages; 2 (n - 1) + 1 probe launches
             const int64_t nh = (int64_t)ctx->hs.size();
-            *launches = (nsteps * (nh - 1) + 1) * ctx->cfg.dims + (ctx->cfg.n_probe > 0 ? 2 * nsteps - 1 : 0);
+            *launches = (nsteps * (nh - 1) + 1) * apply_launches(ctx) + (ctx->cfg.n_probe > 0 ? 2 * nsteps - 1 : 0);
         } else {
             // graph-replayed chunks of kGraphSteps, then the remainder
             const int64_t reps = nsteps >= kGraphSteps ? nsteps / kGraphSteps : 0;
@@ -1903,6 +1977,7 @@ spstd_status spstd_batch_add(spstd_batch *b, spstd_ctx *ctx, int *slot)
         if (ctx->dense[a])
             return bfail(b, SPSTD_EUNSUPPORTED, "batches take FFT axes only (periodic, power-of-two lengths)");
     if (ctx->rk4) return bfail(b, SPSTD_EUNSUPPORTED, "batches take the partitioned symplectic schemes only");
+    if (ctx->long_x) return bfail(b, SPSTD_EUNSUPPORTED, "batches take lines of at most 8192 (1D) / 1024 points");
     for (int s = 0; s < (int)b->slots.size(); ++s) {
         if (!b->slots[s]) {
             // the member's own pending work comes first

@@ -74,8 +74,10 @@ def test_validation_codes(L):
     ]
     for cfg in bad:
         assert _status(cfg)[0] == spstd.SPSTD_EINVAL
-    too_long = spstd.make_config(2, (2048, 16), (0, 0), (1, 1))
-    assert _status(too_long)[0] == spstd.SPSTD_EUNSUPPORTED
+    long_x = spstd.make_config(2, (2048, 16), (0, 0), (1, 1))      # x beyond one block: four-step pass
+    assert _status(long_x)[0] == spstd.SPSTD_OK
+    for n in [(4096, 2048), (1 << 23,)]:                          # long y; x beyond 2^22
+        assert _status(spstd.make_config(len(n), n, (0,) * len(n), (1,) * len(n)))[0] == spstd.SPSTD_EUNSUPPORTED
     odd_long = spstd.make_config(1, (300,), (0,), (1,))          # not a power of two, > 256
     assert _status(odd_long)[0] == spstd.SPSTD_EUNSUPPORTED
     walls = spstd.make_config(3, (9, 12, 100), (0,) * 3, (1,) * 3, bc=(1, 2, 0))
