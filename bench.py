@@ -139,14 +139,21 @@ TRAFFIC_SOURCES = ["paper_1805_03155_gb300/csrc/pass_tma.cuh", "paper_1805_03155
                    "paper_1805_03155_gb300/csrc/tma.cuh", "paper_1805_03155_gb300/csrc/pass_tma_launch.h"]
 
 
-def measured_traffic(workload, kernel):
+def measured_traffic(workload, kernel, schedule=0):
+    """Recorded traffic of the default (pipelined) kernel; None for another
+    schedule or once the kernel sources have changed."""
     import hashlib
+    if schedule != 0:
+        return None
     h = hashlib.sha256()
     for f in TRAFFIC_SOURCES:
         h.update(open(os.path.join(ROOT, f), "rb").read())
     if h.hexdigest()[:16] != MEASURED_TRAFFIC["source_hash"]:
         return None
     return MEASURED_TRAFFIC.get(workload, {}).get(kernel)
+
+
+KIND_AXIS = {"x_pass": 0, "y_pass": 1, "z_pass": 2}
 
 
 def algorithmic_bytes(kind, n_total, es):
@@ -212,13 +219,25 @@ def batched_vs_plain(count=512, steps=20, precision=32, local=0):
     b = spstd.Batch(count + 1, device=local, stream=stream)
     for s in solvers:
         b.spstd_batch_add(s)
-    b.spstd_batch_step(steps)
-    torch.cuda.synchronize()
-    ev[2].record(stream)
-    b.spstd_batch_step(steps)
-    ev[3].record(stream)
-    torch.cuda.synchronize()
-    batch_ms = ev[2].elapsed_time(ev[3])
+
+    def timed_batch():
+        b.spstd_batch_step(steps)  # warm-up: captures the batch graph
+        torch.cuda.synchronize()
+        ev[2].record(stream)
+        b.spstd_batch_step(steps)
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+        return ev[2].elapsed_time(ev[3])
+
+    default_ms = timed_batch()
+    # autotuned schedules per member shape (timed on the members' scratch fields)
+    t_tune = time.perf_counter()
+    b.spstd_batch_tune(reps=3)
+    tune_s = time.perf_counter() - t_tune
+    shapes = sorted({(p.dims, tuple(p.n)) for p in probs if p.dims > 1})
+    tuned = {"%dd:%s" % (d, "x".join(str(v) for v in n[:d])): b.spstd_batch_get_schedule(precision, d, n)[:d]
+             for d, n in shapes}
+    batch_ms = timed_batch()
     launches = b.spstd_batch_launch_count(steps)
     norms = [s.spstd_energy_norm()[0] for s in solvers[:: max(1, count // 16)]]
     b.close()
@@ -230,7 +249,10 @@ def batched_vs_plain(count=512, steps=20, precision=32, local=0):
         "grid_points": pts,
         "steps": steps,
         "batched": {"value": pts * steps / (batch_ms * 1e-3), "ms": batch_ms,
-                    "solves_per_s_5000_steps": count / (batch_ms * 1e-3 * 5000 / steps), "gpu_launches": launches},
+                    "solves_per_s_5000_steps": count / (batch_ms * 1e-3 * 5000 / steps), "gpu_launches": launches,
+                    "schedules": tuned, "tune_s": tune_s,
+                    "default_schedule_ms": default_ms,
+                    "default_schedule_value": pts * steps / (default_ms * 1e-3)},
         "plain": {"value": pts * steps / (plain_ms * 1e-3), "ms": plain_ms,
                   "solves_per_s_5000_steps": count / (plain_ms * 1e-3 * 5000 / steps), "gpu_launches": plain_launches},
         "speedup": plain_ms / batch_ms,
@@ -394,6 +416,9 @@ def main():
     stream = torch.cuda.Stream(device=local)
     s = spstd.solver_for(problem, precision=prec, probe_capacity=total_steps, stream=stream, device=local)
     N = problem.n_total
+    # autotune the pass schedules on this grid (outside the timed region)
+    tune_ms = s.spstd_tune(reps=10)
+    schedules = [s.spstd_get_schedule(a) for a in range(problem.dims)]
 
     # warm-up (also captures the step graph)
     s.spstd_step(args.warmup)
@@ -496,6 +521,8 @@ def main():
                 "l2_policy": "inputs larger than L2 (psi_R, psi_I, V = 3 x %d MB), no flush" % (N * es >> 20)
                              if 3 * N * es > 129 * 2 ** 20 else "L2-resident grid: not flushed between steps",
                 "parallelism": f"replicas{ws}",
+                "schedules": schedules,
+                "schedule_ms": [[round(float(t), 5) for t in row] for row in tune_ms[: problem.dims]],
             },
             "clocks": clk,
             "gpu_launches": int(launches),
@@ -507,7 +534,8 @@ def main():
                 "unit": "GB/s",
                 "frac": achieved / peak,
                 "peak_source": f"{peak_src} hbm_gbs (burst copy)",
-                "traffic": measured_traffic(args.workload, dom),
+                "traffic": measured_traffic(args.workload, dom,
+                                            schedules[KIND_AXIS[dom]] if dom in KIND_AXIS else 0),
                 "algorithmic_bytes_per_launch": abytes,
                 "avg_launch_ms": dom_ms,
                 "step_algorithmic_bytes": step_bytes,

@@ -229,6 +229,32 @@ spstd_status spstd_launch_count(const spstd_ctx *ctx, int64_t nsteps, int64_t *l
 #define SPSTD_KERNEL_KINDS 5
 spstd_status spstd_profile_steps(spstd_ctx *ctx, int64_t nsteps, double *ms, int64_t *cnt);
 
+/* Schedules: the radix and tile plan of an axis's pass kernel (no effect on
+ * what is computed; Eq. 10's transform in a different shape).
+ *   0  the axis's default kernel (the pipelined TMA pass for FP32 2D/3D axes
+ *      of 64..256 points, else the plain pass: 16 FP32 / 8 FP64 points per
+ *      thread, about 256 threads per block)
+ *   1  plain pass, half the lines per block
+ *   2  plain pass, twice the lines per block
+ *   3  plain pass, half the points per thread (one radix lower per stage)
+ *   4  plain pass, default plan (listed only where 0 is the TMA pass)
+ * Schedules 1..3 exist for FFT axes of 32..512 points.  0, 1, 2 and 4 give
+ * bit-identical results on plain axes; 3 changes the rounding (FP32 ~1e-7).
+ * spstd_schedule_candidates lists the schedules axis (0..dims-1) can run in
+ * list[0..*count) (list holds SPSTD_SCHEDULES ints).  spstd_set_schedule
+ * selects one (SPSTD_EINVAL if not a candidate); the next step re-captures its
+ * graph.  spstd_tune times every candidate of every axis on this context's
+ * grid -- H applied to psi_I into the scratch field, once to warm up then reps
+ * times, on the context's stream -- keeps the fastest per axis and, when ms is
+ * not NULL, writes the mean milliseconds per pass to ms[axis * SPSTD_SCHEDULES
+ * + schedule] (-1 where not a candidate).  It synchronises and leaves psi_R,
+ * psi_I, the probes and the step count unchanged. */
+#define SPSTD_SCHEDULES 5
+spstd_status spstd_schedule_candidates(const spstd_ctx *ctx, int axis, int *list, int *count);
+spstd_status spstd_get_schedule(const spstd_ctx *ctx, int axis, int *schedule);
+spstd_status spstd_set_schedule(spstd_ctx *ctx, int axis, int schedule);
+spstd_status spstd_tune(spstd_ctx *ctx, int reps, double *ms);
+
 /* Norm without device allocation (the paper has no counterpart: this is a
  * service for callers that may not allocate device memory where they call).
  * Computes *d_norm = cell_volume * sum_i (psiR[i]^2 + psiI[i]^2) in FP64, in a
@@ -299,6 +325,15 @@ spstd_status spstd_batch_sync(spstd_batch *b);
 /* Kernel launches one spstd_batch_step(b, nsteps) runs (graph nodes included). */
 spstd_status spstd_batch_launch_count(const spstd_batch *b, int64_t nsteps, int64_t *launches);
 const char *spstd_batch_last_error(const spstd_batch *b);
+/* Autotunes the batched passes: for every 2D/3D member shape and axis, times
+ * the batched pass under schedules 0..3 (0 = the default plain plan) over all
+ * members of that shape -- H applied into each member's scratch field, once to
+ * warm up then reps times -- and keeps the fastest.  The choice is kept per
+ * shape (precision, dims, n) for as long as the batch lives, including members
+ * added later; the states are not touched.  Synchronises the batch stream. */
+spstd_status spstd_batch_tune(spstd_batch *b, int reps);
+/* The batch's schedules for a member shape (0 where not tuned); n: 3 sizes. */
+spstd_status spstd_batch_get_schedule(const spstd_batch *b, int precision, int dims, const int64_t *n, int *schedule);
 
 /* Human-readable text of the last failure on ctx (never NULL). */
 const char *spstd_last_error(const spstd_ctx *ctx);

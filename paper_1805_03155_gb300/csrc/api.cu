@@ -22,6 +22,7 @@
 #include "launch.cuh"
 #include "longline.h"
 #include "pass_tma_launch.h"
+#include "sched.h"
 #include "spectrum.h"
 
 using namespace spstd;
@@ -354,6 +355,7 @@ struct spstd_ctx {
     bool long_x = false;                    // x axis runs the four-step pass
     int N1 = 0, N2 = 0;                     // its split N = N1 N2
     int64_t tab_off[3] = {0, 0, 0};         // axis offsets within a multiplier row
+    int sched[3] = {0, 0, 0};               // pass schedule per axis (sched.h)
     // step-boundary merge of the last and first half-stages (same field)
     bool merge = false;
     HalfStage merged{};
@@ -680,7 +682,7 @@ double table_scale(const spstd_ctx *ctx, int table)
 // 2 scratch), multiplier set `table`; the V term rides on the x pass.
 template <typename T>
 cudaError_t enqueue_apply(spstd_ctx *ctx, int fsrc, int fdst, int table, double bV, int reverse, cudaStream_t s,
-                          LaunchTimer *timer = nullptr)
+                          LaunchTimer *timer = nullptr, int only_axis = -1)
 {
     const spstd_config &cfg = ctx->cfg;
     const T *src = field_ptr<T>(ctx, fsrc);
@@ -690,8 +692,10 @@ cudaError_t enqueue_apply(spstd_ctx *ctx, int fsrc, int fdst, int table, double 
     const int64_t *off = ctx->tab_off;
     int *status = (int *)ctx->ptr(ctx->L.status);
     for (int ax = 0; ax < cfg.dims; ++ax) {
+        if (only_axis >= 0 && ax != only_axis) continue;
         const int rev = ax == 1 ? !reverse : reverse;
         const int64_t N = cfg.n[ax];
+        const int sv = ctx->sched[ax];
         if (ax == 0 && ctx->long_x) {
             LongArgs<T> la{};
             la.src = src;
@@ -743,7 +747,7 @@ cudaError_t enqueue_apply(spstd_ctx *ctx, int fsrc, int fdst, int table, double 
         }
         const cpx<T> *tw = (const cpx<T> *)ctx->ptr(ctx->L.tw[ax]);
         if constexpr (sizeof(T) == 4) {
-            if (ctx->tma[ax] && fsrc <= 2 && fdst <= 2) {
+            if (ctx->tma[ax] && sv == 0 && fsrc <= 2 && fdst <= 2) {
                 TmaPassArgs ta{};
                 ta.tw = (const float2 *)tw;
                 ta.mult = (const float *)(mult + off[ax]);
@@ -775,13 +779,15 @@ cudaError_t enqueue_apply(spstd_ctx *ctx, int fsrc, int fdst, int table, double 
             a.bV = (T)bV;
             a.use_V = 1;
             a.n_rows = n1 * n2;
-            SPSTD_TIMED(timer, s, 0, Launch<T>::xpass((int)N, a, s));
+            SPSTD_TIMED(timer, s, 0,
+                        (sv >= 1 && sv <= 3) ? xpass_sched<T>((int)N, sv, a, s) : Launch<T>::xpass((int)N, a, s));
         } else {
             a.stride = ax == 1 ? n0 : n0 * n1;
             a.outer_stride = ax == 1 ? n0 * n1 : n0;
             a.n_outer = ax == 1 ? n2 : n1;
             a.nx = (int)n0;
-            SPSTD_TIMED(timer, s, ax, Launch<T>::spass((int)N, a, s));
+            SPSTD_TIMED(timer, s, ax,
+                        (sv >= 1 && sv <= 3) ? spass_sched<T>((int)N, sv, a, s) : Launch<T>::spass((int)N, a, s));
         }
     }
     return cudaSuccess;
@@ -964,8 +970,15 @@ spstd_status prepare_kernels(spstd_ctx *ctx)
     none.nx = (int)cfg.n[0];
     if (cfg.dims > 1 && !ctx->dense[1]) SPSTD_CU(ctx, Launch<T>::spass((int)cfg.n[1], none, ctx->stream));
     if (cfg.dims == 3 && !ctx->dense[2]) SPSTD_CU(ctx, Launch<T>::spass((int)cfg.n[2], none, ctx->stream));
-    for (int ax = 0; ax < cfg.dims; ++ax)
+    for (int ax = 0; ax < cfg.dims; ++ax) {
         if (ctx->tma[ax]) SPSTD_CU(ctx, prepare_pass_tma(ax, (int)cfg.n[ax]));
+        const int sv = ctx->sched[ax];
+        if (sv >= 1 && sv <= 3) {
+            PassArgs<T> z{};
+            SPSTD_CU(ctx, ax == 0 ? xpass_sched<T>((int)cfg.n[ax], sv, z, ctx->stream)
+                                  : spass_sched<T>((int)cfg.n[ax], sv, z, ctx->stream));
+        }
+    }
     return SPSTD_OK;
 }
 
@@ -1634,11 +1647,19 @@ struct BatchGroupND {
     std::vector<int> slots;
     int nh;
     int tiles[3];
+    int sched[3];      // pass schedule per axis (0..3, sched.h)
     size_t args_off;   // PassArgs<T> [nh * dims][M]
     size_t probe_off;  // ProbeMember<T> [M]
 };
 
 }  // namespace
+
+// A schedule the batch autotuner chose for one member shape.
+struct TunedShape {
+    int precision, dims;
+    int64_t n[3];
+    int sched[3];
+};
 
 struct spstd_batch {
     int device = 0;
@@ -1655,6 +1676,8 @@ struct spstd_batch {
     bool dirty = true;
     std::vector<BatchGroup1D> g1;
     std::vector<BatchGroupND> gn;
+    std::vector<TunedShape> tuned;
+    size_t img_bytes = 0;  // descriptor image size (the tuner's scratch descriptors follow it)
     cudaGraphExec_t gexec = nullptr;
     std::string err;
 };
@@ -1685,7 +1708,7 @@ PassArgs<T> member_pass_args(spstd_ctx *ctx, const HalfStage &h, int ax)
 {
     const spstd_config &cfg = ctx->cfg;
     const int64_t n0 = cfg.n[0], n1 = cfg.n[1], n2 = cfg.n[2];
-    const int64_t off[3] = {0, n0, n0 + n1};
+    const int64_t *off = ctx->tab_off;
     PassArgs<T> a{};
     a.src = field_ptr<T>(ctx, 1 - h.dst);
     a.dst = field_ptr<T>(ctx, h.dst);
@@ -1738,6 +1761,27 @@ size_t put(std::vector<unsigned char> &img, const void *src, size_t bytes)
     return off;
 }
 
+// Blocks per member of a batched pass of axis ax under schedule v.
+template <typename T>
+int group_tiles(const BatchGroupND &g, int ax, int v)
+{
+    if (ax == 0)
+        return v ? xpass_tiles_sched<T>((int)g.n[0], v, g.n[1] * g.n[2])
+                 : Launch<T>::xpass_tiles((int)g.n[0], g.n[1] * g.n[2]);
+    const int64_t outer = ax == 1 ? g.n[2] : g.n[1];
+    return v ? spass_tiles_sched<T>((int)g.n[ax], v, (int)g.n[0], outer)
+             : Launch<T>::spass_tiles((int)g.n[ax], (int)g.n[0], outer);
+}
+
+// One batched pass of axis ax under schedule v (no work: raises the smem limit).
+template <typename T>
+cudaError_t group_pass(const BatchGroupND &g, int ax, int v, const PassArgs<T> *a, int M, int tiles, cudaStream_t s)
+{
+    const int N = (int)g.n[ax];
+    if (ax == 0) return v ? xpass_batch_sched<T>(N, v, a, M, tiles, s) : Launch<T>::xpass_batch(N, a, M, tiles, s);
+    return v ? spass_batch_sched<T>(N, v, a, M, tiles, s) : Launch<T>::spass_batch(N, a, M, tiles, s);
+}
+
 template <typename T>
 void build_nd_descriptors(spstd_batch *b, BatchGroupND &g, std::vector<unsigned char> &img)
 {
@@ -1755,9 +1799,7 @@ void build_nd_descriptors(spstd_batch *b, BatchGroupND &g, std::vector<unsigned 
     }
     g.args_off = put(img, args.data(), sizeof(PassArgs<T>) * args.size());
     g.probe_off = put(img, pm.data(), sizeof(ProbeMember<T>) * pm.size());
-    g.tiles[0] = Launch<T>::xpass_tiles((int)g.n[0], g.n[1] * g.n[2]);
-    g.tiles[1] = g.dims > 1 ? Launch<T>::spass_tiles((int)g.n[1], (int)g.n[0], g.n[2]) : 0;
-    g.tiles[2] = g.dims > 2 ? Launch<T>::spass_tiles((int)g.n[2], (int)g.n[0], g.n[1]) : 0;
+    for (int ax = 0; ax < g.dims; ++ax) g.tiles[ax] = group_tiles<T>(g, ax, g.sched[ax]);
 }
 
 template <typename T>
@@ -1802,6 +1844,10 @@ spstd_status batch_build(spstd_batch *b)
                     ng.d[l] = ctx->d[l];
                 }
                 ng.nh = (int)ctx->hs.size();
+                for (const TunedShape &t : b->tuned)
+                    if (t.precision == ng.precision && t.dims == ng.dims && t.n[0] == ng.n[0] && t.n[1] == ng.n[1] &&
+                        t.n[2] == ng.n[2])
+                        for (int a = 0; a < 3; ++a) ng.sched[a] = t.sched[a];
                 b->gn.push_back(ng);
                 g = &b->gn.back();
             }
@@ -1818,6 +1864,7 @@ spstd_status batch_build(spstd_batch *b)
         else build_nd_descriptors<double>(b, g, img);
     }
     if (img.size() > b->ws_bytes) return bfail(b, SPSTD_ENOMEM, "batch workspace too small for the descriptors");
+    b->img_bytes = img.size();
     if (!img.empty()) {
         SPSTD_BCU(b, cudaMemcpyAsync(b->ws, img.data(), img.size(), cudaMemcpyHostToDevice, b->stream));
         SPSTD_BCU(b, cudaStreamSynchronize(b->stream));
@@ -1838,8 +1885,7 @@ cudaError_t enqueue_group_step(spstd_batch *b, const BatchGroupND &g, cudaStream
     for (int h = 0; h < g.nh; ++h) {
         for (int ax = 0; ax < g.dims; ++ax) {
             const PassArgs<T> *a = args + ((size_t)h * g.dims + ax) * M;
-            cudaError_t e = ax == 0 ? Launch<T>::xpass_batch((int)g.n[0], a, M, g.tiles[0], s)
-                                    : Launch<T>::spass_batch((int)g.n[ax], a, M, g.tiles[ax], s);
+            cudaError_t e = group_pass<T>(g, ax, g.sched[ax], a, M, g.tiles[ax], s);
             if (e != cudaSuccess) return e;
         }
     }
@@ -1884,13 +1930,8 @@ cudaError_t batch_prepare(spstd_batch *b)
 {
     for (const auto &g : b->gn) {
         for (int ax = 0; ax < g.dims; ++ax) {
-            cudaError_t e;
-            if (g.precision == 32)
-                e = ax == 0 ? Launch<float>::xpass_batch((int)g.n[0], nullptr, 0, 0, nullptr)
-                            : Launch<float>::spass_batch((int)g.n[ax], nullptr, 0, 0, nullptr);
-            else
-                e = ax == 0 ? Launch<double>::xpass_batch((int)g.n[0], nullptr, 0, 0, nullptr)
-                            : Launch<double>::spass_batch((int)g.n[ax], nullptr, 0, 0, nullptr);
+            cudaError_t e = g.precision == 32 ? group_pass<float>(g, ax, g.sched[ax], nullptr, 0, 0, nullptr)
+                                              : group_pass<double>(g, ax, g.sched[ax], nullptr, 0, 0, nullptr);
             if (e != cudaSuccess) return e;
         }
     }
@@ -2117,6 +2158,206 @@ spstd_status spstd_batch_launch_count(const spstd_batch *b, int64_t nsteps, int6
 const char *spstd_batch_last_error(const spstd_batch *b)
 {
     return b ? b->err.c_str() : "no batch";
+}
+
+}  // extern "C"
+
+// ---- autotuner ---------------------------------------------------------------
+namespace {
+
+// Schedules an axis of this context can run (sched.h): 0 always; 1..3 for
+// plain FFT passes of tunable length; 4 where 0 is the pipelined TMA pass.
+int schedule_candidates(const spstd_ctx *ctx, int ax, int *list)
+{
+    int n = 0;
+    list[n++] = 0;
+    if (ax < 0 || ax >= ctx->cfg.dims || ctx->dense[ax] || (ax == 0 && ctx->long_x)) return n;
+    const int N = (int)ctx->cfg.n[ax];
+    for (int v = 1; v <= 3; ++v) {
+        const bool ok = ctx->cfg.precision == 32 ? sched_valid<float>(ax, N, v) : sched_valid<double>(ax, N, v);
+        if (ok) list[n++] = v;
+    }
+    if (ctx->tma[ax]) list[n++] = 4;
+    return n;
+}
+
+// Times every candidate schedule of every axis on this context's own grid: the
+// pass applies H to psi_I into the scratch field (the state is not touched),
+// once to warm up, then reps times between two events.  Keeps the fastest.
+template <typename T>
+spstd_status tune_impl(spstd_ctx *ctx, int reps, double *ms)
+{
+    cudaStream_t s = ctx->stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    SPSTD_CU(ctx, cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(ctx, SPSTD_ECUDA, "cudaEventCreate");
+    }
+    spstd_status st = SPSTD_OK;
+    const int tH = 2 * ctx->m;
+    for (int ax = 0; ax < ctx->cfg.dims && st == SPSTD_OK; ++ax) {
+        int list[kSchedules];
+        const int nc = schedule_candidates(ctx, ax, list);
+        int best = ctx->sched[ax];
+        double best_ms = 0.0;
+        for (int i = 0; i < nc && st == SPSTD_OK; ++i) {
+            ctx->sched[ax] = list[i];
+            st = prepare_kernels<T>(ctx);
+            if (st != SPSTD_OK) break;
+            cudaError_t e = enqueue_apply<T>(ctx, 1, 2, tH, 1.0, 0, s, nullptr, ax);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+            for (int r = 0; r < reps && e == cudaSuccess; ++r) e = enqueue_apply<T>(ctx, 1, 2, tH, 1.0, 0, s, nullptr, ax);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float t = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+            if (e != cudaSuccess) {
+                st = cuda_fail(ctx, e, "autotune");
+                break;
+            }
+            const double per = (double)t / reps;
+            if (ms) ms[ax * kSchedules + list[i]] = per;
+            if (i == 0 || per < best_ms) {
+                best_ms = per;
+                best = list[i];
+            }
+        }
+        ctx->sched[ax] = best;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    drop_graph(ctx);
+    if (st == SPSTD_OK) st = check_device_status(ctx);
+    return st;
+}
+
+// Times the batched passes of one member shape under each schedule on the
+// members' scratch fields and keeps the fastest per axis.
+template <typename T>
+spstd_status tune_group(spstd_batch *b, BatchGroupND &g, int reps, cudaEvent_t e0, cudaEvent_t e1)
+{
+    const int M = (int)g.slots.size();
+    const size_t off = (b->img_bytes + 255) & ~size_t(255);
+    if (M == 0 || off + sizeof(PassArgs<T>) * (size_t)M > b->ws_bytes) return SPSTD_OK;  // no room: defaults
+    PassArgs<T> *dargs = (PassArgs<T> *)(b->ws + off);
+    std::vector<PassArgs<T>> args(M);
+    for (int ax = 0; ax < g.dims; ++ax) {
+        for (int i = 0; i < M; ++i) {
+            spstd_ctx *ctx = b->slots[g.slots[i]];
+            args[i] = member_pass_args<T>(ctx, ctx->hs[0], ax);
+            args[i].dst = field_ptr<T>(ctx, 2);
+        }
+        SPSTD_BCU(b, cudaMemcpyAsync(dargs, args.data(), sizeof(PassArgs<T>) * M, cudaMemcpyHostToDevice, b->stream));
+        int best = 0;
+        double best_ms = 0.0;
+        for (int v = 0; v <= 3; ++v) {
+            if (v && !sched_valid<T>(ax, (int)g.n[ax], v)) continue;
+            const int tiles = group_tiles<T>(g, ax, v);
+            SPSTD_BCU(b, group_pass<T>(g, ax, v, dargs, M, tiles, b->stream));
+            SPSTD_BCU(b, cudaEventRecord(e0, b->stream));
+            for (int r = 0; r < reps; ++r) SPSTD_BCU(b, group_pass<T>(g, ax, v, dargs, M, tiles, b->stream));
+            SPSTD_BCU(b, cudaEventRecord(e1, b->stream));
+            SPSTD_BCU(b, cudaEventSynchronize(e1));
+            float t = 0.f;
+            SPSTD_BCU(b, cudaEventElapsedTime(&t, e0, e1));
+            if (v == 0 || t < best_ms) {
+                best_ms = t;
+                best = v;
+            }
+        }
+        g.sched[ax] = best;
+        g.tiles[ax] = group_tiles<T>(g, ax, best);
+    }
+    TunedShape ts{g.precision, g.dims, {g.n[0], g.n[1], g.n[2]}, {g.sched[0], g.sched[1], g.sched[2]}};
+    bool found = false;
+    for (TunedShape &t : b->tuned)
+        if (t.precision == ts.precision && t.dims == ts.dims && t.n[0] == ts.n[0] && t.n[1] == ts.n[1] &&
+            t.n[2] == ts.n[2]) {
+            t = ts;
+            found = true;
+        }
+    if (!found) b->tuned.push_back(ts);
+    return SPSTD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+spstd_status spstd_schedule_candidates(const spstd_ctx *ctx, int axis, int *list, int *count)
+{
+    if (!ctx || !list || !count || axis < 0 || axis >= ctx->cfg.dims) return SPSTD_EINVAL;
+    *count = schedule_candidates(ctx, axis, list);
+    return SPSTD_OK;
+}
+
+spstd_status spstd_get_schedule(const spstd_ctx *ctx, int axis, int *schedule)
+{
+    if (!ctx || !schedule || axis < 0 || axis >= ctx->cfg.dims) return SPSTD_EINVAL;
+    *schedule = ctx->sched[axis];
+    return SPSTD_OK;
+}
+
+spstd_status spstd_set_schedule(spstd_ctx *ctx, int axis, int schedule)
+{
+    if (!ctx || axis < 0 || axis >= ctx->cfg.dims) return SPSTD_EINVAL;
+    int list[kSchedules];
+    const int nc = schedule_candidates(ctx, axis, list);
+    bool ok = false;
+    for (int i = 0; i < nc; ++i) ok |= list[i] == schedule;
+    if (!ok) return fail(ctx, SPSTD_EINVAL, "schedule not available on this axis");
+    if (ctx->sched[axis] != schedule) {
+        ctx->sched[axis] = schedule;
+        drop_graph(ctx);
+    }
+    return SPSTD_OK;
+}
+
+spstd_status spstd_tune(spstd_ctx *ctx, int reps, double *ms)
+{
+    if (!ctx || reps < 1) return SPSTD_EINVAL;
+    if (ms)
+        for (int i = 0; i < 3 * kSchedules; ++i) ms[i] = -1.0;
+    return ctx->cfg.precision == 32 ? tune_impl<float>(ctx, reps, ms) : tune_impl<double>(ctx, reps, ms);
+}
+
+spstd_status spstd_batch_tune(spstd_batch *b, int reps)
+{
+    if (!b || reps < 1) return SPSTD_EINVAL;
+    if (b->dirty) {
+        spstd_status st = batch_build(b);
+        if (st != SPSTD_OK) return st;
+    }
+    SPSTD_BCU(b, cudaStreamSynchronize(b->stream));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    SPSTD_BCU(b, cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return bfail(b, SPSTD_ECUDA, "cudaEventCreate");
+    }
+    spstd_status st = SPSTD_OK;
+    for (auto &g : b->gn) {
+        st = g.precision == 32 ? tune_group<float>(b, g, reps, e0, e1) : tune_group<double>(b, g, reps, e0, e1);
+        if (st != SPSTD_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (b->gexec) {
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+    }
+    return st;
+}
+
+spstd_status spstd_batch_get_schedule(const spstd_batch *b, int precision, int dims, const int64_t *n, int *schedule)
+{
+    if (!b || !n || !schedule) return SPSTD_EINVAL;
+    for (int a = 0; a < 3; ++a) schedule[a] = 0;
+    for (const TunedShape &t : b->tuned)
+        if (t.precision == precision && t.dims == dims && t.n[0] == n[0] && t.n[1] == n[1] && t.n[2] == n[2])
+            for (int a = 0; a < 3; ++a) schedule[a] = t.sched[a];
+    return SPSTD_OK;
 }
 
 }  // extern "C"

@@ -147,10 +147,9 @@ __device__ __forceinline__ void stage_tables(const PassArgs<T> &a, cpx<T> *s_tw,
 // x pass: contiguous lines.  Block (TT, LPC); line pair lp covers rows 2lp and
 // 2lp+1 (the second may be past the end: its half of the complex line is 0).
 // ---------------------------------------------------------------------------
-template <typename T, int N, int LPC>
+template <typename T, int N, int LPC, int E = line_e<T, N>::value>
 __device__ __forceinline__ void xpass_body(const PassArgs<T> &a, int64_t blk)
 {
-    constexpr int E = line_e<T, N>::value;
     constexpr int TT = N / E;
     constexpr int LS = N + N / 32;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -211,21 +210,21 @@ __device__ __forceinline__ void xpass_body(const PassArgs<T> &a, int64_t blk)
     }
 }
 
-template <typename T, int N, int LPC>
-__global__ void __launch_bounds__((N / line_e<T, N>::value) * LPC)
+template <typename T, int N, int LPC, int E = line_e<T, N>::value>
+__global__ void __launch_bounds__((N / E) * LPC)
 xpass_kernel(const PassArgs<T> a)
 {
-    xpass_body<T, N, LPC>(a, a.reverse ? (int64_t)(gridDim.x - 1 - blockIdx.x) : (int64_t)blockIdx.x);
+    xpass_body<T, N, LPC, E>(a, a.reverse ? (int64_t)(gridDim.x - 1 - blockIdx.x) : (int64_t)blockIdx.x);
 }
 
 // Batched x pass: members of one shape, tiles_per_member consecutive blocks each.
-template <typename T, int N, int LPC>
-__global__ void __launch_bounds__((N / line_e<T, N>::value) * LPC)
+template <typename T, int N, int LPC, int E = line_e<T, N>::value>
+__global__ void __launch_bounds__((N / E) * LPC)
 xpass_batch_kernel(const PassArgs<T> *__restrict__ args, int tiles_per_member)
 {
     const int member = blockIdx.x / tiles_per_member;
     const PassArgs<T> a = args[member];
-    xpass_body<T, N, LPC>(a, (int64_t)(blockIdx.x - member * tiles_per_member));
+    xpass_body<T, N, LPC, E>(a, (int64_t)(blockIdx.x - member * tiles_per_member));
 }
 
 // ---------------------------------------------------------------------------
@@ -234,10 +233,9 @@ xpass_batch_kernel(const PassArgs<T> *__restrict__ args, int tiles_per_member)
 // thread within the line, so each warp reads 2 LPC consecutive values of a
 // row per access.  Tile id = outer * n_xt + xt.
 // ---------------------------------------------------------------------------
-template <typename T, int N, int LPC>
+template <typename T, int N, int LPC, int E = line_e<T, N>::value>
 __device__ __forceinline__ void spass_body(const PassArgs<T> &a, int64_t blk)
 {
-    constexpr int E = line_e<T, N>::value;
     constexpr int TT = N / E;
     extern __shared__ __align__(16) unsigned char smem[];
     cpx<T> *s_tw = reinterpret_cast<cpx<T> *>(smem);
@@ -306,20 +304,20 @@ __device__ __forceinline__ void spass_body(const PassArgs<T> &a, int64_t blk)
     }
 }
 
-template <typename T, int N, int LPC>
-__global__ void __launch_bounds__((N / line_e<T, N>::value) * LPC)
+template <typename T, int N, int LPC, int E = line_e<T, N>::value>
+__global__ void __launch_bounds__((N / E) * LPC)
 spass_kernel(const PassArgs<T> a)
 {
-    spass_body<T, N, LPC>(a, a.reverse ? (int64_t)(gridDim.x - 1 - blockIdx.x) : (int64_t)blockIdx.x);
+    spass_body<T, N, LPC, E>(a, a.reverse ? (int64_t)(gridDim.x - 1 - blockIdx.x) : (int64_t)blockIdx.x);
 }
 
-template <typename T, int N, int LPC>
-__global__ void __launch_bounds__((N / line_e<T, N>::value) * LPC)
+template <typename T, int N, int LPC, int E = line_e<T, N>::value>
+__global__ void __launch_bounds__((N / E) * LPC)
 spass_batch_kernel(const PassArgs<T> *__restrict__ args, int tiles_per_member)
 {
     const int member = blockIdx.x / tiles_per_member;
     const PassArgs<T> a = args[member];
-    spass_body<T, N, LPC>(a, (int64_t)(blockIdx.x - member * tiles_per_member));
+    spass_body<T, N, LPC, E>(a, (int64_t)(blockIdx.x - member * tiles_per_member));
 }
 
 // ---------------------------------------------------------------------------

@@ -8,7 +8,9 @@ whose steps are done is retired at the next chunk boundary: its energy, norm
 and probe spectrum are read back, its slot and memory are freed, and its
 latency (retire time minus arrival time) is recorded.  Requests that arrive
 while others run are admitted between chunks, so their work overlaps on the
-device with the running ones.
+device with the running ones.  When a 2D/3D shape joins the batch for the
+first time, the batch's pass schedules are autotuned (spstd_batch_tune, a few
+milliseconds) before the next chunk; the choice stays for later members.
 """
 from __future__ import annotations
 
@@ -37,7 +39,8 @@ class Request:
 
 class Server:
     def __init__(self, hbm_cap_bytes: float = 150e9, max_slots: int = 1024, chunk_steps: int = 500,
-                 precision: int = 32, device: int = 0, keep_state: bool = False, spectrum: bool = True):
+                 precision: int = 32, device: int = 0, keep_state: bool = False, spectrum: bool = True,
+                 tune: bool = True):
         self.batch = spstd.Batch(max_slots, device=device)
         self.cap = hbm_cap_bytes
         self.chunk = int(chunk_steps)
@@ -51,6 +54,9 @@ class Server:
         self.footprint = 0
         self._next = 0
         self.chunks = 0
+        self.tune = tune
+        self.tuned_shapes = set()
+        self._untuned = False
 
     def footprint_of(self, problem) -> int:
         cfg = spstd.make_config(problem.dims, problem.n[: problem.dims], problem.lo[: problem.dims],
@@ -92,7 +98,14 @@ class Server:
             r.admitted = time.perf_counter()
             self.footprint += r.need
             self.running[r.rid] = r
+            shape = (r.problem.dims, tuple(r.problem.n))
+            if r.problem.dims > 1 and shape not in self.tuned_shapes:
+                self.tuned_shapes.add(shape)
+                self._untuned = True
         self.queue = still
+        if self.tune and self._untuned:
+            self.batch.spstd_batch_tune(reps=2)
+            self._untuned = False
 
     def _retire(self):
         for rid in [rid for rid, r in self.running.items() if r.done_steps >= r.steps]:

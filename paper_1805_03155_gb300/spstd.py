@@ -23,6 +23,7 @@ PRESETS = {"CUSTOM": -1, "LEAPFROG": 0, "STRANG": 1, "PAPER3": 2, "FR4": 3, "SUZ
 PERIODIC, DIRICHLET, NEUMANN = 0, 1, 2
 MAX_STAGES = 8
 MAX_PROBES = 16
+SCHEDULES = 5
 
 
 class SpstdError(RuntimeError):
@@ -112,6 +113,12 @@ def lib():
         "spstd_batch_sync": (C.c_int, [vp]),
         "spstd_batch_launch_count": (C.c_int, [vp, C.c_int64, ip]),
         "spstd_batch_last_error": (C.c_char_p, [vp]),
+        "spstd_schedule_candidates": (C.c_int, [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+        "spstd_get_schedule": (C.c_int, [vp, C.c_int, C.POINTER(C.c_int)]),
+        "spstd_set_schedule": (C.c_int, [vp, C.c_int, C.c_int]),
+        "spstd_tune": (C.c_int, [vp, C.c_int, dp]),
+        "spstd_batch_tune": (C.c_int, [vp, C.c_int]),
+        "spstd_batch_get_schedule": (C.c_int, [vp, C.c_int, C.c_int, ip, C.POINTER(C.c_int)]),
         "spstd_last_error": (C.c_char_p, [vp]),
         "spstd_status_string": (C.c_char_p, [C.c_int]),
     }
@@ -312,6 +319,27 @@ class Solver:
         self._check(self.L.spstd_launch_count(self.ctx, int(nsteps), C.byref(v)))
         return v.value
 
+    def spstd_schedule_candidates(self, axis):
+        lst = (C.c_int * SCHEDULES)()
+        n = C.c_int(0)
+        self._check(self.L.spstd_schedule_candidates(self.ctx, int(axis), lst, C.byref(n)))
+        return [lst[i] for i in range(n.value)]
+
+    def spstd_get_schedule(self, axis):
+        v = C.c_int(0)
+        self._check(self.L.spstd_get_schedule(self.ctx, int(axis), C.byref(v)))
+        return v.value
+
+    def spstd_set_schedule(self, axis, schedule):
+        self._check(self.L.spstd_set_schedule(self.ctx, int(axis), int(schedule)))
+
+    def spstd_tune(self, reps=20):
+        """Times every candidate schedule per axis and keeps the fastest;
+        returns ms[axis][schedule] (-1 where not a candidate)."""
+        ms = np.zeros(3 * SCHEDULES)
+        self._check(self.L.spstd_tune(self.ctx, int(reps), _dp(ms)))
+        return ms.reshape(3, SCHEDULES)
+
 
 def stability_limit(cfg: spstd_config, vmax=0.0):
     s = C.c_double(0)
@@ -375,6 +403,15 @@ class Batch:
         v = C.c_int64(0)
         self._check(self.L.spstd_batch_launch_count(self.b, int(nsteps), C.byref(v)))
         return v.value
+
+    def spstd_batch_tune(self, reps=10):
+        self._check(self.L.spstd_batch_tune(self.b, int(reps)))
+
+    def spstd_batch_get_schedule(self, precision, dims, n):
+        nn = (C.c_int64 * 3)(*(list(n) + [1] * (3 - len(n))))
+        out = (C.c_int * 3)()
+        self._check(self.L.spstd_batch_get_schedule(self.b, int(precision), int(dims), nn, out))
+        return [out[i] for i in range(3)]
 
     def close(self):
         if getattr(self, "b", None) is not None and self.b.value:

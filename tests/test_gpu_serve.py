@@ -21,12 +21,16 @@ def requests():
     return probs
 
 
-@pytest.mark.parametrize("precision", [64, 32])
-def test_served_results_equal_lone_solves(precision):
+@pytest.mark.parametrize("precision,tune", [(64, False), (64, True), (32, True)])
+def test_served_results_equal_lone_solves(precision, tune):
+    """Bitwise in FP64 with the default schedules (the same kernels); with
+    autotuned schedules the radix plan may differ from the lone solve's, so
+    FP64 agrees to rounding and FP32 to its tolerance."""
     from paper_1805_03155_gb300 import serve, spstd
 
     reqs = requests()
-    srv = serve.Server(hbm_cap_bytes=2e9, max_slots=4, chunk_steps=9, precision=precision, keep_state=True)
+    srv = serve.Server(hbm_cap_bytes=2e9, max_slots=4, chunk_steps=9, precision=precision, keep_state=True,
+                       tune=tune)
     t0 = time.perf_counter()
     for i, (p, steps) in enumerate(reqs):
         srv.submit(p, steps, arrival=t0 + 0.002 * i)
@@ -45,13 +49,14 @@ def test_served_results_equal_lone_solves(precision):
         nv, ev = s.spstd_energy_norm()
         s.close()
         bR, bI = r.result["state"]
-        if precision == 64:
+        if precision == 64 and not tune:
             assert np.array_equal(bR, R) and np.array_equal(bI, Im), r.rid
             assert r.result["energy"] == ev
         else:
+            tol = 1e-12 if precision == 64 else 1e-5
             scale = max(np.abs(R).max(), np.abs(Im).max())
-            assert np.max(np.abs(bR - R)) <= 1e-5 * scale and np.max(np.abs(bI - Im)) <= 1e-5 * scale
-            assert abs(r.result["energy"] - ev) <= 1e-5 * abs(ev)
+            assert np.max(np.abs(bR - R)) <= tol * scale and np.max(np.abs(bI - Im)) <= tol * scale
+            assert abs(r.result["energy"] - ev) <= tol * abs(ev)
 
 
 def test_admission_respects_hbm_cap():
