@@ -153,13 +153,14 @@ def measured_traffic(workload, kernel, schedule=0):
     return MEASURED_TRAFFIC.get(workload, {}).get(kernel)
 
 
-KIND_AXIS = {"x_pass": 0, "y_pass": 1, "z_pass": 2}
+KIND_AXIS = {"x_pass": 0, "y_pass": 1, "z_pass": 2, "xy_pass": 0}
 
 
 def algorithmic_bytes(kind, n_total, es):
-    """Compulsory bytes of one launch: x pass reads src, V, dst and writes dst;
-    a strided pass reads src, dst and writes dst."""
-    return (4 if kind == "x_pass" else 3) * es * n_total
+    """Compulsory bytes of one launch: the x pass (and the fused x-y pass)
+    reads src, V, dst and writes dst; a strided pass reads src, dst and writes
+    dst."""
+    return (4 if kind in ("x_pass", "xy_pass") else 3) * es * n_total
 
 
 def cpu_baseline(problem, budget_s=20.0):
@@ -419,6 +420,7 @@ def main():
     # autotune the pass schedules on this grid (outside the timed region)
     tune_ms = s.spstd_tune(reps=10)
     schedules = [s.spstd_get_schedule(a) for a in range(problem.dims)]
+    xy_fused = s.spstd_get_xy_fusion()
 
     # warm-up (also captures the step graph)
     s.spstd_step(args.warmup)
@@ -454,9 +456,9 @@ def main():
     peak, peak_src = measured_peaks()
     abytes = algorithmic_bytes(dom, N, es)
     achieved = abytes / (dom_ms * 1e-3) / 1e9
-    step_bytes = sum(algorithmic_bytes(k, N, es) * kinds[k][1] for k in ("x_pass", "y_pass", "z_pass")
+    step_bytes = sum(algorithmic_bytes(k, N, es) * kinds[k][1] for k in ("x_pass", "y_pass", "z_pass", "xy_pass")
                      if k in kinds) / prof_steps
-    half_stages = kinds.get("x_pass", (0, 0))[1] / prof_steps
+    half_stages = (kinds.get("x_pass", (0, 0))[1] + kinds.get("xy_pass", (0, 0))[1]) / prof_steps
 
     # ---- end to end through the C ABI with pinned host buffers --------------
     pin_r = torch.empty(N, dtype=torch.float64, pin_memory=True)
@@ -522,6 +524,7 @@ def main():
                              if 3 * N * es > 129 * 2 ** 20 else "L2-resident grid: not flushed between steps",
                 "parallelism": f"replicas{ws}",
                 "schedules": schedules,
+                "xy_fused": xy_fused,
                 "schedule_ms": [[round(float(t), 5) for t in row] for row in tune_ms[: problem.dims]],
             },
             "clocks": clk,

@@ -224,9 +224,9 @@ spstd_status spstd_launch_count(const spstd_ctx *ctx, int64_t nsteps, int64_t *l
  * probes record) with direct launches instead of graph replays, a CUDA event
  * pair around every launch on the context's stream, and returns per kernel
  * kind k the summed device time ms[k] (milliseconds) and launch count cnt[k]:
- * k = 0 x pass, 1 y pass, 2 z pass, 3 probe recorder, 4 resident 1D solver.
- * Synchronises. */
-#define SPSTD_KERNEL_KINDS 5
+ * k = 0 x pass, 1 y pass, 2 z pass, 3 probe recorder, 4 resident 1D solver,
+ * 5 fused x-y pass.  Synchronises. */
+#define SPSTD_KERNEL_KINDS 6
 spstd_status spstd_profile_steps(spstd_ctx *ctx, int64_t nsteps, double *ms, int64_t *cnt);
 
 /* Schedules: the radix and tile plan of an axis's pass kernel (no effect on
@@ -254,6 +254,27 @@ spstd_status spstd_schedule_candidates(const spstd_ctx *ctx, int axis, int *list
 spstd_status spstd_get_schedule(const spstd_ctx *ctx, int axis, int *schedule);
 spstd_status spstd_set_schedule(spstd_ctx *ctx, int axis, int schedule);
 spstd_status spstd_tune(spstd_ctx *ctx, int reps, double *ms);
+
+/* x-y fusion (3D FP32 grids with nx = ny in {64, 128, 256}, x and y on
+ * schedule 0; off by default): the x and y passes of each half-stage run
+ * as one persistent launch that visits every plane's y tiles and then, while
+ * the plane is still in L2, its x tiles, so that HBM carries src, V and dst
+ * once for both passes (the sum of Eq. 18's x and y terms, accumulated y then
+ * x; FP32 rounding differs from the separate passes).  spstd_tune also times
+ * fused against separate and keeps the faster.  spstd_set_xy_fusion returns
+ * SPSTD_EUNSUPPORTED when asked to fuse a grid that cannot; *on reports
+ * whether steps use the fused launch. */
+spstd_status spstd_set_xy_fusion(spstd_ctx *ctx, int on);
+spstd_status spstd_get_xy_fusion(const spstd_ctx *ctx, int *on);
+
+/* Test hook for the failure path of the bounded device waits: makes the next
+ * fused x-y pass skip one y tile of its first plane, so that the x tiles of
+ * that plane wait in vain until their bounded waits run out (about a second)
+ * and their blocks return early with the device status word set.  The next synchronising call then reports SPSTD_ETIMEOUT
+ * and clears the status and the pass's counters; psi_R and psi_I are left
+ * partly updated, and the context stays usable (set a state and step again).
+ * SPSTD_EUNSUPPORTED when the context has no fused pass. */
+spstd_status spstd_inject_wait_timeout(spstd_ctx *ctx);
 
 /* Norm without device allocation (the paper has no counterpart: this is a
  * service for callers that may not allocate device memory where they call).

@@ -22,6 +22,7 @@
 #include "launch.cuh"
 #include "longline.h"
 #include "pass_tma_launch.h"
+#include "pass_xy.cuh"
 #include "sched.h"
 #include "spectrum.h"
 
@@ -43,7 +44,7 @@ struct HalfStage {
 
 struct Layout {
     size_t psi[2], V, tmp, staging, ring, counter, status, snap, partial, dout, tw[3], mult, dense[3], spec;
-    size_t eig_acc, eig_theta, eig_step, rk[6], lscr, total;
+    size_t eig_acc, eig_theta, eig_step, rk[6], lscr, xy, total;
 };
 
 // An axis uses the FFT passes when it is periodic with a power-of-two length
@@ -62,6 +63,15 @@ bool axis_is_long(const spstd_config &cfg, int a)
 {
     const int64_t n = cfg.n[a];
     return a == 0 && cfg.bc[a] == SPSTD_PERIODIC && (n & (n - 1)) == 0 && !axis_is_fft(cfg, a) && n <= kMaxLongN;
+}
+
+// 3D FP32 grids whose x and y axes both take the pipelined passes at the same
+// length can run them as one fused launch (pass_xy.cuh).
+bool xy_fusable(const spstd_config &cfg)
+{
+    auto tma_len = [](int64_t n) { return n == 64 || n == 128 || n == 256; };
+    return cfg.precision == 32 && cfg.dims == 3 && cfg.n[0] == cfg.n[1] && tma_len(cfg.n[0]) &&
+           cfg.bc[0] == SPSTD_PERIODIC && cfg.bc[1] == SPSTD_PERIODIC && cfg.n[2] >= 2;
 }
 
 // Entries of an axis in each multiplier row (the four-step pass computes its
@@ -326,6 +336,8 @@ Layout make_layout(const spstd_config &cfg, int m)
     for (int k = 0; k < 6; ++k) L.rk[k] = take(cfg.preset == SPSTD_RK4 ? es * ntot : 0);  // t, h, acc (R, I)
     // four-step scratch: one complex line per pair of x lines
     L.lscr = take(axis_is_long(cfg, 0) ? 2 * es * (size_t)((cfg.n[1] * cfg.n[2] + 1) / 2) * cfg.n[0] : 0);
+    // fused x-y pass counters: ticket/claim words, then per plane y tiles done and x tiles seen
+    L.xy = take(xy_fusable(cfg) ? 4 * (size_t)(4 + 2 * cfg.n[2]) : 0);
     L.total = off;
     return L;
 }
@@ -356,6 +368,7 @@ struct spstd_ctx {
     int N1 = 0, N2 = 0;                     // its split N = N1 N2
     int64_t tab_off[3] = {0, 0, 0};         // axis offsets within a multiplier row
     int sched[3] = {0, 0, 0};               // pass schedule per axis (sched.h)
+    bool fuse_xy = false;                   // x and y passes as one launch (when both are schedule 0)
     // step-boundary merge of the last and first half-stages (same field)
     bool merge = false;
     HalfStage merged{};
@@ -396,7 +409,14 @@ spstd_status check_device_status(spstd_ctx *ctx)
     cudaError_t e = cudaMemcpyAsync(&st, ctx->ptr(ctx->L.status), sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "status read");
-    if (st != 0) return fail(ctx, SPSTD_ETIMEOUT, "a device wait timed out (status word set by a pass kernel)");
+    if (st != 0) {
+        // a timed-out fused pass may leave its counters mid-count: clear them with the status
+        if (xy_fusable(ctx->cfg))
+            cudaMemsetAsync(ctx->ptr(ctx->L.xy), 0, 4 * (size_t)(4 + 2 * ctx->cfg.n[2]), ctx->stream);
+        cudaMemsetAsync(ctx->ptr(ctx->L.status), 0, sizeof(int), ctx->stream);
+        cudaStreamSynchronize(ctx->stream);
+        return fail(ctx, SPSTD_ETIMEOUT, "a device wait timed out (status word set by a pass kernel)");
+    }
     return SPSTD_OK;
 }
 
@@ -678,6 +698,9 @@ double table_scale(const spstd_ctx *ctx, int table)
     return (table & 1) ? -ctx->d[l] * ctx->dt : ctx->c[l] * ctx->dt;
 }
 
+// Whether an H-apply between psi_R, psi_I and the scratch field runs x and y as one launch.
+bool fused_active(const spstd_ctx *ctx) { return ctx->fuse_xy && ctx->sched[0] == 0 && ctx->sched[1] == 0; }
+
 // dst += a sum_d L_d src + bV V src for fields fsrc -> fdst (0 psi_R, 1 psi_I,
 // 2 scratch), multiplier set `table`; the V term rides on the x pass.
 template <typename T>
@@ -691,7 +714,33 @@ cudaError_t enqueue_apply(spstd_ctx *ctx, int fsrc, int fdst, int table, double 
     const int64_t n0 = cfg.n[0], n1 = cfg.n[1], n2 = cfg.n[2];
     const int64_t *off = ctx->tab_off;
     int *status = (int *)ctx->ptr(ctx->L.status);
-    for (int ax = 0; ax < cfg.dims; ++ax) {
+    int ax0 = 0;
+    if constexpr (sizeof(T) == 4) {
+        if (fused_active(ctx) && only_axis < 0 && fsrc <= 2 && fdst <= 2) {
+            XyPassArgs xa{};
+            xa.twx = (const float2 *)ctx->ptr(ctx->L.tw[0]);
+            xa.twy = (const float2 *)ctx->ptr(ctx->L.tw[1]);
+            xa.multx = (const float *)(mult + off[0]);
+            xa.multy = (const float *)(mult + off[1]);
+            xa.V = (const float *)ctx->ptr(ctx->L.V);
+            xa.bV = (float)bV;
+            xa.nx = (int)n0;
+            xa.ny = (int)n1;
+            xa.nz = (int)n2;
+            xa.nyt = (int)(n0 / tma_cols_per_tile());
+            xa.nxt = (int)(n1 / tma_rows_per_tile());
+            unsigned *cnt = (unsigned *)ctx->ptr(ctx->L.xy);
+            xa.claim = cnt;
+            xa.ydone = cnt + 4;
+            xa.xseen = cnt + 4 + n2;
+            xa.status = status;
+            SPSTD_TIMED(timer, s, 5,
+                        launch_xypass_tma((int)n0, ctx->tmap[fsrc][0], ctx->tmap[fdst][0], ctx->tmap[fsrc][1],
+                                          ctx->tmap[fdst][1], xa, s));
+            ax0 = 2;
+        }
+    }
+    for (int ax = ax0; ax < cfg.dims; ++ax) {
         if (only_axis >= 0 && ax != only_axis) continue;
         const int rev = ax == 1 ? !reverse : reverse;
         const int64_t N = cfg.n[ax];
@@ -888,8 +937,12 @@ cudaError_t enqueue_merged_piece(spstd_ctx *ctx, int piece, int64_t units, cudaS
 }
 
 // Kernel launches enqueue_steps(n) issues.
-// Kernel launches of one H-apply: one per axis, three for a four-step x axis.
-int64_t apply_launches(const spstd_ctx *ctx) { return ctx->cfg.dims + (ctx->long_x ? 2 : 0); }
+// Kernel launches of one H-apply between the state fields: one per axis, three
+// for a four-step x axis, one for a fused x-y pair.
+int64_t apply_launches(const spstd_ctx *ctx)
+{
+    return ctx->cfg.dims + (ctx->long_x ? 2 : 0) - (fused_active(ctx) ? 1 : 0);
+}
 
 // A 1D grid runs all steps of a call in one resident launch unless its line
 // is too long for one block.
@@ -970,6 +1023,7 @@ spstd_status prepare_kernels(spstd_ctx *ctx)
     none.nx = (int)cfg.n[0];
     if (cfg.dims > 1 && !ctx->dense[1]) SPSTD_CU(ctx, Launch<T>::spass((int)cfg.n[1], none, ctx->stream));
     if (cfg.dims == 3 && !ctx->dense[2]) SPSTD_CU(ctx, Launch<T>::spass((int)cfg.n[2], none, ctx->stream));
+    if (ctx->fuse_xy) SPSTD_CU(ctx, prepare_xypass_tma((int)cfg.n[0]));
     for (int ax = 0; ax < cfg.dims; ++ax) {
         if (ctx->tma[ax]) SPSTD_CU(ctx, prepare_pass_tma(ax, (int)cfg.n[ax]));
         const int sv = ctx->sched[ax];
@@ -1240,6 +1294,9 @@ spstd_status spstd_create(const spstd_config *cfg, void *d_workspace, size_t wor
     st = set_dt(ctx, 0.0);
     if (st != SPSTD_OK) return bail(st);
     setup_tma(ctx);
+    // fused x-y pass: available where xy_fusable holds, off until spstd_set_xy_fusion or
+    // spstd_tune selects it (measured slower than the separate passes at 256^3)
+    ctx->fuse_xy = false;
     *out = ctx;
     return SPSTD_OK;
 }
@@ -1594,7 +1651,9 @@ spstd_status spstd_launch_count(const spstd_ctx *ctx, int64_t nsteps, int64_t *l
     if (nsteps == 0) {
         *launches = 0;
     } else if (ctx->rk4) {
-        *launches = nsteps * (8 * apply_launches(ctx) + 4 + (ctx->cfg.n_probe > 0 ? 1 : 0) + (ctx->eig_active ? 1 : 0));
+        // Runge-Kutta stage fields take the unfused passes
+        *launches = nsteps * (8 * (ctx->cfg.dims + (ctx->long_x ? 2 : 0)) + 4 + (ctx->cfg.n_probe > 0 ? 1 : 0) +
+                              (ctx->eig_active ? 1 : 0));
     } else if (ctx->eig_active) {
         *launches = nsteps * ((int64_t)ctx->hs.size() * apply_launches(ctx) + (ctx->cfg.n_probe > 0 ? 1 : 0) + 1);
     } else if (resident_path(ctx)) {
@@ -2225,6 +2284,26 @@ spstd_status tune_impl(spstd_ctx *ctx, int reps, double *ms)
         }
         ctx->sched[ax] = best;
     }
+    // x and y as one launch or two: time a whole H-apply each way
+    if (st == SPSTD_OK && xy_fusable(ctx->cfg) && ctx->tma[0] && ctx->tma[1] && ctx->sched[0] == 0 &&
+        ctx->sched[1] == 0) {
+        double t2[2] = {0, 0};
+        for (int f = 0; f < 2 && st == SPSTD_OK; ++f) {
+            ctx->fuse_xy = f == 1;
+            st = prepare_kernels<T>(ctx);
+            if (st != SPSTD_OK) break;
+            cudaError_t e = enqueue_apply<T>(ctx, 1, 2, tH, 1.0, 0, s);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+            for (int r = 0; r < reps && e == cudaSuccess; ++r) e = enqueue_apply<T>(ctx, 1, 2, tH, 1.0, 0, s);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float t = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+            if (e != cudaSuccess) st = cuda_fail(ctx, e, "autotune");
+            t2[f] = t;
+        }
+        ctx->fuse_xy = st == SPSTD_OK ? t2[1] <= t2[0] : true;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     drop_graph(ctx);
@@ -2311,6 +2390,37 @@ spstd_status spstd_set_schedule(spstd_ctx *ctx, int axis, int schedule)
         ctx->sched[axis] = schedule;
         drop_graph(ctx);
     }
+    return SPSTD_OK;
+}
+
+spstd_status spstd_set_xy_fusion(spstd_ctx *ctx, int on)
+{
+    if (!ctx) return SPSTD_EINVAL;
+    const bool can = xy_fusable(ctx->cfg) && ctx->tma[0] && ctx->tma[1];
+    if (on && !can) return fail(ctx, SPSTD_EUNSUPPORTED, "x-y fusion needs a 3D FP32 grid with nx = ny in {64, 128, 256}");
+    if (ctx->fuse_xy != (on != 0)) {
+        ctx->fuse_xy = on != 0;
+        drop_graph(ctx);
+    }
+    return SPSTD_OK;
+}
+
+spstd_status spstd_inject_wait_timeout(spstd_ctx *ctx)
+{
+    if (!ctx) return SPSTD_EINVAL;
+    if (!fused_active(ctx)) return fail(ctx, SPSTD_EUNSUPPORTED, "no fused x-y pass to stall");
+    // the next fused pass starts its work list at item 1: the first y tile of
+    // plane 0 is never claimed, so that plane's x tiles wait in vain
+    const unsigned first = 1u;
+    SPSTD_CU(ctx, cudaMemcpyAsync(ctx->ptr(ctx->L.xy), &first, sizeof(first), cudaMemcpyHostToDevice, ctx->stream));
+    SPSTD_CU(ctx, cudaStreamSynchronize(ctx->stream));
+    return SPSTD_OK;
+}
+
+spstd_status spstd_get_xy_fusion(const spstd_ctx *ctx, int *on)
+{
+    if (!ctx || !on) return SPSTD_EINVAL;
+    *on = fused_active(ctx) ? 1 : 0;
     return SPSTD_OK;
 }
 

@@ -31,4 +31,12 @@ cudaError_t launch_pass_tma(int axis, int N, const CUtensorMap &msrc, const CUte
 // The same set-up without a launch (call before a stream capture).
 cudaError_t prepare_pass_tma(int axis, int N);
 
+struct XyPassArgs;
+// x and y passes of a 3D half-stage in one persistent launch (pass_xy.cuh);
+// nx = ny = N in {64, 128, 256}; maps: src and dst in the x view (N x 32-row
+// box) and the y view (32-column x N box).
+cudaError_t launch_xypass_tma(int N, const CUtensorMap &src_x, const CUtensorMap &dst_x, const CUtensorMap &src_y,
+                              const CUtensorMap &dst_y, const XyPassArgs &a, cudaStream_t s);
+cudaError_t prepare_xypass_tma(int N);
+
 }  // namespace spstd

@@ -117,6 +117,9 @@ def lib():
         "spstd_get_schedule": (C.c_int, [vp, C.c_int, C.POINTER(C.c_int)]),
         "spstd_set_schedule": (C.c_int, [vp, C.c_int, C.c_int]),
         "spstd_tune": (C.c_int, [vp, C.c_int, dp]),
+        "spstd_set_xy_fusion": (C.c_int, [vp, C.c_int]),
+        "spstd_get_xy_fusion": (C.c_int, [vp, C.POINTER(C.c_int)]),
+        "spstd_inject_wait_timeout": (C.c_int, [vp]),
         "spstd_batch_tune": (C.c_int, [vp, C.c_int]),
         "spstd_batch_get_schedule": (C.c_int, [vp, C.c_int, C.c_int, ip, C.POINTER(C.c_int)]),
         "spstd_last_error": (C.c_char_p, [vp]),
@@ -304,7 +307,7 @@ class Solver:
     def spstd_eigenstates_end(self):
         self._check(self.L.spstd_eigenstates_end(self.ctx))
 
-    KERNEL_KINDS = ("x_pass", "y_pass", "z_pass", "probe", "resident_1d")
+    KERNEL_KINDS = ("x_pass", "y_pass", "z_pass", "probe", "resident_1d", "xy_pass")
 
     def spstd_profile_steps(self, nsteps):
         """Per kernel kind: (total device ms, launches) over nsteps real steps."""
@@ -332,6 +335,17 @@ class Solver:
 
     def spstd_set_schedule(self, axis, schedule):
         self._check(self.L.spstd_set_schedule(self.ctx, int(axis), int(schedule)))
+
+    def spstd_set_xy_fusion(self, on):
+        self._check(self.L.spstd_set_xy_fusion(self.ctx, int(bool(on))))
+
+    def spstd_inject_wait_timeout(self):
+        self._check(self.L.spstd_inject_wait_timeout(self.ctx))
+
+    def spstd_get_xy_fusion(self):
+        v = C.c_int(0)
+        self._check(self.L.spstd_get_xy_fusion(self.ctx, C.byref(v)))
+        return bool(v.value)
 
     def spstd_tune(self, reps=20):
         """Times every candidate schedule per axis and keeps the fastest;
