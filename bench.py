@@ -127,13 +127,12 @@ def measured_peaks():
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
-# 256^3 FP32 kernels from one ncu capture (profiles/xpass_tma_aniso_ho_3d_256.md,
-# profiles/spass_tma_aniso_ho_3d_256.md), valid while the kernel sources hash
-# to the recorded value.
+# 256^3 FP32 kernels from one ncu capture (profiles/traffic_aniso_ho_3d_256.md),
+# valid while the kernel sources hash to the recorded value.
 MEASURED_TRAFFIC = {
-    "source_hash": "01c5a2b7ac202a73",
-    "aniso_ho_3d_256": {"x_pass": 201.361664e6 + 36.185344e6, "y_pass": 134.249216e6 + 21.008896e6,
-                        "z_pass": 134.249216e6 + 21.008896e6},
+    "source_hash": "02f4709334e711dc",
+    "aniso_ho_3d_256": {"x_pass": 201.362944e6 + 36.269312e6, "y_pass": 134.249216e6 + 18.558976e6,
+                        "z_pass": 134.249216e6 + 19.057920e6},
 }
 TRAFFIC_SOURCES = ["paper_1805_03155_gb300/csrc/pass_tma.cuh", "paper_1805_03155_gb300/csrc/fft_line.cuh",
                    "paper_1805_03155_gb300/csrc/tma.cuh", "paper_1805_03155_gb300/csrc/pass_tma_launch.h"]
@@ -390,6 +389,8 @@ def main():
     ap.add_argument("--workload", default="aniso_ho_3d_256", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-plain and serving legs")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the default pass schedules (no autotuning launches; for profiler launch lists)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -418,7 +419,7 @@ def main():
     s = spstd.solver_for(problem, precision=prec, probe_capacity=total_steps, stream=stream, device=local)
     N = problem.n_total
     # autotune the pass schedules on this grid (outside the timed region)
-    tune_ms = s.spstd_tune(reps=10)
+    tune_ms = s.spstd_tune(reps=10) if not args.no_tune else np.full((3, spstd.SCHEDULES), -1.0)
     schedules = [s.spstd_get_schedule(a) for a in range(problem.dims)]
     xy_fused = s.spstd_get_xy_fusion()
 
