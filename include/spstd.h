@@ -232,12 +232,15 @@ spstd_status spstd_profile_steps(spstd_ctx *ctx, int64_t nsteps, double *ms, int
 /* Schedules: the radix and tile plan of an axis's pass kernel (no effect on
  * what is computed; Eq. 10's transform in a different shape).
  *   0  the axis's default kernel (the pipelined TMA pass for FP32 2D/3D axes
- *      of 64..256 points, else the plain pass: 16 FP32 / 8 FP64 points per
+ *      of 64..256 points, whose destination field is accumulated at L2 by a
+ *      TMA reduce-add, else the plain pass: 16 FP32 / 8 FP64 points per
  *      thread, about 256 threads per block)
  *   1  plain pass, half the lines per block
  *   2  plain pass, twice the lines per block
  *   3  plain pass, half the points per thread (one radix lower per stage)
  *   4  plain pass, default plan (listed only where 0 is the TMA pass)
+ *   5  TMA pass that loads the destination tile into shared memory, adds
+ *      there and stores it back (listed only where 0 is the TMA pass)
  * Schedules 1..3 exist for FFT axes of 32..512 points.  0, 1, 2 and 4 give
  * bit-identical results on plain axes; 3 changes the rounding (FP32 ~1e-7).
  * spstd_schedule_candidates lists the schedules axis (0..dims-1) can run in
@@ -249,7 +252,7 @@ spstd_status spstd_profile_steps(spstd_ctx *ctx, int64_t nsteps, double *ms, int
  * not NULL, writes the mean milliseconds per pass to ms[axis * SPSTD_SCHEDULES
  * + schedule] (-1 where not a candidate).  It synchronises and leaves psi_R,
  * psi_I, the probes and the step count unchanged. */
-#define SPSTD_SCHEDULES 5
+#define SPSTD_SCHEDULES 6
 spstd_status spstd_schedule_candidates(const spstd_ctx *ctx, int axis, int *list, int *count);
 spstd_status spstd_get_schedule(const spstd_ctx *ctx, int axis, int *schedule);
 spstd_status spstd_set_schedule(spstd_ctx *ctx, int axis, int schedule);

@@ -362,6 +362,7 @@ struct spstd_ctx {
     // pipelined FP32 passes: tensor maps [field: psi_R, psi_I, tmp][view: x, y, z]
     bool tma[3] = {false, false, false};
     CUtensorMap tmap[3][3];
+    CUtensorMap xrmap[4];  // x view of psi_R, psi_I, tmp, V with the reduce-add x pass's tile height
     spstd_batch *batch = nullptr;  // batch this context is a member of
     bool dense[3] = {false, false, false};  // axis applies the dense operator
     bool long_x = false;                    // x axis runs the four-step pass
@@ -601,6 +602,12 @@ void setup_tma(spstd_ctx *ctx)
             void *base = ctx->ptr(ctx->field_off(f));
             if (v == 0)
                 ok = encode_map(&ctx->tmap[f][0], base, n0, n1 * n2, 1, (uint32_t)n0, tma_rows_per_tile(), 1, false);
+            if (v == 0)
+                ok = ok && encode_map(&ctx->xrmap[f], base, n0, n1 * n2, 1, (uint32_t)n0, (uint32_t)tmared_x_rows(),
+                                      1, false);
+            if (v == 0 && f == 0)
+                ok = ok && encode_map(&ctx->xrmap[3], ctx->ptr(ctx->L.V), n0, n1 * n2, 1, (uint32_t)n0,
+                                      (uint32_t)tmared_x_rows(), 1, false);
             if (v == 1)
                 ok = encode_map(&ctx->tmap[f][1], base, n0, n1, n2, tma_cols_per_tile(), (uint32_t)n1, 1, false);
             if (v == 2)
@@ -796,7 +803,7 @@ cudaError_t enqueue_apply(spstd_ctx *ctx, int fsrc, int fdst, int table, double 
         }
         const cpx<T> *tw = (const cpx<T> *)ctx->ptr(ctx->L.tw[ax]);
         if constexpr (sizeof(T) == 4) {
-            if (ctx->tma[ax] && sv == 0 && fsrc <= 2 && fdst <= 2) {
+            if (ctx->tma[ax] && (sv == 0 || sv == 5) && fsrc <= 2 && fdst <= 2) {
                 TmaPassArgs ta{};
                 ta.tw = (const float2 *)tw;
                 ta.mult = (const float *)(mult + off[ax]);
@@ -813,7 +820,15 @@ cudaError_t enqueue_apply(spstd_ctx *ctx, int fsrc, int fdst, int table, double 
                     ta.n_xt = (int)((n0 + tma_cols_per_tile() - 1) / tma_cols_per_tile());
                     ta.n_tiles = ta.n_xt * (int)(ax == 1 ? n2 : n1);
                 }
-                SPSTD_TIMED(timer, s, ax, launch_pass_tma(ax, (int)N, ctx->tmap[fsrc][ax], ctx->tmap[fdst][ax], ta, s));
+                if (sv == 5)
+                    SPSTD_TIMED(timer, s, ax,
+                                launch_pass_tma(ax, (int)N, ctx->tmap[fsrc][ax], ctx->tmap[fdst][ax], ta, s));
+                else
+                    SPSTD_TIMED(timer, s, ax,
+                                ax == 0 ? launch_pass_tmared(0, (int)N, ctx->xrmap[fsrc], ctx->xrmap[3],
+                                                             ctx->xrmap[fdst], ta, s)
+                                        : launch_pass_tmared(ax, (int)N, ctx->tmap[fsrc][ax], ctx->xrmap[3],
+                                                             ctx->tmap[fdst][ax], ta, s));
                 continue;
             }
         }
@@ -1025,7 +1040,10 @@ spstd_status prepare_kernels(spstd_ctx *ctx)
     if (cfg.dims == 3 && !ctx->dense[2]) SPSTD_CU(ctx, Launch<T>::spass((int)cfg.n[2], none, ctx->stream));
     if (ctx->fuse_xy) SPSTD_CU(ctx, prepare_xypass_tma((int)cfg.n[0]));
     for (int ax = 0; ax < cfg.dims; ++ax) {
-        if (ctx->tma[ax]) SPSTD_CU(ctx, prepare_pass_tma(ax, (int)cfg.n[ax]));
+        if (ctx->tma[ax]) {
+            SPSTD_CU(ctx, prepare_pass_tmared(ax, (int)cfg.n[ax]));
+            SPSTD_CU(ctx, prepare_pass_tma(ax, (int)cfg.n[ax]));
+        }
         const int sv = ctx->sched[ax];
         if (sv >= 1 && sv <= 3) {
             PassArgs<T> z{};
@@ -2225,7 +2243,7 @@ const char *spstd_batch_last_error(const spstd_batch *b)
 namespace {
 
 // Schedules an axis of this context can run (sched.h): 0 always; 1..3 for
-// plain FFT passes of tunable length; 4 where 0 is the pipelined TMA pass.
+// plain FFT passes of tunable length; 4 and 5 where 0 is the pipelined TMA pass.
 int schedule_candidates(const spstd_ctx *ctx, int ax, int *list)
 {
     int n = 0;
@@ -2236,7 +2254,10 @@ int schedule_candidates(const spstd_ctx *ctx, int ax, int *list)
         const bool ok = ctx->cfg.precision == 32 ? sched_valid<float>(ax, N, v) : sched_valid<double>(ax, N, v);
         if (ok) list[n++] = v;
     }
-    if (ctx->tma[ax]) list[n++] = 4;
+    if (ctx->tma[ax]) {
+        list[n++] = 4;
+        list[n++] = 5;
+    }
     return n;
 }
 

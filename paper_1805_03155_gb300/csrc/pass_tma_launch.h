@@ -31,6 +31,15 @@ cudaError_t launch_pass_tma(int axis, int N, const CUtensorMap &msrc, const CUte
 // The same set-up without a launch (call before a stream capture).
 cudaError_t prepare_pass_tma(int axis, int N);
 
+// Reduce-add variants (the dst tile is accumulated by a TMA reduce at L2
+// instead of being loaded and stored): mV is the potential in the x view
+// (x pass only; unused otherwise).
+cudaError_t launch_pass_tmared(int axis, int N, const CUtensorMap &msrc, const CUtensorMap &mV,
+                               const CUtensorMap &mdst, const TmaPassArgs &a, cudaStream_t s);
+cudaError_t prepare_pass_tmared(int axis, int N);
+// Rows per tile of the reduce-add x pass (its x-view maps use this box height).
+int tmared_x_rows();
+
 struct XyPassArgs;
 // x and y passes of a 3D half-stage in one persistent launch (pass_xy.cuh);
 // nx = ny = N in {64, 128, 256}; maps: src and dst in the x view (N x 32-row

@@ -1,6 +1,7 @@
 // sched.h -- schedules (radix and tile plans) of the plain pass kernels, the
 // choices the autotuner times.  A schedule is chosen per axis:
-//   0  the default kernel of the axis (the pipelined TMA pass where one exists,
+//   0  the default kernel of the axis (the pipelined TMA pass with its
+//      reduce-add epilogue where one exists,
 //      else the plain pass with E = 16 FP32 / 8 FP64 points per thread and
 //      about 256 threads per block)
 //   1  plain, half the lines per block
@@ -8,6 +9,7 @@
 //   3  plain, half the points per thread (one radix lower per stage), half
 //      the lines per block
 //   4  plain, the default plan (differs from 0 only on TMA axes)
+//   5  the TMA pass with loaded and stored destination tiles (TMA axes only)
 // Schedules 1..3 exist for lines of kSchedMinN..kSchedMaxN points; 1, 2 and 4
 // run exactly the arithmetic of the default plain kernel (same results bit for
 // bit), 3 changes the radix sequence and so the rounding.
@@ -20,7 +22,7 @@
 
 namespace spstd {
 
-constexpr int kSchedules = 5;
+constexpr int kSchedules = 6;
 constexpr int kSchedMinN = 32;
 constexpr int kSchedMaxN = 512;
 

@@ -81,6 +81,17 @@ __device__ __forceinline__ void tma_store_3d(const CUtensorMap *map, int x, int 
                  : "memory");
 }
 
+// Shared -> global element-wise f32 add of a tile (3D tensor map) into the
+// current bulk group: global[i] += smem[i], performed at L2, so the SM never
+// loads the destination.  Box elements outside the tensor are not touched.
+__device__ __forceinline__ void tma_reduce_add_3d(const CUtensorMap *map, int x, int y, int z, const void *smem_src)
+{
+    asm volatile("cp.reduce.async.bulk.tensor.3d.global.shared::cta.add.tile.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y), "r"(z), "r"(smem_u32(smem_src))
+                 : "memory");
+}
+
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 
 // Wait until at most N committed bulk groups still read their shared source.

@@ -78,6 +78,8 @@ def test_set_schedule_rejects_unknown():
 
 @pytest.mark.parametrize("precision", [32, 64])
 def test_tune_keeps_state_and_picks_a_candidate(precision):
+    from paper_1805_03155_gb300 import spstd
+
     p = stable(inputs.gaussian_problem((64, 128, 32), steps=6))
     s = gpu_solver(p, precision, cap=16)
     s.spstd_step(3)
@@ -90,7 +92,7 @@ def test_tune_keeps_state_and_picks_a_candidate(precision):
         cand = s.spstd_schedule_candidates(ax)
         chosen = s.spstd_get_schedule(ax)
         assert chosen in cand
-        for v in range(5):
+        for v in range(spstd.SCHEDULES):
             assert (ms[ax, v] > 0) == (v in cand)
         assert ms[ax, chosen] == min(ms[ax, v] for v in cand)
     s.spstd_step(3)
