@@ -350,8 +350,10 @@ spstd_status spstd_batch_sync(spstd_batch *b);
 spstd_status spstd_batch_launch_count(const spstd_batch *b, int64_t nsteps, int64_t *launches);
 const char *spstd_batch_last_error(const spstd_batch *b);
 /* Autotunes the batched passes: for every 2D/3D member shape and axis, times
- * the batched pass under schedules 0..3 (0 = the default plain plan) over all
- * members of that shape -- H applied into each member's scratch field, once to
+ * the batched pass under schedules 0..4 over all members of that shape
+ * (0 = the default: the pipelined TMA reduce-add pass over every member's
+ * tiles for FP32 axes of 64..256 points, else the plain plan; 1..3 as for a
+ * lone context; 4 = the plain plan where 0 is the TMA pass) -- H applied into each member's scratch field, once to
  * warm up then reps times -- and keeps the fastest.  The choice is kept per
  * shape (precision, dims, n) for as long as the batch lives, including members
  * added later; the states are not touched.  Synchronises the batch stream. */

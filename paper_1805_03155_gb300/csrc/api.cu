@@ -360,9 +360,14 @@ struct spstd_ctx {
     cudaGraphExec_t gexec = nullptr;
     std::string err;
     // pipelined FP32 passes: tensor maps [field: psi_R, psi_I, tmp][view: x, y, z]
+    // default (reduce-add) passes: tma[axis]; x view of psi_R, psi_I, tmp, V;
+    // y and z views of the fields, with the boxes of pass_tmared.cuh
     bool tma[3] = {false, false, false};
+    CUtensorMap xrmap[4];
+    CUtensorMap srmap[3][2];
+    // stored-tile passes (schedule 5, fused x-y): tma_st[axis]; [field][view]
+    bool tma_st[3] = {false, false, false};
     CUtensorMap tmap[3][3];
-    CUtensorMap xrmap[4];  // x view of psi_R, psi_I, tmp, V with the reduce-add x pass's tile height
     spstd_batch *batch = nullptr;  // batch this context is a member of
     bool dense[3] = {false, false, false};  // axis applies the dense operator
     bool long_x = false;                    // x axis runs the four-step pass
@@ -586,32 +591,70 @@ bool encode_map(CUtensorMap *m, void *base, uint64_t d0, uint64_t d1, uint64_t d
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// Enables the pipelined passes for FP32 axes of 64..256 points.
+// 4D FP32 tensor map (dims d[0] fastest; strides of dims 1..3 in elements)
+// with the given box; out-of-range box elements load as zero and are not
+// written back.
+bool encode_map4(CUtensorMap *m, void *base, const uint64_t *d, const uint64_t *stride, const uint32_t *box)
+{
+    auto enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[4] = {d[0], d[1], d[2], d[3]};
+    const cuuint64_t strides[3] = {stride[0] * sizeof(float), stride[1] * sizeof(float), stride[2] * sizeof(float)};
+    const cuuint32_t bx[4] = {box[0], box[1], box[2], box[3]};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, bx, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Maps of the reduce-add passes (pass_tmared.cuh): the line axis of length N
+// is split as (L1, L2) = (min(N, 256), N / L1) so that no box dimension
+// exceeds 256.  v = 0: x view (x_lo, x_hi, row, 1); v = 1: y view (x, y_lo,
+// y_hi, z); v = 2: z view (x, y, z_lo, z_hi).
+bool encode_red_map(CUtensorMap *m, void *base, const int64_t *n, int v)
+{
+    const uint64_t n0 = n[0], n1 = n[1], n2 = n[2];
+    const uint64_t N = (uint64_t)n[v], L1 = N < 256 ? N : 256, L2 = N / L1;
+    if (v == 0) {
+        const uint64_t d[4] = {L1, L2, n1 * n2, 1}, st[3] = {L1, n0, n0 * n1 * n2};
+        const uint32_t box[4] = {(uint32_t)L1, (uint32_t)L2, (uint32_t)tmared_rows_x((int)N), 1};
+        return encode_map4(m, base, d, st, box);
+    }
+    const uint32_t cols = 2u * (uint32_t)tmared_pairs((int)N, (int64_t)n0);
+    if (v == 1) {
+        const uint64_t d[4] = {n0, L1, L2, n2}, st[3] = {n0, n0 * L1, n0 * n1};
+        const uint32_t box[4] = {cols, (uint32_t)L1, (uint32_t)L2, 1};
+        return encode_map4(m, base, d, st, box);
+    }
+    const uint64_t d[4] = {n0, n1, L1, L2}, st[3] = {n0, n0 * n1, n0 * n1 * L1};
+    const uint32_t box[4] = {cols, 1, (uint32_t)L1, (uint32_t)L2};
+    return encode_map4(m, base, d, st, box);
+}
+
+// Enables the pipelined passes for FP32 axes of 64..512 points.
 void setup_tma(spstd_ctx *ctx)
 {
     const spstd_config &cfg = ctx->cfg;
     if (cfg.precision != 32 || cfg.dims < 2) return;
     const uint64_t n0 = cfg.n[0], n1 = cfg.n[1], n2 = cfg.n[2];
-    auto eligible = [](int64_t n) { return n == 64 || n == 128 || n == 256; };
-    bool want[3] = {eligible(cfg.n[0]) && !ctx->dense[0], eligible(cfg.n[1]) && !ctx->dense[1],
-                    cfg.dims == 3 && eligible(cfg.n[2]) && !ctx->dense[2]};
-    for (int v = 0; v < 3; ++v) {
-        if (!want[v]) continue;
-        bool ok = true;
+    auto stored_ok = [](int64_t n) { return n == 64 || n == 128 || n == 256; };
+    for (int v = 0; v < cfg.dims; ++v) {
+        if (ctx->dense[v]) continue;
+        // stored-tile passes (schedule 5 and the fused x-y pass): 32-row / 32-column boxes
+        bool ok = stored_ok(cfg.n[v]);
         for (int f = 0; f < 3 && ok; ++f) {
             void *base = ctx->ptr(ctx->field_off(f));
-            if (v == 0)
-                ok = encode_map(&ctx->tmap[f][0], base, n0, n1 * n2, 1, (uint32_t)n0, tma_rows_per_tile(), 1, false);
-            if (v == 0)
-                ok = ok && encode_map(&ctx->xrmap[f], base, n0, n1 * n2, 1, (uint32_t)n0, (uint32_t)tmared_x_rows(),
-                                      1, false);
-            if (v == 0 && f == 0)
-                ok = ok && encode_map(&ctx->xrmap[3], ctx->ptr(ctx->L.V), n0, n1 * n2, 1, (uint32_t)n0,
-                                      (uint32_t)tmared_x_rows(), 1, false);
-            if (v == 1)
-                ok = encode_map(&ctx->tmap[f][1], base, n0, n1, n2, tma_cols_per_tile(), (uint32_t)n1, 1, false);
-            if (v == 2)
-                ok = encode_map(&ctx->tmap[f][2], base, n0, n1, n2, tma_cols_per_tile(), 1, (uint32_t)n2, false);
+            if (v == 0) ok = encode_map(&ctx->tmap[f][0], base, n0, n1 * n2, 1, (uint32_t)n0, tma_rows_per_tile(), 1, false);
+            if (v == 1) ok = encode_map(&ctx->tmap[f][1], base, n0, n1, n2, tma_cols_per_tile(), (uint32_t)n1, 1, false);
+            if (v == 2) ok = encode_map(&ctx->tmap[f][2], base, n0, n1, n2, tma_cols_per_tile(), 1, (uint32_t)n2, false);
+        }
+        ctx->tma_st[v] = ok;
+        // reduce-add passes (the default): boxes sized per line length
+        ok = tmared_eligible(cfg.n[v]) && (v == 0 || tmared_pairs((int)cfg.n[v], cfg.n[0]) > 0);
+        for (int f = 0; f < 4 && ok; ++f) {
+            void *base = f < 3 ? ctx->ptr(ctx->field_off(f)) : ctx->ptr(ctx->L.V);
+            if (v == 0) ok = encode_red_map(&ctx->xrmap[f], base, cfg.n, 0);
+            else if (f < 3) ok = encode_red_map(&ctx->srmap[f][v - 1], base, cfg.n, v);
         }
         ctx->tma[v] = ok;
     }
@@ -803,7 +846,8 @@ cudaError_t enqueue_apply(spstd_ctx *ctx, int fsrc, int fdst, int table, double 
         }
         const cpx<T> *tw = (const cpx<T> *)ctx->ptr(ctx->L.tw[ax]);
         if constexpr (sizeof(T) == 4) {
-            if (ctx->tma[ax] && (sv == 0 || sv == 5) && fsrc <= 2 && fdst <= 2) {
+            const bool red = ctx->tma[ax] && sv == 0, st = ctx->tma_st[ax] && sv == 5;
+            if ((red || st) && fsrc <= 2 && fdst <= 2) {
                 TmaPassArgs ta{};
                 ta.tw = (const float2 *)tw;
                 ta.mult = (const float *)(mult + off[ax]);
@@ -814,21 +858,27 @@ cudaError_t enqueue_apply(spstd_ctx *ctx, int fsrc, int fdst, int table, double 
                 ta.axis = ax;
                 ta.reverse = rev;
                 ta.status = status;
-                if (ax == 0) {
-                    ta.n_tiles = (int)((n1 * n2 + tma_rows_per_tile() - 1) / tma_rows_per_tile());
+                ta.nx = (int)n0;
+                if (red) {
+                    ta.n_tiles = tmared_tiles(ax, cfg.n, &ta.n_xt);
+                    if (ax == 0)
+                        SPSTD_TIMED(timer, s, ax,
+                                    launch_pass_tmared(0, (int)N, ctx->xrmap[fsrc], ctx->xrmap[3], ctx->xrmap[fdst],
+                                                       ta, s));
+                    else
+                        SPSTD_TIMED(timer, s, ax,
+                                    launch_pass_tmared(ax, (int)N, ctx->srmap[fsrc][ax - 1], ctx->xrmap[3],
+                                                       ctx->srmap[fdst][ax - 1], ta, s));
                 } else {
-                    ta.n_xt = (int)((n0 + tma_cols_per_tile() - 1) / tma_cols_per_tile());
-                    ta.n_tiles = ta.n_xt * (int)(ax == 1 ? n2 : n1);
-                }
-                if (sv == 5)
+                    if (ax == 0) {
+                        ta.n_tiles = (int)((n1 * n2 + tma_rows_per_tile() - 1) / tma_rows_per_tile());
+                    } else {
+                        ta.n_xt = (int)((n0 + tma_cols_per_tile() - 1) / tma_cols_per_tile());
+                        ta.n_tiles = ta.n_xt * (int)(ax == 1 ? n2 : n1);
+                    }
                     SPSTD_TIMED(timer, s, ax,
                                 launch_pass_tma(ax, (int)N, ctx->tmap[fsrc][ax], ctx->tmap[fdst][ax], ta, s));
-                else
-                    SPSTD_TIMED(timer, s, ax,
-                                ax == 0 ? launch_pass_tmared(0, (int)N, ctx->xrmap[fsrc], ctx->xrmap[3],
-                                                             ctx->xrmap[fdst], ta, s)
-                                        : launch_pass_tmared(ax, (int)N, ctx->tmap[fsrc][ax], ctx->xrmap[3],
-                                                             ctx->tmap[fdst][ax], ta, s));
+                }
                 continue;
             }
         }
@@ -1040,10 +1090,8 @@ spstd_status prepare_kernels(spstd_ctx *ctx)
     if (cfg.dims == 3 && !ctx->dense[2]) SPSTD_CU(ctx, Launch<T>::spass((int)cfg.n[2], none, ctx->stream));
     if (ctx->fuse_xy) SPSTD_CU(ctx, prepare_xypass_tma((int)cfg.n[0]));
     for (int ax = 0; ax < cfg.dims; ++ax) {
-        if (ctx->tma[ax]) {
-            SPSTD_CU(ctx, prepare_pass_tmared(ax, (int)cfg.n[ax]));
-            SPSTD_CU(ctx, prepare_pass_tma(ax, (int)cfg.n[ax]));
-        }
+        if (ctx->tma[ax]) SPSTD_CU(ctx, prepare_pass_tmared(ax, (int)cfg.n[ax], cfg.n[0]));
+        if (ctx->tma_st[ax]) SPSTD_CU(ctx, prepare_pass_tma(ax, (int)cfg.n[ax]));
         const int sv = ctx->sched[ax];
         if (sv >= 1 && sv <= 3) {
             PassArgs<T> z{};
@@ -1724,9 +1772,12 @@ struct BatchGroupND {
     std::vector<int> slots;
     int nh;
     int tiles[3];
-    int sched[3];      // pass schedule per axis (0..3, sched.h)
+    int sched[3];      // pass schedule per axis (0..4; 0 is the TMA pass where tma[ax])
+    bool tma[3];       // axis can run the batched reduce-add TMA pass
     size_t args_off;   // PassArgs<T> [nh * dims][M]
     size_t probe_off;  // ProbeMember<T> [M]
+    size_t tma_off;    // TmaMember [M] (when any tma[ax])
+    const void *tw[3]; // twiddle table per axis (identical in every member; the first member's)
 };
 
 }  // namespace
@@ -1838,10 +1889,16 @@ size_t put(std::vector<unsigned char> &img, const void *src, size_t bytes)
     return off;
 }
 
-// Blocks per member of a batched pass of axis ax under schedule v.
+// Whether schedule v of axis ax runs the batched TMA pass.
+bool group_uses_tma(const BatchGroupND &g, int ax, int v) { return v == 0 && g.tma[ax]; }
+
+// Blocks per member of a batched pass of axis ax under schedule v (4: the
+// plain default where 0 is the TMA pass).
 template <typename T>
 int group_tiles(const BatchGroupND &g, int ax, int v)
 {
+    if (group_uses_tma(g, ax, v)) return tmared_tiles(ax, g.n, nullptr);
+    if (v == 4) v = 0;
     if (ax == 0)
         return v ? xpass_tiles_sched<T>((int)g.n[0], v, g.n[1] * g.n[2])
                  : Launch<T>::xpass_tiles((int)g.n[0], g.n[1] * g.n[2]);
@@ -1850,11 +1907,32 @@ int group_tiles(const BatchGroupND &g, int ax, int v)
              : Launch<T>::spass_tiles((int)g.n[ax], (int)g.n[0], outer);
 }
 
-// One batched pass of axis ax under schedule v (no work: raises the smem limit).
+// One batched pass of axis ax under schedule v (no work: raises the smem
+// limit).  The TMA pass reads field src (or 1 - dst when src < 0) of each
+// member through mem and accumulates into field dst.
 template <typename T>
-cudaError_t group_pass(const BatchGroupND &g, int ax, int v, const PassArgs<T> *a, int M, int tiles, cudaStream_t s)
+cudaError_t group_pass(const BatchGroupND &g, int ax, int v, const PassArgs<T> *a, int M, int tiles, cudaStream_t s,
+                       const TmaMember *mem = nullptr, int src = -1, int dst = 0)
 {
     const int N = (int)g.n[ax];
+    if constexpr (sizeof(T) == 4) {
+        if (group_uses_tma(g, ax, v)) {
+            if (!a) return prepare_pass_tmared_batch(ax, N, g.n[0]);
+            TmaBatchArgs ta{};
+            ta.mem = mem;
+            ta.pa = a;
+            ta.tw = (const float2 *)g.tw[ax];
+            ta.src = src;
+            ta.dst = dst;
+            ta.members = M;
+            ta.tiles = tiles;
+            tmared_tiles(ax, g.n, &ta.n_xt);
+            ta.nx = (int)g.n[0];
+            ta.axis = ax;
+            return launch_pass_tmared_batch(ax, N, ta, s);
+        }
+    }
+    if (v == 4) v = 0;
     if (ax == 0) return v ? xpass_batch_sched<T>(N, v, a, M, tiles, s) : Launch<T>::xpass_batch(N, a, M, tiles, s);
     return v ? spass_batch_sched<T>(N, v, a, M, tiles, s) : Launch<T>::spass_batch(N, a, M, tiles, s);
 }
@@ -1876,6 +1954,38 @@ void build_nd_descriptors(spstd_batch *b, BatchGroupND &g, std::vector<unsigned 
     }
     g.args_off = put(img, args.data(), sizeof(PassArgs<T>) * args.size());
     g.probe_off = put(img, pm.data(), sizeof(ProbeMember<T>) * pm.size());
+    // batched TMA passes: FP32 axes where every member has its tensor maps and
+    // 16-byte aligned multiplier rows (the stage's bulk copy needs both)
+    bool any = false;
+    for (int ax = 0; ax < 3; ++ax) {
+        g.tw[ax] = b->slots[g.slots[0]]->ptr(b->slots[g.slots[0]]->L.tw[ax]);
+        bool ok = sizeof(T) == 4 && ax < g.dims;
+        for (int i = 0; i < M && ok; ++i) {
+            spstd_ctx *ctx = b->slots[g.slots[i]];
+            ok = ctx->tma[ax];
+            for (int h = 0; h < g.nh && ok; ++h)
+                ok = ((uintptr_t)args[((size_t)h * g.dims + ax) * M + i].mult & 15) == 0;
+        }
+        g.tma[ax] = ok;
+        any |= ok;
+    }
+    g.tma_off = 0;
+    if (any) {
+        std::vector<TmaMember> tm(M);
+        for (int i = 0; i < M; ++i) {
+            spstd_ctx *ctx = b->slots[g.slots[i]];
+            TmaMember &t = tm[i];
+            std::memset(&t, 0, sizeof(t));
+            for (int f = 0; f < 4; ++f)
+                if (g.tma[0]) t.x[f] = ctx->xrmap[f];
+            for (int f = 0; f < 3; ++f) {
+                if (g.tma[1]) t.y[f] = ctx->srmap[f][0];
+                if (g.tma[2]) t.z[f] = ctx->srmap[f][1];
+            }
+            t.status = (int *)ctx->ptr(ctx->L.status);
+        }
+        g.tma_off = put(img, tm.data(), sizeof(TmaMember) * tm.size());
+    }
     for (int ax = 0; ax < g.dims; ++ax) g.tiles[ax] = group_tiles<T>(g, ax, g.sched[ax]);
 }
 
@@ -1959,10 +2069,12 @@ cudaError_t enqueue_group_step(spstd_batch *b, const BatchGroupND &g, cudaStream
 {
     const int M = (int)g.slots.size();
     const PassArgs<T> *args = (const PassArgs<T> *)(b->ws + g.args_off);
+    const TmaMember *mem = (const TmaMember *)(b->ws + g.tma_off);
+    const spstd_ctx *first = b->slots[g.slots[0]];
     for (int h = 0; h < g.nh; ++h) {
         for (int ax = 0; ax < g.dims; ++ax) {
             const PassArgs<T> *a = args + ((size_t)h * g.dims + ax) * M;
-            cudaError_t e = group_pass<T>(g, ax, g.sched[ax], a, M, g.tiles[ax], s);
+            cudaError_t e = group_pass<T>(g, ax, g.sched[ax], a, M, g.tiles[ax], s, mem, -1, first->hs[h].dst);
             if (e != cudaSuccess) return e;
         }
     }
@@ -2254,10 +2366,8 @@ int schedule_candidates(const spstd_ctx *ctx, int ax, int *list)
         const bool ok = ctx->cfg.precision == 32 ? sched_valid<float>(ax, N, v) : sched_valid<double>(ax, N, v);
         if (ok) list[n++] = v;
     }
-    if (ctx->tma[ax]) {
-        list[n++] = 4;
-        list[n++] = 5;
-    }
+    if (ctx->tma[ax]) list[n++] = 4;
+    if (ctx->tma[ax] && ctx->tma_st[ax]) list[n++] = 5;
     return n;
 }
 
@@ -2306,7 +2416,7 @@ spstd_status tune_impl(spstd_ctx *ctx, int reps, double *ms)
         ctx->sched[ax] = best;
     }
     // x and y as one launch or two: time a whole H-apply each way
-    if (st == SPSTD_OK && xy_fusable(ctx->cfg) && ctx->tma[0] && ctx->tma[1] && ctx->sched[0] == 0 &&
+    if (st == SPSTD_OK && xy_fusable(ctx->cfg) && ctx->tma_st[0] && ctx->tma_st[1] && ctx->sched[0] == 0 &&
         ctx->sched[1] == 0) {
         double t2[2] = {0, 0};
         for (int f = 0; f < 2 && st == SPSTD_OK; ++f) {
@@ -2351,12 +2461,16 @@ spstd_status tune_group(spstd_batch *b, BatchGroupND &g, int reps, cudaEvent_t e
         SPSTD_BCU(b, cudaMemcpyAsync(dargs, args.data(), sizeof(PassArgs<T>) * M, cudaMemcpyHostToDevice, b->stream));
         int best = 0;
         double best_ms = 0.0;
-        for (int v = 0; v <= 3; ++v) {
-            if (v && !sched_valid<T>(ax, (int)g.n[ax], v)) continue;
+        const TmaMember *mem = (const TmaMember *)(b->ws + g.tma_off);
+        const int fsrc = 1 - b->slots[g.slots[0]]->hs[0].dst;
+        for (int v = 0; v <= 4; ++v) {
+            if (v >= 1 && v <= 3 && !sched_valid<T>(ax, (int)g.n[ax], v)) continue;
+            if (v == 4 && !g.tma[ax]) continue;
             const int tiles = group_tiles<T>(g, ax, v);
-            SPSTD_BCU(b, group_pass<T>(g, ax, v, dargs, M, tiles, b->stream));
+            SPSTD_BCU(b, group_pass<T>(g, ax, v, dargs, M, tiles, b->stream, mem, fsrc, 2));
             SPSTD_BCU(b, cudaEventRecord(e0, b->stream));
-            for (int r = 0; r < reps; ++r) SPSTD_BCU(b, group_pass<T>(g, ax, v, dargs, M, tiles, b->stream));
+            for (int r = 0; r < reps; ++r)
+                SPSTD_BCU(b, group_pass<T>(g, ax, v, dargs, M, tiles, b->stream, mem, fsrc, 2));
             SPSTD_BCU(b, cudaEventRecord(e1, b->stream));
             SPSTD_BCU(b, cudaEventSynchronize(e1));
             float t = 0.f;
@@ -2417,7 +2531,7 @@ spstd_status spstd_set_schedule(spstd_ctx *ctx, int axis, int schedule)
 spstd_status spstd_set_xy_fusion(spstd_ctx *ctx, int on)
 {
     if (!ctx) return SPSTD_EINVAL;
-    const bool can = xy_fusable(ctx->cfg) && ctx->tma[0] && ctx->tma[1];
+    const bool can = xy_fusable(ctx->cfg) && ctx->tma_st[0] && ctx->tma_st[1];
     if (on && !can) return fail(ctx, SPSTD_EUNSUPPORTED, "x-y fusion needs a 3D FP32 grid with nx = ny in {64, 128, 256}");
     if (ctx->fuse_xy != (on != 0)) {
         ctx->fuse_xy = on != 0;

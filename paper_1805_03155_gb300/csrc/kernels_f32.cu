@@ -3,35 +3,12 @@
 #include "pass_tma.cuh"
 #include "pass_tma_launch.h"
 #include "pass_xy.cuh"
+#include "persist.cuh"
 
 namespace spstd {
 template struct Launch<float>;
 
 namespace {
-
-// Persistent grid size per (kernel, device): SMs x resident blocks per SM.
-template <auto Kernel>
-cudaError_t persistent_grid(int threads, size_t smem, int *grid)
-{
-    static int cached[64] = {0};
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (!cached[dev]) {
-        e = cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        int sms = 0, per = 0;
-        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, Kernel, threads, smem);
-        if (e != cudaSuccess) return e;
-        if (per < 1) return cudaErrorInvalidConfiguration;
-        cached[dev] = sms * per;
-    }
-    *grid = cached[dev];
-    return cudaSuccess;
-}
 
 // Complex points per thread of the pipelined x and strided passes.
 template <int N>
@@ -80,59 +57,6 @@ cudaError_t pass_any(int axis, int N, const CUtensorMap *ms, const CUtensorMap *
     }
 }
 
-// Reduce-add passes: the x pass takes tiles of 16 rows, two blocks per SM
-// (3-stage rings of src + V tiles); the strided passes take two blocks per SM
-// (3-stage rings of 32-column src tiles).  Measured at 256^3 against one block
-// of 32-row tiles per SM: x 0.047 vs 0.051 ms, y 0.030 vs 0.033 ms.
-constexpr int kRedRowsX = 16;
-constexpr int kRedBlocksX = 2;
-constexpr int kRedBlocksS = 2;
-
-template <int N, int ROWS, int B>
-cudaError_t redx_n(const CUtensorMap *ms, const CUtensorMap *mv, const CUtensorMap *md, const TmaPassArgs *a,
-                   cudaStream_t s)
-{
-    constexpr int E = tma_e_x<N>(), TT = N / E;
-    constexpr size_t smem = tmared_pass_smem<N, ROWS * N, 2, B>();
-    int grid = 0;
-    cudaError_t e = persistent_grid<xpass_tmared_kernel<N, E, ROWS, B>>((ROWS / 2) * TT, smem, &grid);
-    if (e != cudaSuccess || !a) return e;
-    TmaPassArgs b = *a;
-    b.n_tiles = (b.rows + ROWS - 1) / ROWS;
-    if (b.n_tiles < grid) grid = b.n_tiles;
-    if (grid <= 0) return cudaSuccess;
-    xpass_tmared_kernel<N, E, ROWS, B><<<grid, dim3(TT, ROWS / 2), smem, s>>>(*ms, *mv, *md, b);
-    return cudaGetLastError();
-}
-
-template <int N>
-cudaError_t red_n(int axis, const CUtensorMap *ms, const CUtensorMap *mv, const CUtensorMap *md,
-                  const TmaPassArgs *a, cudaStream_t s)
-{
-    if (axis == 0) return redx_n<N, kRedRowsX, kRedBlocksX>(ms, mv, md, a, s);
-    constexpr int E = tma_e_s<N>(), TT = N / E;
-    constexpr int B = kRedBlocksS;
-    constexpr size_t smem = tmared_pass_smem<N, kTmaCols * N, 1, B>();
-    int grid = 0;
-    cudaError_t e = persistent_grid<spass_tmared_kernel<N, E, B>>(16 * TT, smem, &grid);
-    if (e != cudaSuccess || !a) return e;
-    if (a->n_tiles < grid) grid = a->n_tiles;
-    if (grid <= 0) return cudaSuccess;
-    spass_tmared_kernel<N, E, B><<<grid, dim3(16, TT), smem, s>>>(*ms, *md, *a);
-    return cudaGetLastError();
-}
-
-cudaError_t red_any(int axis, int N, const CUtensorMap *ms, const CUtensorMap *mv, const CUtensorMap *md,
-                    const TmaPassArgs *a, cudaStream_t s)
-{
-    switch (N) {
-    case 64: return red_n<64>(axis, ms, mv, md, a, s);
-    case 128: return red_n<128>(axis, ms, mv, md, a, s);
-    case 256: return red_n<256>(axis, ms, mv, md, a, s);
-    default: return cudaErrorInvalidValue;
-    }
-}
-
 template <int N>
 cudaError_t xy_n(const CUtensorMap *maps, const XyPassArgs *a, cudaStream_t s)
 {
@@ -177,16 +101,6 @@ cudaError_t launch_pass_tma(int axis, int N, const CUtensorMap &msrc, const CUte
 {
     return pass_any(axis, N, &msrc, &mdst, &a, s);
 }
-
-cudaError_t launch_pass_tmared(int axis, int N, const CUtensorMap &msrc, const CUtensorMap &mV,
-                               const CUtensorMap &mdst, const TmaPassArgs &a, cudaStream_t s)
-{
-    return red_any(axis, N, &msrc, &mV, &mdst, &a, s);
-}
-
-int tmared_x_rows() { return kRedRowsX; }
-
-cudaError_t prepare_pass_tmared(int axis, int N) { return red_any(axis, N, nullptr, nullptr, nullptr, nullptr, nullptr); }
 
 cudaError_t prepare_pass_tma(int axis, int N) { return pass_any(axis, N, nullptr, nullptr, nullptr, nullptr); }
 }

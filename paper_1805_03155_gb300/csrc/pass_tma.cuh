@@ -17,9 +17,8 @@
 // Waits are bounded: on a timeout the block records kStatusTimeout, lets its
 // stores drain and returns.
 //
-// The reduce-add variants at the end of this file are the default kernels:
-// they never load the destination tile (a TMA reduce-add accumulates it at
-// L2), which frees shared memory for two blocks per SM with 3-stage rings.
+// These stored-tile kernels are schedule 5; the default kernels are the
+// reduce-add passes of pass_tmared.cuh.
 #pragma once
 
 #include "fft_line.cuh"
@@ -288,234 +287,6 @@ spass_tma_kernel(const __grid_constant__ CUtensorMap msrc, const __grid_constant
             if (k + kTmaStages - 1 < nk) {
                 bulk_wait_read<1>();
                 issue(k + kTmaStages - 1);
-            }
-        }
-    }
-    if (tid == 0) bulk_wait_all();
-}
-
-// ---------------------------------------------------------------------------
-// Reduce-add variants.  The destination field never enters the SM: the block
-// writes its contribution a L_d src (+ bV V src on the x pass) into the
-// consumed src tile and a TMA reduce-add (cp.reduce.async.bulk.tensor .add)
-// accumulates it into dst at L2.  A stage then holds only src (and V on the
-// x pass), so the same shared memory holds more stages: two blocks per SM,
-// each with its own 3-stage ring, keep more loads in flight and overlap one
-// block's barriers with the other's compute.  Each dst element receives exactly one add per
-// launch, so the result is deterministic; it equals the stored-tile kernels'
-// up to the rounding of the V term (a product, then the add).
-// ---------------------------------------------------------------------------
-constexpr size_t kTmaRedRing = 192 * 1024;  // shared memory for the ring
-
-// Ring stages: as many stages of PARTS tiles of TILE floats as fit
-// kTmaRedRing / B (B blocks per SM), at most 8.
-template <int TILE, int PARTS, int B>
-__host__ __device__ constexpr int tmared_stages()
-{
-    return (int)(kTmaRedRing / B / ((size_t)PARTS * TILE * sizeof(float)) < 8
-                     ? kTmaRedRing / B / ((size_t)PARTS * TILE * sizeof(float))
-                     : 8);
-}
-
-template <int N, int TILE, int PARTS, int B>
-__host__ __device__ constexpr size_t tmared_pass_smem()
-{
-    return (size_t)tmared_stages<TILE, PARTS, B>() * PARTS * TILE * sizeof(float) + N * sizeof(float2) +
-           N * sizeof(float) + tmared_stages<TILE, PARTS, B>() * sizeof(uint64_t) + 1024;
-}
-
-struct TmaRedSmem {
-    float *src, *vt;  // vt: x pass only
-    float2 *tw;
-    float *mult;
-    uint64_t *full;
-};
-
-template <int N, int TILE, int PARTS, int B>
-__device__ __forceinline__ TmaRedSmem tmared_carve(unsigned char *raw)
-{
-    constexpr int S = tmared_stages<TILE, PARTS, B>();
-    const uint32_t pad = (1024u - (smem_u32(raw) & 1023u)) & 1023u;
-    unsigned char *p = raw + pad;
-    TmaRedSmem m;
-    m.src = reinterpret_cast<float *>(p);
-    m.vt = m.src + S * TILE;
-    m.tw = reinterpret_cast<float2 *>(m.src + S * PARTS * TILE);
-    m.mult = reinterpret_cast<float *>(m.tw + N);
-    m.full = reinterpret_cast<uint64_t *>(m.mult + N);
-    return m;
-}
-
-template <int N, int S>
-__device__ __forceinline__ void tmared_setup(const TmaRedSmem &m, const TmaPassArgs &a, int tid, int nthreads)
-{
-    if (tid == 0) {
-        for (int s = 0; s < S; ++s) mbar_init(&m.full[s], 1);
-        mbar_fence_init();
-    }
-    for (int i = tid; i < N; i += nthreads) {
-        m.tw[i] = a.tw[i];
-        m.mult[i] = a.mult[i];
-    }
-    __syncthreads();
-}
-
-// x pass: tile = ROWS contiguous rows of N points (ROWS/2 complex line pairs,
-// block (N/E, ROWS/2)); stage = src + V tiles; B blocks per SM.
-template <int N, int E, int ROWS, int B>
-__global__ void __launch_bounds__((ROWS / 2) * (N / E), B)
-xpass_tmared_kernel(const __grid_constant__ CUtensorMap msrc, const __grid_constant__ CUtensorMap mV,
-                    const __grid_constant__ CUtensorMap mdst, const TmaPassArgs a)
-{
-    constexpr int TT = N / E;
-    constexpr int TILE = ROWS * N;
-    constexpr int S = tmared_stages<TILE, 2, B>();
-    constexpr uint32_t kTileBytes = TILE * sizeof(float);
-    extern __shared__ unsigned char smem_raw[];
-    const TmaRedSmem m = tmared_carve<N, TILE, 2, B>(smem_raw);
-    const int t = threadIdx.x, l = threadIdx.y, tid = l * TT + t;
-    tmared_setup<N, S>(m, a, tid, (ROWS / 2) * TT);
-    const bool useV = a.use_V != 0;
-
-    const int nk = (int)blockIdx.x < a.n_tiles ? (a.n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    auto tile_of = [&](int k) {
-        const int tile = (int)blockIdx.x + k * (int)gridDim.x;
-        return a.reverse ? a.n_tiles - 1 - tile : tile;
-    };
-    auto issue = [&](int k) {
-        const int s = k % S;
-        const int row0 = tile_of(k) * ROWS;
-        mbar_arrive_expect_tx(&m.full[s], (useV ? 2 : 1) * kTileBytes);
-        tma_load_3d(m.src + s * TILE, &msrc, 0, row0, 0, &m.full[s]);
-        if (useV) tma_load_3d(m.vt + s * TILE, &mV, 0, row0, 0, &m.full[s]);
-    };
-    if (tid == 0)
-        for (int k = 0; k < S - 1 && k < nk; ++k) issue(k);
-
-    for (int k = 0; k < nk; ++k) {
-        const int s = k % S;
-        if (!stage_wait(&m.full[s], (uint32_t)((k / S) & 1), tid)) {
-            if (tid == 0) {
-                atomicExch(a.status, kStatusTimeout);
-                bulk_wait_all();
-            }
-            return;
-        }
-        float *src = m.src + s * TILE;
-        float *vt = m.vt + s * TILE;
-        const int r0 = 2 * l, r1 = 2 * l + 1;
-        float2 v[E];
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const int i = t + e * TT;
-            v[e] = make_float2(src[r0 * N + i], src[r1 * N + i]);
-            // the V term of this element, parked in its own V slot
-            if (useV) {
-                vt[r0 * N + i] = a.bV * vt[r0 * N + i] * v[e].x;
-                vt[r1 * N + i] = a.bV * vt[r1 * N + i] * v[e].y;
-            }
-        }
-        // rows r0, r1 belong to this line's 16 threads (one warp) alone: the
-        // exchange below is line-private, so no block barrier is needed here
-        XcLine<N> xc{reinterpret_cast<float2 *>(src) + l * N};
-        fft_line<float, N, E, false>(v, t, xc, m.tw);
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const float mm = m.mult[t + e * TT];
-            v[e].x *= mm;
-            v[e].y *= mm;
-        }
-        fft_line<float, N, E, true>(v, t, xc, m.tw);
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const int i = t + e * TT;
-            src[r0 * N + i] = useV ? v[e].x + vt[r0 * N + i] : v[e].x;
-            src[r1 * N + i] = useV ? v[e].y + vt[r1 * N + i] : v[e].y;
-        }
-        fence_proxy_async();
-        __syncthreads();
-        if (tid == 0) {
-            tma_reduce_add_3d(&mdst, 0, tile_of(k) * ROWS, 0, src);
-            bulk_commit();
-            if (k + S - 1 < nk) {
-                bulk_wait_read<1>();
-                issue(k + S - 1);
-            }
-        }
-    }
-    if (tid == 0) bulk_wait_all();
-}
-
-// strided pass (y or z): tile = N points along the axis x 32 adjacent x
-// columns (16 column pairs); stage = src tile.
-template <int N, int E, int B = 1>
-__global__ void __launch_bounds__(16 * (N / E), B)
-spass_tmared_kernel(const __grid_constant__ CUtensorMap msrc, const __grid_constant__ CUtensorMap mdst,
-                    const TmaPassArgs a)
-{
-    constexpr int TT = N / E;
-    constexpr int S = tmared_stages<kTmaCols * N, 1, B>();
-    constexpr uint32_t kTileBytes = kTmaCols * N * sizeof(float);
-    extern __shared__ unsigned char smem_raw[];
-    const TmaRedSmem m = tmared_carve<N, kTmaCols * N, 1, B>(smem_raw);
-    const int p = threadIdx.x, t = threadIdx.y, tid = t * 16 + p;
-    tmared_setup<N, S>(m, a, tid, 16 * TT);
-
-    const int nk = (int)blockIdx.x < a.n_tiles ? (a.n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    auto coords = [&](int k, int &x, int &y, int &z) {
-        int tile = (int)blockIdx.x + k * (int)gridDim.x;
-        if (a.reverse) tile = a.n_tiles - 1 - tile;
-        const int outer = tile / a.n_xt;
-        x = (tile - outer * a.n_xt) * kTmaCols;
-        y = a.axis == 1 ? 0 : outer;
-        z = a.axis == 1 ? outer : 0;
-    };
-    auto issue = [&](int k) {
-        const int s = k % S;
-        int x, y, z;
-        coords(k, x, y, z);
-        mbar_arrive_expect_tx(&m.full[s], kTileBytes);
-        tma_load_3d(m.src + s * kTmaCols * N, &msrc, x, y, z, &m.full[s]);
-    };
-    if (tid == 0)
-        for (int k = 0; k < S - 1 && k < nk; ++k) issue(k);
-
-    for (int k = 0; k < nk; ++k) {
-        const int s = k % S;
-        if (!stage_wait(&m.full[s], (uint32_t)((k / S) & 1), tid)) {
-            if (tid == 0) {
-                atomicExch(a.status, kStatusTimeout);
-                bulk_wait_all();
-            }
-            return;
-        }
-        float2 *src = reinterpret_cast<float2 *>(m.src + s * kTmaCols * N);
-        float2 v[E];
-#pragma unroll
-        for (int e = 0; e < E; ++e) v[e] = src[(t + e * TT) * 16 + p];
-        __syncthreads();
-        XcColB xc{src + p};
-        fft_line<float, N, E, false>(v, t, xc, m.tw);
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const float mm = m.mult[t + e * TT];
-            v[e].x *= mm;
-            v[e].y *= mm;
-        }
-        fft_line<float, N, E, true>(v, t, xc, m.tw);
-        // the inverse's last exchange ended with a block barrier: the tile is free
-#pragma unroll
-        for (int e = 0; e < E; ++e) src[(t + e * TT) * 16 + p] = v[e];
-        fence_proxy_async();
-        __syncthreads();
-        if (tid == 0) {
-            int x, y, z;
-            coords(k, x, y, z);
-            tma_reduce_add_3d(&mdst, x, y, z, src);
-            bulk_commit();
-            if (k + S - 1 < nk) {
-                bulk_wait_read<1>();
-                issue(k + S - 1);
             }
         }
     }

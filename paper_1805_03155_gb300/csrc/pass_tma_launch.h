@@ -4,6 +4,8 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include "kernels.cuh"
+
 namespace spstd {
 
 struct TmaPassArgs {
@@ -18,27 +20,87 @@ struct TmaPassArgs {
     int axis;            // strided pass: 1 (y) or 2 (z)
     int reverse;
     int *status;         // device status word (kStatusTimeout on a timed-out wait)
+    int nx;              // reduce-add passes: points along x
 };
 
 // Tile geometry the tensor maps must use.
 constexpr unsigned tma_rows_per_tile() { return 32; }  // x pass: contiguous rows per tile
 constexpr unsigned tma_cols_per_tile() { return 32; }  // strided pass: x columns per tile
 
-// axis 0: x pass, 1: y pass, 2: z pass; N in {64, 128, 256}.  Raises the
-// kernel's shared-memory limit and sizes the persistent grid on first use.
+// Stored-tile passes (pass_tma.cuh, schedule 5).  axis 0: x pass, 1: y pass,
+// 2: z pass; N in {64, 128, 256}.  Raises the kernel's shared-memory limit and
+// sizes the persistent grid on first use.
 cudaError_t launch_pass_tma(int axis, int N, const CUtensorMap &msrc, const CUtensorMap &mdst,
                             const TmaPassArgs &a, cudaStream_t s);
 // The same set-up without a launch (call before a stream capture).
 cudaError_t prepare_pass_tma(int axis, int N);
 
-// Reduce-add variants (the dst tile is accumulated by a TMA reduce at L2
-// instead of being loaded and stored): mV is the potential in the x view
-// (x pass only; unused otherwise).
+// ---------------------------------------------------------------------------
+// Reduce-add passes (pass_tmared.cuh), the default for FP32 lines of 64..512
+// points: the destination is accumulated at L2 by a TMA reduce-add.
+// ---------------------------------------------------------------------------
+constexpr bool tmared_eligible(int64_t N) { return N == 64 || N == 128 || N == 256 || N == 512; }
+// x pass: rows per tile (the box height of its x-view maps).
+constexpr int tmared_rows_x(int N) { return 4096 / N; }
+// Strided pass over N points along y or z with nx points along x: column
+// pairs per tile (its y/z-view maps' box is 2P columns wide); 0 if nx < 16.
+constexpr int tmared_pairs(int N, int64_t nx)
+{
+    int P = 4096 / N;
+    while (P > 8 && 2 * (int64_t)P > nx) P /= 2;
+    return nx >= 16 ? P : 0;
+}
+// Tiles of one grid (or one batch member) shaped n[3] in the pass of axis ax;
+// *n_xt: tiles across x (strided passes).
+inline int tmared_tiles(int axis, const int64_t *n, int *n_xt)
+{
+    if (axis == 0) {
+        if (n_xt) *n_xt = 1;
+        const int R = tmared_rows_x((int)n[0]);
+        return (int)((n[1] * n[2] + R - 1) / R);
+    }
+    const int cols = 2 * tmared_pairs((int)n[axis], n[0]);
+    const int nxt = cols ? (int)((n[0] + cols - 1) / cols) : 0;
+    if (n_xt) *n_xt = nxt;
+    return nxt * (int)(axis == 1 ? n[2] : n[1]);
+}
+
+// Single grid: a.n_tiles / a.n_xt from tmared_tiles, a.nx = points along x;
+// mV is the potential in the x view (x pass only).
 cudaError_t launch_pass_tmared(int axis, int N, const CUtensorMap &msrc, const CUtensorMap &mV,
                                const CUtensorMap &mdst, const TmaPassArgs &a, cudaStream_t s);
-cudaError_t prepare_pass_tmared(int axis, int N);
-// Rows per tile of the reduce-add x pass (its x-view maps use this box height).
-int tmared_x_rows();
+// Raises the kernel's shared-memory limit and sizes its persistent grid (call
+// before a stream capture); nx: points along x.
+cudaError_t prepare_pass_tmared(int axis, int N, int64_t nx);
+
+// One member of a batched pass: tensor maps over its own fields (0 psi_R,
+// 1 psi_I, 2 scratch; index 3 of the x view is V) with the reduce-add boxes,
+// and its device status word.  Lives in device memory (64-byte aligned).
+struct TmaMember {
+    CUtensorMap x[4];  // x view, box N x tmared_rows_x(N)
+    CUtensorMap y[3];  // y view, box 2P columns x N
+    CUtensorMap z[3];  // z view, box 2P columns x 1 x N
+    int *status;
+};
+
+// A batched reduce-add pass over `members` members of one shape: member i
+// reads field src (1 - dst when src < 0) through mem[i] and accumulates into
+// field dst, with the multipliers pa[i].mult (N floats, 16-byte aligned) and,
+// on the x pass, pa[i].bV.  tiles / n_xt from tmared_tiles.
+struct TmaBatchArgs {
+    const TmaMember *mem;
+    const PassArgs<float> *pa;
+    const float2 *tw;  // W_N, the same for every member
+    int src, dst;
+    int members;
+    int tiles;
+    int n_xt;
+    int nx;            // points along x
+    int axis;
+};
+
+cudaError_t launch_pass_tmared_batch(int axis, int N, const TmaBatchArgs &a, cudaStream_t s);
+cudaError_t prepare_pass_tmared_batch(int axis, int N, int64_t nx);
 
 struct XyPassArgs;
 // x and y passes of a 3D half-stage in one persistent launch (pass_xy.cuh);

@@ -1,0 +1,116 @@
+// Instantiations and launchers of the reduce-add pipelined passes
+// (pass_tmared.cuh): single grids and batches, lines of 64..512 points.
+#include "pass_tmared.cuh"
+#include "persist.cuh"
+
+namespace spstd {
+namespace {
+
+constexpr int kRedE = 16;  // complex points per thread
+
+template <int N, bool BATCH>
+cudaError_t red_x(const CUtensorMap *ms, const CUtensorMap *mv, const CUtensorMap *md, const TmaPassArgs *a,
+                  const TmaBatchArgs *ba, cudaStream_t s)
+{
+    using G = XRed<N, kRedE, BATCH>;
+    int grid = 0;
+    cudaError_t e = persistent_grid<xpass_tmared_kernel<N, kRedE, BATCH>>(G::THREADS, G::SMEM, &grid);
+    if (e != cudaSuccess || !(BATCH ? (const void *)ba : (const void *)a)) return e;
+    const int total = BATCH ? ba->members * ba->tiles : a->n_tiles;
+    if (total < grid) grid = total;
+    if (grid <= 0) return cudaSuccess;
+    const CUtensorMap none{};
+    const TmaPassArgs a0{};
+    const TmaBatchArgs b0{};
+    xpass_tmared_kernel<N, kRedE, BATCH><<<grid, dim3(G::TT, G::LP), G::SMEM, s>>>(
+        BATCH ? none : *ms, BATCH ? none : *mv, BATCH ? none : *md, BATCH ? a0 : *a, BATCH ? *ba : b0);
+    return cudaGetLastError();
+}
+
+template <int N, int P, bool BATCH>
+cudaError_t red_s(const CUtensorMap *ms, const CUtensorMap *md, const TmaPassArgs *a, const TmaBatchArgs *ba,
+                  cudaStream_t s)
+{
+    using G = SRed<N, kRedE, P, BATCH>;
+    int grid = 0;
+    cudaError_t e = persistent_grid<spass_tmared_kernel<N, kRedE, P, BATCH>>(G::THREADS, G::SMEM, &grid);
+    if (e != cudaSuccess || !(BATCH ? (const void *)ba : (const void *)a)) return e;
+    const int total = BATCH ? ba->members * ba->tiles : a->n_tiles;
+    if (total < grid) grid = total;
+    if (grid <= 0) return cudaSuccess;
+    const CUtensorMap none{};
+    const TmaPassArgs a0{};
+    const TmaBatchArgs b0{};
+    spass_tmared_kernel<N, kRedE, P, BATCH><<<grid, dim3(P, G::TT), G::SMEM, s>>>(
+        BATCH ? none : *ms, BATCH ? none : *md, BATCH ? a0 : *a, BATCH ? *ba : b0);
+    return cudaGetLastError();
+}
+
+// Strided pass of N points with P column pairs (P from tmared_pairs).
+template <int N, bool BATCH>
+cudaError_t red_s_p(int P, const CUtensorMap *ms, const CUtensorMap *md, const TmaPassArgs *a,
+                    const TmaBatchArgs *ba, cudaStream_t s)
+{
+    switch (P) {
+    case 8: return red_s<N, 8, BATCH>(ms, md, a, ba, s);
+    case 16:
+        if constexpr (4096 / N >= 16) return red_s<N, 16, BATCH>(ms, md, a, ba, s);
+        break;
+    case 32:
+        if constexpr (4096 / N >= 32) return red_s<N, 32, BATCH>(ms, md, a, ba, s);
+        break;
+    case 64:
+        if constexpr (4096 / N >= 64) return red_s<N, 64, BATCH>(ms, md, a, ba, s);
+        break;
+    default: break;
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <bool BATCH>
+cudaError_t red_any(int axis, int N, int64_t nx, const CUtensorMap *ms, const CUtensorMap *mv,
+                    const CUtensorMap *md, const TmaPassArgs *a, const TmaBatchArgs *ba, cudaStream_t s)
+{
+    if (!tmared_eligible(N)) return cudaErrorInvalidValue;
+    if (axis == 0) {
+        if (nx != N) return cudaErrorInvalidValue;
+        switch (N) {
+        case 64: return red_x<64, BATCH>(ms, mv, md, a, ba, s);
+        case 128: return red_x<128, BATCH>(ms, mv, md, a, ba, s);
+        case 256: return red_x<256, BATCH>(ms, mv, md, a, ba, s);
+        default: return red_x<512, BATCH>(ms, mv, md, a, ba, s);
+        }
+    }
+    const int P = tmared_pairs(N, nx);
+    switch (N) {
+    case 64: return red_s_p<64, BATCH>(P, ms, md, a, ba, s);
+    case 128: return red_s_p<128, BATCH>(P, ms, md, a, ba, s);
+    case 256: return red_s_p<256, BATCH>(P, ms, md, a, ba, s);
+    default: return red_s_p<512, BATCH>(P, ms, md, a, ba, s);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_pass_tmared(int axis, int N, const CUtensorMap &msrc, const CUtensorMap &mV,
+                               const CUtensorMap &mdst, const TmaPassArgs &a, cudaStream_t s)
+{
+    return red_any<false>(axis, N, a.nx, &msrc, &mV, &mdst, &a, nullptr, s);
+}
+
+cudaError_t prepare_pass_tmared(int axis, int N, int64_t nx)
+{
+    return red_any<false>(axis, N, nx, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+}
+
+cudaError_t launch_pass_tmared_batch(int axis, int N, const TmaBatchArgs &a, cudaStream_t s)
+{
+    return red_any<true>(axis, N, a.nx, nullptr, nullptr, nullptr, nullptr, &a, s);
+}
+
+cudaError_t prepare_pass_tmared_batch(int axis, int N, int64_t nx)
+{
+    return red_any<true>(axis, N, nx, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+}
+
+}  // namespace spstd

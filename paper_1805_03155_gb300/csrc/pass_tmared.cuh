@@ -1,0 +1,398 @@
+// pass_tmared.cuh -- the default pipelined FP32 half-stage passes (lines of
+// 64..512 points): TMA loads into shared-memory rings, a TMA reduce-add
+// epilogue.
+//
+// The destination field never enters the SM.  A block computes its tile's
+// contribution a L_d src (+ bV V src on the x pass, Eq. 16/18) into the
+// consumed src tile, and a TMA reduce-add (cp.reduce.async.bulk.tensor .add)
+// accumulates it into dst at L2.  Each dst element receives exactly one add
+// per launch, so results are deterministic.  Without a dst tile a stage holds
+// only src (and V on the x pass): two persistent blocks per SM, each with its
+// own ring of up to 8 stages, keep loads in flight and overlap one block's
+// barriers with the other's compute.
+//
+// Tile geometry (sizes are fixed per line length N so that every block has
+// 128 (x) or 256 (strided) threads and a 16 KB / 32 KB tile part):
+//   x pass:        ROWS = 4096/N contiguous rows of N points, ROWS/2 line
+//                  pairs, block (N/E, ROWS/2), stage = src + V tiles;
+//   strided pass:  N points along y or z x 2P adjacent x columns (P column
+//                  pairs, P = min(4096/N, n_x/2)), block (P, N/E).
+// Waits are bounded: on a timeout the block records kStatusTimeout, lets its
+// bulk operations drain and returns.
+//
+// Batched forms run the tiles of many same-shaped members in one launch; each
+// stage then also carries its member's multiplier row (bulk-copied on the
+// stage barrier), because dt and the stage coefficient differ per member.
+#pragma once
+
+#include "fft_line.cuh"
+#include "pass_tma_launch.h"
+#include "tma.cuh"
+
+namespace spstd {
+
+constexpr size_t kTmaRedRing = 192 * 1024;  // shared memory for the rings of the blocks of one SM
+constexpr int kRedBlocks = 2;               // persistent blocks per SM
+
+// Ring stages: as many stages of PARTS tiles of TILE floats as fit
+// kTmaRedRing / B (B blocks per SM), at most 8.
+template <int TILE, int PARTS, int B>
+__host__ __device__ constexpr int tmared_stages()
+{
+    return (int)(kTmaRedRing / B / ((size_t)PARTS * TILE * sizeof(float)) < 8
+                     ? kTmaRedRing / B / ((size_t)PARTS * TILE * sizeof(float))
+                     : 8);
+}
+
+// Shared memory of a block: S stages of PARTS tiles (plus, batched, a
+// multiplier row per stage), then the twiddles (and, single-grid, the
+// multipliers) and the barriers, with room for 1024-byte alignment.
+template <int N, int TILE, int PARTS, int S, bool BATCH>
+__host__ __device__ constexpr size_t tmared_smem()
+{
+    return (size_t)S * (PARTS * TILE + (BATCH ? N : 0)) * sizeof(float) + N * sizeof(float2) +
+           (BATCH ? 0 : N * sizeof(float)) + S * sizeof(uint64_t) + 1024;
+}
+
+struct TmaRedSmem {
+    float *src, *vt;  // [S] src tiles, [S] V tiles (x pass)
+    float *mult;      // single-grid: one row; batched: [S] rows
+    float2 *tw;
+    uint64_t *full;
+};
+
+template <int N, int TILE, int PARTS, int S, bool BATCH>
+__device__ __forceinline__ TmaRedSmem tmared_carve(unsigned char *raw)
+{
+    const uint32_t pad = (1024u - (smem_u32(raw) & 1023u)) & 1023u;
+    TmaRedSmem m;
+    m.src = reinterpret_cast<float *>(raw + pad);
+    m.vt = m.src + S * TILE;
+    m.mult = m.src + S * PARTS * TILE;
+    m.tw = reinterpret_cast<float2 *>(m.mult + (BATCH ? S * N : N));
+    m.full = reinterpret_cast<uint64_t *>(m.tw + N);
+    return m;
+}
+
+template <int N, int S>
+__device__ __forceinline__ void tmared_setup(const TmaRedSmem &m, const float2 *tw, const float *mult, int tid,
+                                             int nthreads)
+{
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) mbar_init(&m.full[s], 1);
+        mbar_fence_init();
+    }
+    for (int i = tid; i < N; i += nthreads) {
+        m.tw[i] = tw[i];
+        if (mult) m.mult[i] = mult[i];
+    }
+    __syncthreads();
+}
+
+// Column exchange inside a strided tile ([N rows][P pairs], pair p at column
+// p): a warp spans consecutive pairs of one or more rows, so its accesses are
+// contiguous row segments.  Block barriers order it; each read phase is closed
+// by a second barrier (flip) before the next write phase.
+template <int P>
+struct XcColP {
+    float2 *base;  // tile + p
+    __device__ __forceinline__ float2 &at(int idx) { return base[idx * P]; }
+    __device__ __forceinline__ void st(int idx, float2 v) { at(idx) = v; }
+    __device__ __forceinline__ float2 ld(int idx) { return at(idx); }
+    __device__ __forceinline__ void sync() { __syncthreads(); }
+    __device__ __forceinline__ void flip() { __syncthreads(); }
+};
+
+// Line-private exchange region of an x tile: line pair l owns N consecutive
+// complex slots (its own two rows), index XOR-swizzled within groups of 16.
+// The threads of a line sit in one warp, so warp barriers order it.
+template <int N>
+struct XcLineR {
+    float2 *base;  // tile + l * N complex slots
+    __device__ __forceinline__ float2 &at(int idx) { return base[idx ^ ((idx >> 4) & 15)]; }
+    __device__ __forceinline__ void st(int idx, float2 v) { at(idx) = v; }
+    __device__ __forceinline__ float2 ld(int idx) { return at(idx); }
+    __device__ __forceinline__ void sync() { __syncwarp(); }
+    __device__ __forceinline__ void flip() { __syncwarp(); }
+};
+
+// Bounded wait on a stage barrier by every thread, then a block vote: false if
+// any thread timed out.
+__device__ __forceinline__ bool red_stage_wait(uint64_t *bar, uint32_t parity)
+{
+    const bool ok = mbar_wait(bar, parity);
+    return !__syncthreads_or(!ok);
+}
+
+// One x tile: line pair l (rows 2l, 2l+1 of the tile), thread t.  Reads src
+// (and V), computes a L_x src (+ bV V src) with the multipliers `mult` and
+// leaves it in the src tile.  No block barrier inside: the rows of a line pair
+// belong to its N/E threads (within one warp) alone.
+template <int N, int E>
+__device__ __forceinline__ void xred_tile(float *src, float *vt, const float *mult, const float2 *tw, float bV,
+                                          bool useV, int t, int l)
+{
+    constexpr int TT = N / E;
+    const int r0 = 2 * l, r1 = 2 * l + 1;
+    float2 v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int i = t + e * TT;
+        v[e] = make_float2(src[r0 * N + i], src[r1 * N + i]);
+        // the V term of this element, parked in its own V slot
+        if (useV) {
+            vt[r0 * N + i] = bV * vt[r0 * N + i] * v[e].x;
+            vt[r1 * N + i] = bV * vt[r1 * N + i] * v[e].y;
+        }
+    }
+    XcLineR<N> xc{reinterpret_cast<float2 *>(src) + l * N};
+    fft_line<float, N, E, false>(v, t, xc, tw);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const float mm = mult[t + e * TT];
+        v[e].x *= mm;
+        v[e].y *= mm;
+    }
+    fft_line<float, N, E, true>(v, t, xc, tw);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int i = t + e * TT;
+        src[r0 * N + i] = useV ? v[e].x + vt[r0 * N + i] : v[e].x;
+        src[r1 * N + i] = useV ? v[e].y + vt[r1 * N + i] : v[e].y;
+    }
+}
+
+// One strided tile ([N rows][P column pairs] of float2): column pair p,
+// thread t.  Computes a L_d src and leaves it in the tile.  Contains block
+// barriers (the column exchange spans the block).
+template <int N, int E, int P>
+__device__ __forceinline__ void sred_tile(float2 *src, const float *mult, const float2 *tw, int t, int p)
+{
+    constexpr int TT = N / E;
+    float2 v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = src[(t + e * TT) * P + p];
+    __syncthreads();
+    XcColP<P> xc{src + p};
+    fft_line<float, N, E, false>(v, t, xc, tw);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const float mm = mult[t + e * TT];
+        v[e].x *= mm;
+        v[e].y *= mm;
+    }
+    fft_line<float, N, E, true>(v, t, xc, tw);
+    // the inverse's last exchange ended with a block barrier: the tile is free
+#pragma unroll
+    for (int e = 0; e < E; ++e) src[(t + e * TT) * P + p] = v[e];
+}
+
+// Where tile g of a launch is: member i (0 for a single grid) and the 4D
+// coordinates of its box.  The maps split the line axis into (L1, L2) =
+// (min(N, 256), N / L1) so that no box dimension exceeds 256:
+//   x view  (x_lo, x_hi, row, 1)      box (L1, L2, ROWS, 1)
+//   y view  (x, y_lo, y_hi, z)        box (2P, L1, L2, 1)
+//   z view  (x, y, z_lo, z_hi)        box (2P, 1, L1, L2)
+// and each box lands in shared memory row-major along the line.
+struct TileAt {
+    int i, c[4];
+};
+
+__device__ __forceinline__ TileAt tile_at_x(int g, int tiles, int rows, int reverse, int total)
+{
+    if (reverse) g = total - 1 - g;
+    TileAt a;
+    a.i = g / tiles;
+    a.c[0] = 0;
+    a.c[1] = 0;
+    a.c[2] = (g - a.i * tiles) * rows;
+    a.c[3] = 0;
+    return a;
+}
+
+__device__ __forceinline__ TileAt tile_at_s(int g, int tiles, int n_xt, int cols, int axis, int reverse, int total)
+{
+    if (reverse) g = total - 1 - g;
+    TileAt a;
+    a.i = g / tiles;
+    const int lt = g - a.i * tiles;
+    const int outer = lt / n_xt;
+    a.c[0] = (lt - outer * n_xt) * cols;
+    a.c[1] = axis == 1 ? 0 : outer;
+    a.c[2] = 0;
+    a.c[3] = axis == 1 ? outer : 0;
+    return a;
+}
+
+__device__ __forceinline__ void load_tile(void *smem, const CUtensorMap *map, const TileAt &c, uint64_t *bar)
+{
+    tma_load_4d(smem, map, c.c[0], c.c[1], c.c[2], c.c[3], bar);
+}
+
+__device__ __forceinline__ void reduce_tile(const CUtensorMap *map, const TileAt &c, const void *smem)
+{
+    tma_reduce_add_4d(map, c.c[0], c.c[1], c.c[2], c.c[3], smem);
+}
+
+// ---------------------------------------------------------------------------
+// x pass.  Single grid (BATCH = false): maps msrc / mV / mdst, a.mult, a.bV.
+// Batched: member i's maps in ba.mem[i], its multipliers and bV in ba.pa[i].
+// ---------------------------------------------------------------------------
+template <int N, int E, bool BATCH>
+struct XRed {
+    static constexpr int TT = N / E;
+    static constexpr int ROWS = tmared_rows_x(N);
+    static constexpr int LP = ROWS / 2;
+    static constexpr int THREADS = LP * TT;
+    static constexpr int TILE = ROWS * N;
+    static constexpr int S = tmared_stages<TILE, 2, kRedBlocks>();
+    static constexpr size_t SMEM = tmared_smem<N, TILE, 2, S, BATCH>();
+};
+
+template <int N, int E, bool BATCH>
+__global__ void __launch_bounds__(XRed<N, E, BATCH>::THREADS, kRedBlocks)
+xpass_tmared_kernel(const __grid_constant__ CUtensorMap msrc, const __grid_constant__ CUtensorMap mV,
+                    const __grid_constant__ CUtensorMap mdst, const TmaPassArgs a, const TmaBatchArgs ba)
+{
+    using G = XRed<N, E, BATCH>;
+    constexpr int TT = G::TT, ROWS = G::ROWS, TILE = G::TILE, S = G::S;
+    constexpr uint32_t kTileBytes = TILE * sizeof(float);
+    extern __shared__ unsigned char smem_raw[];
+    const TmaRedSmem m = tmared_carve<N, TILE, 2, S, BATCH>(smem_raw);
+    const int t = threadIdx.x, l = threadIdx.y, tid = l * TT + t;
+    tmared_setup<N, S>(m, BATCH ? ba.tw : a.tw, BATCH ? nullptr : a.mult, tid, G::THREADS);
+    const bool useV = BATCH || a.use_V != 0;
+    const int fsrc = BATCH ? (ba.src >= 0 ? ba.src : 1 - ba.dst) : 0;
+
+    const int tiles = BATCH ? ba.tiles : a.n_tiles;
+    const int total = BATCH ? ba.members * ba.tiles : a.n_tiles;
+    const int reverse = BATCH ? 0 : a.reverse;
+    const int nk = (int)blockIdx.x < total ? (total - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    auto at = [&](int k) { return tile_at_x((int)blockIdx.x + k * (int)gridDim.x, tiles, ROWS, reverse, total); };
+    auto issue = [&](int k) {
+        const int s = k % S;
+        const TileAt c = at(k);
+        if constexpr (BATCH) {
+            const TmaMember *mm = ba.mem + c.i;
+            mbar_arrive_expect_tx(&m.full[s], 2 * kTileBytes + N * sizeof(float));
+            load_tile(m.src + s * TILE, &mm->x[fsrc], c, &m.full[s]);
+            load_tile(m.vt + s * TILE, &mm->x[3], c, &m.full[s]);
+            bulk_load(m.mult + s * N, ba.pa[c.i].mult, N * sizeof(float), &m.full[s]);
+        } else {
+            mbar_arrive_expect_tx(&m.full[s], (useV ? 2 : 1) * kTileBytes);
+            load_tile(m.src + s * TILE, &msrc, c, &m.full[s]);
+            if (useV) load_tile(m.vt + s * TILE, &mV, c, &m.full[s]);
+        }
+    };
+    if (tid == 0)
+        for (int k = 0; k < S - 1 && k < nk; ++k) issue(k);
+
+    for (int k = 0; k < nk; ++k) {
+        const int s = k % S;
+        const TileAt c = at(k);
+        if (!red_stage_wait(&m.full[s], (uint32_t)((k / S) & 1))) {
+            if (tid == 0) {
+                atomicExch(BATCH ? ba.mem[c.i].status : a.status, kStatusTimeout);
+                bulk_wait_all();
+            }
+            return;
+        }
+        float *src = m.src + s * TILE;
+        if constexpr (BATCH)
+            xred_tile<N, E>(src, m.vt + s * TILE, m.mult + s * N, m.tw, ba.pa[c.i].bV, true, t, l);
+        else
+            xred_tile<N, E>(src, m.vt + s * TILE, m.mult, m.tw, a.bV, useV, t, l);
+        fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+            reduce_tile(BATCH ? &ba.mem[c.i].x[ba.dst] : &mdst, c, src);
+            bulk_commit();
+            if (k + S - 1 < nk) {
+                bulk_wait_read<1>();
+                issue(k + S - 1);
+            }
+        }
+    }
+    if (tid == 0) bulk_wait_all();
+}
+
+// ---------------------------------------------------------------------------
+// strided pass (y or z), P column pairs per tile.
+// ---------------------------------------------------------------------------
+template <int N, int E, int P, bool BATCH>
+struct SRed {
+    static constexpr int TT = N / E;
+    static constexpr int THREADS = P * TT;
+    static constexpr int TILE = 2 * P * N;
+    static constexpr int S = tmared_stages<TILE, 1, kRedBlocks>();
+    static constexpr size_t SMEM = tmared_smem<N, TILE, 1, S, BATCH>();
+};
+
+template <int N, int E, int P, bool BATCH>
+__global__ void __launch_bounds__(SRed<N, E, P, BATCH>::THREADS, kRedBlocks)
+spass_tmared_kernel(const __grid_constant__ CUtensorMap msrc, const __grid_constant__ CUtensorMap mdst,
+                    const TmaPassArgs a, const TmaBatchArgs ba)
+{
+    using G = SRed<N, E, P, BATCH>;
+    constexpr int TILE = G::TILE, S = G::S;
+    constexpr uint32_t kTileBytes = TILE * sizeof(float);
+    extern __shared__ unsigned char smem_raw[];
+    const TmaRedSmem m = tmared_carve<N, TILE, 1, S, BATCH>(smem_raw);
+    const int p = threadIdx.x, t = threadIdx.y, tid = t * P + p;
+    tmared_setup<N, S>(m, BATCH ? ba.tw : a.tw, BATCH ? nullptr : a.mult, tid, G::THREADS);
+    const int axis = BATCH ? ba.axis : a.axis;
+    const int fsrc = BATCH ? (ba.src >= 0 ? ba.src : 1 - ba.dst) : 0;
+
+    const int tiles = BATCH ? ba.tiles : a.n_tiles;
+    const int n_xt = BATCH ? ba.n_xt : a.n_xt;
+    const int total = BATCH ? ba.members * ba.tiles : a.n_tiles;
+    const int reverse = BATCH ? 0 : a.reverse;
+    const int nk = (int)blockIdx.x < total ? (total - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    auto at = [&](int k) {
+        return tile_at_s((int)blockIdx.x + k * (int)gridDim.x, tiles, n_xt, 2 * P, axis, reverse, total);
+    };
+    auto view = [&](int i, int f) -> const CUtensorMap * {
+        return axis == 1 ? &ba.mem[i].y[f] : &ba.mem[i].z[f];
+    };
+    auto issue = [&](int k) {
+        const int s = k % S;
+        const TileAt c = at(k);
+        if constexpr (BATCH) {
+            mbar_arrive_expect_tx(&m.full[s], kTileBytes + N * sizeof(float));
+            load_tile(m.src + s * TILE, view(c.i, fsrc), c, &m.full[s]);
+            bulk_load(m.mult + s * N, ba.pa[c.i].mult, N * sizeof(float), &m.full[s]);
+        } else {
+            mbar_arrive_expect_tx(&m.full[s], kTileBytes);
+            load_tile(m.src + s * TILE, &msrc, c, &m.full[s]);
+        }
+    };
+    if (tid == 0)
+        for (int k = 0; k < S - 1 && k < nk; ++k) issue(k);
+
+    for (int k = 0; k < nk; ++k) {
+        const int s = k % S;
+        const TileAt c = at(k);
+        if (!red_stage_wait(&m.full[s], (uint32_t)((k / S) & 1))) {
+            if (tid == 0) {
+                atomicExch(BATCH ? ba.mem[c.i].status : a.status, kStatusTimeout);
+                bulk_wait_all();
+            }
+            return;
+        }
+        float2 *src = reinterpret_cast<float2 *>(m.src + s * TILE);
+        sred_tile<N, E, P>(src, BATCH ? m.mult + s * N : m.mult, m.tw, t, p);
+        fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+            reduce_tile(BATCH ? view(c.i, ba.dst) : &mdst, c, src);
+            bulk_commit();
+            if (k + S - 1 < nk) {
+                bulk_wait_read<1>();
+                issue(k + S - 1);
+            }
+        }
+    }
+    if (tid == 0) bulk_wait_all();
+}
+
+}  // namespace spstd

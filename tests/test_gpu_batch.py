@@ -92,3 +92,48 @@ def test_batch_membership_changes():
     batch.close()
     for s in solvers:
         s.close()
+
+
+def test_tma_batch_members_equal_lone_solves_bitwise():
+    """FP32 members whose axes all have 64..256 points run the batched
+    pipelined passes (every member's tiles in one launch, its own tensor maps
+    and dt-scaled multipliers); they reach bit for bit the state and probes
+    of the same solve stepped alone on the single-grid pipelined passes,
+    which do the same per-tile arithmetic."""
+    from paper_1805_03155_gb300 import spstd
+
+    shapes = [((64, 64), "FR4"), ((64, 64), "FR4"), ((128, 64), "SUZUKI6"), ((64, 64, 64), "FR4"),
+              ((64, 64, 64), "FR4"), ((64, 128, 64), "FR4"), ((256, 64), "FR4"), ((512, 512), "FR4"),
+              ((512, 512), "FR4"), ((32, 64, 128), "FR4")]
+    probs = []
+    for k, (shape, integ) in enumerate(shapes):
+        dims = len(shape)
+        lo = [-5.0 - 0.4 * k] * dims
+        hi = [5.0 + 0.3 * k] * dims
+        probs.append(inputs.gaussian_problem(shape, lo, hi, seed=300 + k, integrator=integ, dt=0.0, steps=0,
+                                             n_probe=2))
+    steps = 23  # two graph chunks of 10 + 3 direct steps
+    alone = []
+    for p in probs:
+        s = gpu_solver(p, 32, cap=steps, merge=False)
+        s.spstd_step(steps)
+        R, Im = s.spstd_get_state()
+        alone.append((R, Im, np.array([s.spstd_probe(q) for q in range(2)])))
+        s.close()
+    batch = spstd.Batch(len(probs))
+    solvers = [gpu_solver(p, 32, cap=steps) for p in probs]
+    for s in solvers:
+        batch.spstd_batch_add(s)
+    batch.spstd_batch_step(steps)
+    batch.spstd_batch_sync()
+    for i, (s, (R, Im, pr)) in enumerate(zip(solvers, alone)):
+        bR, bI = s.spstd_get_state()
+        bp = np.array([s.spstd_probe(q) for q in range(2)])
+        assert np.array_equal(bR, R) and np.array_equal(bI, Im), i
+        assert np.array_equal(bp, pr), i
+    for (shape, _) in shapes:
+        assert batch.spstd_batch_get_schedule(32, len(shape), shape) == [0, 0, 0]
+    assert batch.spstd_batch_launch_count(steps) > 0
+    batch.close()
+    for s in solvers:
+        s.close()
