@@ -6,15 +6,17 @@
 namespace spstd {
 namespace {
 
-constexpr int kRedE = 16;  // complex points per thread
+// Complex points per thread.  Measured at 256^3: E = 8 (256-thread x blocks,
+// 16 warps per SM) takes 0.054 ms per x pass against 0.047 ms for E = 16.
+constexpr int kRedE = 16;
 
-template <int N, bool BATCH>
+template <int N, bool BATCH, int EX = kRedE>
 cudaError_t red_x(const CUtensorMap *ms, const CUtensorMap *mv, const CUtensorMap *md, const TmaPassArgs *a,
                   const TmaBatchArgs *ba, cudaStream_t s)
 {
-    using G = XRed<N, kRedE, BATCH>;
+    using G = XRed<N, EX, BATCH>;
     int grid = 0;
-    cudaError_t e = persistent_grid<xpass_tmared_kernel<N, kRedE, BATCH>>(G::THREADS, G::SMEM, &grid);
+    cudaError_t e = persistent_grid<xpass_tmared_kernel<N, EX, BATCH>>(G::THREADS, G::SMEM, &grid);
     if (e != cudaSuccess || !(BATCH ? (const void *)ba : (const void *)a)) return e;
     const int total = BATCH ? ba->members * ba->tiles : a->n_tiles;
     if (total < grid) grid = total;
@@ -22,7 +24,7 @@ cudaError_t red_x(const CUtensorMap *ms, const CUtensorMap *mv, const CUtensorMa
     const CUtensorMap none{};
     const TmaPassArgs a0{};
     const TmaBatchArgs b0{};
-    xpass_tmared_kernel<N, kRedE, BATCH><<<grid, dim3(G::TT, G::LP), G::SMEM, s>>>(
+    xpass_tmared_kernel<N, EX, BATCH><<<grid, dim3(G::TT, G::LP), G::SMEM, s>>>(
         BATCH ? none : *ms, BATCH ? none : *mv, BATCH ? none : *md, BATCH ? a0 : *a, BATCH ? *ba : b0);
     return cudaGetLastError();
 }

@@ -104,17 +104,39 @@ struct XcColP {
 };
 
 // Line-private exchange region of an x tile: line pair l owns N consecutive
-// complex slots (its own two rows), index XOR-swizzled within groups of 16.
-// The threads of a line sit in one warp, so warp barriers order it.
+// complex slots (its own two rows), index XOR-swizzled within groups of 16 so
+// that a line's threads hit distinct 8-byte bank pairs; c (a multiple of the
+// line's thread count) moves the line pairs that share a warp onto different
+// bank pairs.  The threads of a line sit in one warp, so warp barriers order
+// it.
 template <int N>
 struct XcLineR {
     float2 *base;  // tile + l * N complex slots
-    __device__ __forceinline__ float2 &at(int idx) { return base[idx ^ ((idx >> 4) & 15)]; }
+    int c;
+    __device__ __forceinline__ float2 &at(int idx) { return base[idx ^ (((idx >> 4) & 15) ^ c)]; }
     __device__ __forceinline__ void st(int idx, float2 v) { at(idx) = v; }
     __device__ __forceinline__ float2 ld(int idx) { return at(idx); }
     __device__ __forceinline__ void sync() { __syncwarp(); }
     __device__ __forceinline__ void flip() { __syncwarp(); }
 };
+
+// v[e] <-> v[e ^ g] for a g below G (a power of two): conditional swaps bit by
+// bit, as selects (g differs between the line pairs of one warp).
+template <int E, int G>
+__device__ __forceinline__ void xor_permute(float2 (&v)[E], int g)
+{
+#pragma unroll
+    for (int m = 1; m < G; m <<= 1) {
+        const bool f = (g & m) != 0;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            if (e & m) continue;
+            const float2 a = v[e], b = v[e | m];
+            v[e] = f ? b : a;
+            v[e | m] = f ? a : b;
+        }
+    }
+}
 
 // Bounded wait on a stage barrier by every thread, then a block vote: false if
 // any thread timed out.
@@ -128,16 +150,24 @@ __device__ __forceinline__ bool red_stage_wait(uint64_t *bar, uint32_t parity)
 // (and V), computes a L_x src (+ bV V src) with the multipliers `mult` and
 // leaves it in the src tile.  No block barrier inside: the rows of a line pair
 // belong to its N/E threads (within one warp) alone.
+//
+// Rows are multiples of 32 floats apart, so the G = 32/(N/E) line pairs of a
+// warp would read and write the same banks.  Line pair g of its warp
+// therefore moves element t + TT (e ^ g) through register slot e and the
+// registers are permuted into the FFT's natural order (and back) in between.
 template <int N, int E>
 __device__ __forceinline__ void xred_tile(float *src, float *vt, const float *mult, const float2 *tw, float bV,
                                           bool useV, int t, int l)
 {
     constexpr int TT = N / E;
+    static_assert(TT <= 32, "a line's threads must share one warp (the exchange uses warp barriers)");
+    constexpr int G = TT >= 32 ? 1 : 32 / TT;
+    const int g = l & (G - 1);
     const int r0 = 2 * l, r1 = 2 * l + 1;
     float2 v[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-        const int i = t + e * TT;
+        const int i = t + ((TT * e) ^ (TT * g));
         v[e] = make_float2(src[r0 * N + i], src[r1 * N + i]);
         // the V term of this element, parked in its own V slot
         if (useV) {
@@ -145,7 +175,8 @@ __device__ __forceinline__ void xred_tile(float *src, float *vt, const float *mu
             vt[r1 * N + i] = bV * vt[r1 * N + i] * v[e].y;
         }
     }
-    XcLineR<N> xc{reinterpret_cast<float2 *>(src) + l * N};
+    xor_permute<E, G>(v, g);
+    XcLineR<N> xc{reinterpret_cast<float2 *>(src) + l * N, TT < 16 ? (g & (16 / TT - 1)) * TT : 0};
     fft_line<float, N, E, false>(v, t, xc, tw);
 #pragma unroll
     for (int e = 0; e < E; ++e) {
@@ -154,9 +185,10 @@ __device__ __forceinline__ void xred_tile(float *src, float *vt, const float *mu
         v[e].y *= mm;
     }
     fft_line<float, N, E, true>(v, t, xc, tw);
+    xor_permute<E, G>(v, g);
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-        const int i = t + e * TT;
+        const int i = t + ((TT * e) ^ (TT * g));
         src[r0 * N + i] = useV ? v[e].x + vt[r0 * N + i] : v[e].x;
         src[r1 * N + i] = useV ? v[e].y + vt[r1 * N + i] : v[e].y;
     }
