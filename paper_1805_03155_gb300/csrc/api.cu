@@ -591,6 +591,13 @@ bool encode_map(CUtensorMap *m, void *base, uint64_t d0, uint64_t d1, uint64_t d
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Planes per tile of the reduce-add strided pass of axis ax (1 for the x pass).
+int red_planes(const int64_t *n, int ax)
+{
+    if (ax == 0) return 1;
+    return tmared_planes((int)n[ax], tmared_pairs((int)n[ax], n[0]), ax == 1 ? n[2] : n[1]);
+}
+
 // 4D FP32 tensor map (dims d[0] fastest; strides of dims 1..3 in elements)
 // with the given box; out-of-range box elements load as zero and are not
 // written back.
@@ -610,7 +617,8 @@ bool encode_map4(CUtensorMap *m, void *base, const uint64_t *d, const uint64_t *
 // Maps of the reduce-add passes (pass_tmared.cuh): the line axis of length N
 // is split as (L1, L2) = (min(N, 256), N / L1) so that no box dimension
 // exceeds 256.  v = 0: x view (x_lo, x_hi, row, 1); v = 1: y view (x, y_lo,
-// y_hi, z); v = 2: z view (x, y, z_lo, z_hi).
+// y_hi, z); v = 2: z view (x, y, z_lo, z_hi).  Strided boxes span
+// tmared_planes() planes of the outer axis.
 bool encode_red_map(CUtensorMap *m, void *base, const int64_t *n, int v)
 {
     const uint64_t n0 = n[0], n1 = n[1], n2 = n[2];
@@ -620,18 +628,19 @@ bool encode_red_map(CUtensorMap *m, void *base, const int64_t *n, int v)
         const uint32_t box[4] = {(uint32_t)L1, (uint32_t)L2, (uint32_t)tmared_rows_x((int)N), 1};
         return encode_map4(m, base, d, st, box);
     }
-    const uint32_t cols = 2u * (uint32_t)tmared_pairs((int)N, (int64_t)n0);
+    const int P = tmared_pairs((int)N, (int64_t)n0);
+    const uint32_t cols = 2u * (uint32_t)P, K = (uint32_t)red_planes(n, v);
     if (v == 1) {
         const uint64_t d[4] = {n0, L1, L2, n2}, st[3] = {n0, n0 * L1, n0 * n1};
-        const uint32_t box[4] = {cols, (uint32_t)L1, (uint32_t)L2, 1};
+        const uint32_t box[4] = {cols, (uint32_t)L1, (uint32_t)L2, K};
         return encode_map4(m, base, d, st, box);
     }
     const uint64_t d[4] = {n0, n1, L1, L2}, st[3] = {n0, n0 * n1, n0 * n1 * L1};
-    const uint32_t box[4] = {cols, 1, (uint32_t)L1, (uint32_t)L2};
+    const uint32_t box[4] = {cols, K, (uint32_t)L1, (uint32_t)L2};
     return encode_map4(m, base, d, st, box);
 }
 
-// Enables the pipelined passes for FP32 axes of 64..512 points.
+// Enables the pipelined passes for FP32 axes of 32..512 points.
 void setup_tma(spstd_ctx *ctx)
 {
     const spstd_config &cfg = ctx->cfg;
@@ -859,6 +868,7 @@ cudaError_t enqueue_apply(spstd_ctx *ctx, int fsrc, int fdst, int table, double 
                 ta.reverse = rev;
                 ta.status = status;
                 ta.nx = (int)n0;
+                ta.planes = red_planes(cfg.n, ax);
                 if (red) {
                     ta.n_tiles = tmared_tiles(ax, cfg.n, &ta.n_xt);
                     if (ax == 0)
@@ -1090,7 +1100,7 @@ spstd_status prepare_kernels(spstd_ctx *ctx)
     if (cfg.dims == 3 && !ctx->dense[2]) SPSTD_CU(ctx, Launch<T>::spass((int)cfg.n[2], none, ctx->stream));
     if (ctx->fuse_xy) SPSTD_CU(ctx, prepare_xypass_tma((int)cfg.n[0]));
     for (int ax = 0; ax < cfg.dims; ++ax) {
-        if (ctx->tma[ax]) SPSTD_CU(ctx, prepare_pass_tmared(ax, (int)cfg.n[ax], cfg.n[0]));
+        if (ctx->tma[ax]) SPSTD_CU(ctx, prepare_pass_tmared(ax, (int)cfg.n[ax], cfg.n[0], red_planes(cfg.n, ax)));
         if (ctx->tma_st[ax]) SPSTD_CU(ctx, prepare_pass_tma(ax, (int)cfg.n[ax]));
         const int sv = ctx->sched[ax];
         if (sv >= 1 && sv <= 3) {
@@ -1917,7 +1927,7 @@ cudaError_t group_pass(const BatchGroupND &g, int ax, int v, const PassArgs<T> *
     const int N = (int)g.n[ax];
     if constexpr (sizeof(T) == 4) {
         if (group_uses_tma(g, ax, v)) {
-            if (!a) return prepare_pass_tmared_batch(ax, N, g.n[0]);
+            if (!a) return prepare_pass_tmared_batch(ax, N, g.n[0], red_planes(g.n, ax));
             TmaBatchArgs ta{};
             ta.mem = mem;
             ta.pa = a;
@@ -1928,6 +1938,7 @@ cudaError_t group_pass(const BatchGroupND &g, int ax, int v, const PassArgs<T> *
             ta.tiles = tiles;
             tmared_tiles(ax, g.n, &ta.n_xt);
             ta.nx = (int)g.n[0];
+            ta.planes = red_planes(g.n, ax);
             ta.axis = ax;
             return launch_pass_tmared_batch(ax, N, ta, s);
         }

@@ -21,6 +21,7 @@ struct TmaPassArgs {
     int reverse;
     int *status;         // device status word (kStatusTimeout on a timed-out wait)
     int nx;              // reduce-add passes: points along x
+    int planes;          // reduce-add strided pass: tmared_planes()
 };
 
 // Tile geometry the tensor maps must use.
@@ -36,19 +37,30 @@ cudaError_t launch_pass_tma(int axis, int N, const CUtensorMap &msrc, const CUte
 cudaError_t prepare_pass_tma(int axis, int N);
 
 // ---------------------------------------------------------------------------
-// Reduce-add passes (pass_tmared.cuh), the default for FP32 lines of 64..512
+// Reduce-add passes (pass_tmared.cuh), the default for FP32 lines of 32..512
 // points: the destination is accumulated at L2 by a TMA reduce-add.
 // ---------------------------------------------------------------------------
-constexpr bool tmared_eligible(int64_t N) { return N == 64 || N == 128 || N == 256 || N == 512; }
+constexpr bool tmared_eligible(int64_t N) { return N == 32 || N == 64 || N == 128 || N == 256 || N == 512; }
 // x pass: rows per tile (the box height of its x-view maps).
 constexpr int tmared_rows_x(int N) { return 4096 / N; }
 // Strided pass over N points along y or z with nx points along x: column
-// pairs per tile (its y/z-view maps' box is 2P columns wide); 0 if nx < 16.
+// pairs per tile, at most 64 (its y/z-view maps' box is 2P columns wide); 0
+// if nx < 16.
 constexpr int tmared_pairs(int N, int64_t nx)
 {
-    int P = 4096 / N;
+    int P = 4096 / N < 64 ? 4096 / N : 64;
     while (P > 8 && 2 * (int64_t)P > nx) P /= 2;
     return nx >= 16 ? P : 0;
+}
+// Strided pass: planes of the outer axis per tile -- enough for 256 threads
+// per block (tmared_max_planes), or 1 when the outer axis is shorter than that.
+constexpr int tmared_max_planes(int N, int P)
+{
+    return P > 0 && 256 / (P * (N / 16)) > 1 ? 256 / (P * (N / 16)) : 1;
+}
+constexpr int tmared_planes(int N, int P, int64_t outer)
+{
+    return outer >= tmared_max_planes(N, P) ? tmared_max_planes(N, P) : 1;
 }
 // Tiles of one grid (or one batch member) shaped n[3] in the pass of axis ax;
 // *n_xt: tiles across x (strided passes).
@@ -59,19 +71,21 @@ inline int tmared_tiles(int axis, const int64_t *n, int *n_xt)
         const int R = tmared_rows_x((int)n[0]);
         return (int)((n[1] * n[2] + R - 1) / R);
     }
-    const int cols = 2 * tmared_pairs((int)n[axis], n[0]);
-    const int nxt = cols ? (int)((n[0] + cols - 1) / cols) : 0;
+    const int P = tmared_pairs((int)n[axis], n[0]);
+    const int64_t outer = axis == 1 ? n[2] : n[1];
+    const int K = tmared_planes((int)n[axis], P, outer);
+    const int nxt = P ? (int)((n[0] + 2 * P - 1) / (2 * P)) : 0;
     if (n_xt) *n_xt = nxt;
-    return nxt * (int)(axis == 1 ? n[2] : n[1]);
+    return nxt * (int)((outer + K - 1) / K);
 }
 
-// Single grid: a.n_tiles / a.n_xt from tmared_tiles, a.nx = points along x;
-// mV is the potential in the x view (x pass only).
+// Single grid: a.n_tiles / a.n_xt from tmared_tiles, a.nx = points along x,
+// a.planes from tmared_planes; mV is the potential in the x view (x pass only).
 cudaError_t launch_pass_tmared(int axis, int N, const CUtensorMap &msrc, const CUtensorMap &mV,
                                const CUtensorMap &mdst, const TmaPassArgs &a, cudaStream_t s);
 // Raises the kernel's shared-memory limit and sizes its persistent grid (call
 // before a stream capture); nx: points along x.
-cudaError_t prepare_pass_tmared(int axis, int N, int64_t nx);
+cudaError_t prepare_pass_tmared(int axis, int N, int64_t nx, int planes);
 
 // One member of a batched pass: tensor maps over its own fields (0 psi_R,
 // 1 psi_I, 2 scratch; index 3 of the x view is V) with the reduce-add boxes,
@@ -96,11 +110,12 @@ struct TmaBatchArgs {
     int tiles;
     int n_xt;
     int nx;            // points along x
+    int planes;        // strided pass: tmared_planes()
     int axis;
 };
 
 cudaError_t launch_pass_tmared_batch(int axis, int N, const TmaBatchArgs &a, cudaStream_t s);
-cudaError_t prepare_pass_tmared_batch(int axis, int N, int64_t nx);
+cudaError_t prepare_pass_tmared_batch(int axis, int N, int64_t nx, int planes);
 
 struct XyPassArgs;
 // x and y passes of a 3D half-stage in one persistent launch (pass_xy.cuh);

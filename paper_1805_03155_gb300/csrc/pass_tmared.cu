@@ -1,5 +1,5 @@
 // Instantiations and launchers of the reduce-add pipelined passes
-// (pass_tmared.cuh): single grids and batches, lines of 64..512 points.
+// (pass_tmared.cuh): single grids and batches, lines of 32..512 points.
 #include "pass_tmared.cuh"
 #include "persist.cuh"
 
@@ -29,13 +29,13 @@ cudaError_t red_x(const CUtensorMap *ms, const CUtensorMap *mv, const CUtensorMa
     return cudaGetLastError();
 }
 
-template <int N, int P, bool BATCH>
+template <int N, int P, int K, bool BATCH>
 cudaError_t red_s(const CUtensorMap *ms, const CUtensorMap *md, const TmaPassArgs *a, const TmaBatchArgs *ba,
                   cudaStream_t s)
 {
-    using G = SRed<N, kRedE, P, BATCH>;
+    using G = SRed<N, kRedE, P, K, BATCH>;
     int grid = 0;
-    cudaError_t e = persistent_grid<spass_tmared_kernel<N, kRedE, P, BATCH>>(G::THREADS, G::SMEM, &grid);
+    cudaError_t e = persistent_grid<spass_tmared_kernel<N, kRedE, P, K, BATCH>>(G::THREADS, G::SMEM, &grid);
     if (e != cudaSuccess || !(BATCH ? (const void *)ba : (const void *)a)) return e;
     const int total = BATCH ? ba->members * ba->tiles : a->n_tiles;
     if (total < grid) grid = total;
@@ -43,26 +43,39 @@ cudaError_t red_s(const CUtensorMap *ms, const CUtensorMap *md, const TmaPassArg
     const CUtensorMap none{};
     const TmaPassArgs a0{};
     const TmaBatchArgs b0{};
-    spass_tmared_kernel<N, kRedE, P, BATCH><<<grid, dim3(P, G::TT), G::SMEM, s>>>(
+    spass_tmared_kernel<N, kRedE, P, K, BATCH><<<grid, dim3(P, G::TT, K), G::SMEM, s>>>(
         BATCH ? none : *ms, BATCH ? none : *md, BATCH ? a0 : *a, BATCH ? *ba : b0);
     return cudaGetLastError();
 }
 
-// Strided pass of N points with P column pairs (P from tmared_pairs).
+// Strided pass of N points with P column pairs and K planes per tile (from
+// tmared_pairs, tmared_planes: K is tmared_max_planes(N, P) or 1).
+template <int N, int P, bool BATCH>
+cudaError_t red_s_k(int K, const CUtensorMap *ms, const CUtensorMap *md, const TmaPassArgs *a,
+                    const TmaBatchArgs *ba, cudaStream_t s)
+{
+    constexpr int KM = tmared_max_planes(N, P);
+    if (K == KM) return red_s<N, P, KM, BATCH>(ms, md, a, ba, s);
+    if constexpr (KM > 1) {
+        if (K == 1) return red_s<N, P, 1, BATCH>(ms, md, a, ba, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
 template <int N, bool BATCH>
-cudaError_t red_s_p(int P, const CUtensorMap *ms, const CUtensorMap *md, const TmaPassArgs *a,
+cudaError_t red_s_p(int P, int K, const CUtensorMap *ms, const CUtensorMap *md, const TmaPassArgs *a,
                     const TmaBatchArgs *ba, cudaStream_t s)
 {
     switch (P) {
-    case 8: return red_s<N, 8, BATCH>(ms, md, a, ba, s);
+    case 8: return red_s_k<N, 8, BATCH>(K, ms, md, a, ba, s);
     case 16:
-        if constexpr (4096 / N >= 16) return red_s<N, 16, BATCH>(ms, md, a, ba, s);
+        if constexpr (4096 / N >= 16) return red_s_k<N, 16, BATCH>(K, ms, md, a, ba, s);
         break;
     case 32:
-        if constexpr (4096 / N >= 32) return red_s<N, 32, BATCH>(ms, md, a, ba, s);
+        if constexpr (4096 / N >= 32) return red_s_k<N, 32, BATCH>(K, ms, md, a, ba, s);
         break;
     case 64:
-        if constexpr (4096 / N >= 64) return red_s<N, 64, BATCH>(ms, md, a, ba, s);
+        if constexpr (4096 / N >= 64) return red_s_k<N, 64, BATCH>(K, ms, md, a, ba, s);
         break;
     default: break;
     }
@@ -70,13 +83,14 @@ cudaError_t red_s_p(int P, const CUtensorMap *ms, const CUtensorMap *md, const T
 }
 
 template <bool BATCH>
-cudaError_t red_any(int axis, int N, int64_t nx, const CUtensorMap *ms, const CUtensorMap *mv,
+cudaError_t red_any(int axis, int N, int64_t nx, int K, const CUtensorMap *ms, const CUtensorMap *mv,
                     const CUtensorMap *md, const TmaPassArgs *a, const TmaBatchArgs *ba, cudaStream_t s)
 {
     if (!tmared_eligible(N)) return cudaErrorInvalidValue;
     if (axis == 0) {
         if (nx != N) return cudaErrorInvalidValue;
         switch (N) {
+        case 32: return red_x<32, BATCH>(ms, mv, md, a, ba, s);
         case 64: return red_x<64, BATCH>(ms, mv, md, a, ba, s);
         case 128: return red_x<128, BATCH>(ms, mv, md, a, ba, s);
         case 256: return red_x<256, BATCH>(ms, mv, md, a, ba, s);
@@ -85,10 +99,11 @@ cudaError_t red_any(int axis, int N, int64_t nx, const CUtensorMap *ms, const CU
     }
     const int P = tmared_pairs(N, nx);
     switch (N) {
-    case 64: return red_s_p<64, BATCH>(P, ms, md, a, ba, s);
-    case 128: return red_s_p<128, BATCH>(P, ms, md, a, ba, s);
-    case 256: return red_s_p<256, BATCH>(P, ms, md, a, ba, s);
-    default: return red_s_p<512, BATCH>(P, ms, md, a, ba, s);
+    case 32: return red_s_p<32, BATCH>(P, K, ms, md, a, ba, s);
+    case 64: return red_s_p<64, BATCH>(P, K, ms, md, a, ba, s);
+    case 128: return red_s_p<128, BATCH>(P, K, ms, md, a, ba, s);
+    case 256: return red_s_p<256, BATCH>(P, K, ms, md, a, ba, s);
+    default: return red_s_p<512, BATCH>(P, K, ms, md, a, ba, s);
     }
 }
 
@@ -97,22 +112,22 @@ cudaError_t red_any(int axis, int N, int64_t nx, const CUtensorMap *ms, const CU
 cudaError_t launch_pass_tmared(int axis, int N, const CUtensorMap &msrc, const CUtensorMap &mV,
                                const CUtensorMap &mdst, const TmaPassArgs &a, cudaStream_t s)
 {
-    return red_any<false>(axis, N, a.nx, &msrc, &mV, &mdst, &a, nullptr, s);
+    return red_any<false>(axis, N, a.nx, a.planes, &msrc, &mV, &mdst, &a, nullptr, s);
 }
 
-cudaError_t prepare_pass_tmared(int axis, int N, int64_t nx)
+cudaError_t prepare_pass_tmared(int axis, int N, int64_t nx, int planes)
 {
-    return red_any<false>(axis, N, nx, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+    return red_any<false>(axis, N, nx, planes, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
 }
 
 cudaError_t launch_pass_tmared_batch(int axis, int N, const TmaBatchArgs &a, cudaStream_t s)
 {
-    return red_any<true>(axis, N, a.nx, nullptr, nullptr, nullptr, nullptr, &a, s);
+    return red_any<true>(axis, N, a.nx, a.planes, nullptr, nullptr, nullptr, nullptr, &a, s);
 }
 
-cudaError_t prepare_pass_tmared_batch(int axis, int N, int64_t nx)
+cudaError_t prepare_pass_tmared_batch(int axis, int N, int64_t nx, int planes)
 {
-    return red_any<true>(axis, N, nx, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+    return red_any<true>(axis, N, nx, planes, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
 }
 
 }  // namespace spstd

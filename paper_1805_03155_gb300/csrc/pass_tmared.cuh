@@ -1,5 +1,5 @@
 // pass_tmared.cuh -- the default pipelined FP32 half-stage passes (lines of
-// 64..512 points): TMA loads into shared-memory rings, a TMA reduce-add
+// 32..512 points): TMA loads into shared-memory rings, a TMA reduce-add
 // epilogue.
 //
 // The destination field never enters the SM.  A block computes its tile's
@@ -15,8 +15,9 @@
 // 128 (x) or 256 (strided) threads and a 16 KB / 32 KB tile part):
 //   x pass:        ROWS = 4096/N contiguous rows of N points, ROWS/2 line
 //                  pairs, block (N/E, ROWS/2), stage = src + V tiles;
-//   strided pass:  N points along y or z x 2P adjacent x columns (P column
-//                  pairs, P = min(4096/N, n_x/2)), block (P, N/E).
+//   strided pass:  K planes of N points along y or z x 2P adjacent x columns
+//                  (P column pairs, P = min(4096/N, n_x/2); K = 256/(P N/E)
+//                  planes, at least 1), block (P, N/E, K).
 // Waits are bounded: on a timeout the block records kStatusTimeout, lets its
 // bulk operations drain and returns.
 //
@@ -89,14 +90,15 @@ __device__ __forceinline__ void tmared_setup(const TmaRedSmem &m, const float2 *
     __syncthreads();
 }
 
-// Column exchange inside a strided tile ([N rows][P pairs], pair p at column
-// p): a warp spans consecutive pairs of one or more rows, so its accesses are
-// contiguous row segments.  Block barriers order it; each read phase is closed
-// by a second barrier (flip) before the next write phase.
-template <int P>
+// Column exchange inside a strided tile: element idx of a line sits rs
+// complex slots after element idx - 1 (rs = P, or K P for a z tile of K
+// planes); a warp spans consecutive pairs of one or more rows, so its accesses
+// are contiguous row segments.  Block barriers order it; each read phase is
+// closed by a second barrier (flip) before the next write phase.
 struct XcColP {
-    float2 *base;  // tile + p
-    __device__ __forceinline__ float2 &at(int idx) { return base[idx * P]; }
+    float2 *base;  // the line's first element
+    int rs;
+    __device__ __forceinline__ float2 &at(int idx) { return base[idx * rs]; }
     __device__ __forceinline__ void st(int idx, float2 v) { at(idx) = v; }
     __device__ __forceinline__ float2 ld(int idx) { return at(idx); }
     __device__ __forceinline__ void sync() { __syncthreads(); }
@@ -194,18 +196,19 @@ __device__ __forceinline__ void xred_tile(float *src, float *vt, const float *mu
     }
 }
 
-// One strided tile ([N rows][P column pairs] of float2): column pair p,
-// thread t.  Computes a L_d src and leaves it in the tile.  Contains block
-// barriers (the column exchange spans the block).
-template <int N, int E, int P>
-__device__ __forceinline__ void sred_tile(float2 *src, const float *mult, const float2 *tw, int t, int p)
+// One line of a strided tile (its first element at `line`, consecutive
+// elements rs complex slots apart), thread t.  Computes a L_d src and leaves
+// it in the tile.  Contains block barriers (the column exchange spans the
+// block).
+template <int N, int E>
+__device__ __forceinline__ void sred_tile(float2 *line, int rs, const float *mult, const float2 *tw, int t)
 {
     constexpr int TT = N / E;
     float2 v[E];
 #pragma unroll
-    for (int e = 0; e < E; ++e) v[e] = src[(t + e * TT) * P + p];
+    for (int e = 0; e < E; ++e) v[e] = line[(t + e * TT) * rs];
     __syncthreads();
-    XcColP<P> xc{src + p};
+    XcColP xc{line, rs};
     fft_line<float, N, E, false>(v, t, xc, tw);
 #pragma unroll
     for (int e = 0; e < E; ++e) {
@@ -216,16 +219,15 @@ __device__ __forceinline__ void sred_tile(float2 *src, const float *mult, const 
     fft_line<float, N, E, true>(v, t, xc, tw);
     // the inverse's last exchange ended with a block barrier: the tile is free
 #pragma unroll
-    for (int e = 0; e < E; ++e) src[(t + e * TT) * P + p] = v[e];
+    for (int e = 0; e < E; ++e) line[(t + e * TT) * rs] = v[e];
 }
 
 // Where tile g of a launch is: member i (0 for a single grid) and the 4D
 // coordinates of its box.  The maps split the line axis into (L1, L2) =
 // (min(N, 256), N / L1) so that no box dimension exceeds 256:
-//   x view  (x_lo, x_hi, row, 1)      box (L1, L2, ROWS, 1)
-//   y view  (x, y_lo, y_hi, z)        box (2P, L1, L2, 1)
-//   z view  (x, y, z_lo, z_hi)        box (2P, 1, L1, L2)
-// and each box lands in shared memory row-major along the line.
+//   x view  (x_lo, x_hi, row, 1)      box (L1, L2, ROWS, 1)   smem [ROWS][N]
+//   y view  (x, y_lo, y_hi, z)        box (2P, L1, L2, K)     smem [K][N][2P]
+//   z view  (x, y, z_lo, z_hi)        box (2P, K, L1, L2)     smem [N][K][2P]
 struct TileAt {
     int i, c[4];
 };
@@ -242,7 +244,10 @@ __device__ __forceinline__ TileAt tile_at_x(int g, int tiles, int rows, int reve
     return a;
 }
 
-__device__ __forceinline__ TileAt tile_at_s(int g, int tiles, int n_xt, int cols, int axis, int reverse, int total)
+// Strided tiles hold K consecutive planes of the outer axis (z for the y
+// pass, y for the z pass).
+__device__ __forceinline__ TileAt tile_at_s(int g, int tiles, int n_xt, int cols, int K, int axis, int reverse,
+                                            int total)
 {
     if (reverse) g = total - 1 - g;
     TileAt a;
@@ -250,9 +255,9 @@ __device__ __forceinline__ TileAt tile_at_s(int g, int tiles, int n_xt, int cols
     const int lt = g - a.i * tiles;
     const int outer = lt / n_xt;
     a.c[0] = (lt - outer * n_xt) * cols;
-    a.c[1] = axis == 1 ? 0 : outer;
+    a.c[1] = axis == 1 ? 0 : outer * K;
     a.c[2] = 0;
-    a.c[3] = axis == 1 ? outer : 0;
+    a.c[3] = axis == 1 ? outer * K : 0;
     return a;
 }
 
@@ -351,44 +356,49 @@ xpass_tmared_kernel(const __grid_constant__ CUtensorMap msrc, const __grid_const
 // ---------------------------------------------------------------------------
 // strided pass (y or z), P column pairs per tile.
 // ---------------------------------------------------------------------------
-template <int N, int E, int P, bool BATCH>
+template <int N, int E, int P, int K, bool BATCH>
 struct SRed {
     static constexpr int TT = N / E;
-    static constexpr int THREADS = P * TT;
-    static constexpr int TILE = 2 * P * N;
+    static constexpr int THREADS = P * TT * K;
+    static constexpr int TILE = 2 * P * N * K;
     static constexpr int S = tmared_stages<TILE, 1, kRedBlocks>();
     static constexpr size_t SMEM = tmared_smem<N, TILE, 1, S, BATCH>();
 };
 
-template <int N, int E, int P, bool BATCH>
-__global__ void __launch_bounds__(SRed<N, E, P, BATCH>::THREADS, kRedBlocks)
+// block (P, N/E, K): column pair p of plane k.
+template <int N, int E, int P, int K, bool BATCH>
+__global__ void __launch_bounds__(SRed<N, E, P, K, BATCH>::THREADS, kRedBlocks)
 spass_tmared_kernel(const __grid_constant__ CUtensorMap msrc, const __grid_constant__ CUtensorMap mdst,
                     const TmaPassArgs a, const TmaBatchArgs ba)
 {
-    using G = SRed<N, E, P, BATCH>;
+    using G = SRed<N, E, P, K, BATCH>;
     constexpr int TILE = G::TILE, S = G::S;
     constexpr uint32_t kTileBytes = TILE * sizeof(float);
     extern __shared__ unsigned char smem_raw[];
     const TmaRedSmem m = tmared_carve<N, TILE, 1, S, BATCH>(smem_raw);
-    const int p = threadIdx.x, t = threadIdx.y, tid = t * P + p;
+    const int p = threadIdx.x, t = threadIdx.y, k = threadIdx.z;
+    const int tid = (k * G::TT + t) * P + p;
     tmared_setup<N, S>(m, BATCH ? ba.tw : a.tw, BATCH ? nullptr : a.mult, tid, G::THREADS);
     const int axis = BATCH ? ba.axis : a.axis;
     const int fsrc = BATCH ? (ba.src >= 0 ? ba.src : 1 - ba.dst) : 0;
+    // this thread's line in a tile, and the distance between its elements
+    const int line0 = K == 1 ? p : (axis == 1 ? k * N * P + p : k * P + p);
+    const int rs = K == 1 ? P : (axis == 1 ? P : K * P);
 
     const int tiles = BATCH ? ba.tiles : a.n_tiles;
     const int n_xt = BATCH ? ba.n_xt : a.n_xt;
     const int total = BATCH ? ba.members * ba.tiles : a.n_tiles;
     const int reverse = BATCH ? 0 : a.reverse;
     const int nk = (int)blockIdx.x < total ? (total - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    auto at = [&](int k) {
-        return tile_at_s((int)blockIdx.x + k * (int)gridDim.x, tiles, n_xt, 2 * P, axis, reverse, total);
+    auto at = [&](int kk) {
+        return tile_at_s((int)blockIdx.x + kk * (int)gridDim.x, tiles, n_xt, 2 * P, K, axis, reverse, total);
     };
     auto view = [&](int i, int f) -> const CUtensorMap * {
         return axis == 1 ? &ba.mem[i].y[f] : &ba.mem[i].z[f];
     };
-    auto issue = [&](int k) {
-        const int s = k % S;
-        const TileAt c = at(k);
+    auto issue = [&](int kk) {
+        const int s = kk % S;
+        const TileAt c = at(kk);
         if constexpr (BATCH) {
             mbar_arrive_expect_tx(&m.full[s], kTileBytes + N * sizeof(float));
             load_tile(m.src + s * TILE, view(c.i, fsrc), c, &m.full[s]);
@@ -399,12 +409,12 @@ spass_tmared_kernel(const __grid_constant__ CUtensorMap msrc, const __grid_const
         }
     };
     if (tid == 0)
-        for (int k = 0; k < S - 1 && k < nk; ++k) issue(k);
+        for (int kk = 0; kk < S - 1 && kk < nk; ++kk) issue(kk);
 
-    for (int k = 0; k < nk; ++k) {
-        const int s = k % S;
-        const TileAt c = at(k);
-        if (!red_stage_wait(&m.full[s], (uint32_t)((k / S) & 1))) {
+    for (int kk = 0; kk < nk; ++kk) {
+        const int s = kk % S;
+        const TileAt c = at(kk);
+        if (!red_stage_wait(&m.full[s], (uint32_t)((kk / S) & 1))) {
             if (tid == 0) {
                 atomicExch(BATCH ? ba.mem[c.i].status : a.status, kStatusTimeout);
                 bulk_wait_all();
@@ -412,15 +422,15 @@ spass_tmared_kernel(const __grid_constant__ CUtensorMap msrc, const __grid_const
             return;
         }
         float2 *src = reinterpret_cast<float2 *>(m.src + s * TILE);
-        sred_tile<N, E, P>(src, BATCH ? m.mult + s * N : m.mult, m.tw, t, p);
+        sred_tile<N, E>(src + line0, rs, BATCH ? m.mult + s * N : m.mult, m.tw, t);
         fence_proxy_async();
         __syncthreads();
         if (tid == 0) {
             reduce_tile(BATCH ? view(c.i, ba.dst) : &mdst, c, src);
             bulk_commit();
-            if (k + S - 1 < nk) {
+            if (kk + S - 1 < nk) {
                 bulk_wait_read<1>();
-                issue(k + S - 1);
+                issue(kk + S - 1);
             }
         }
     }

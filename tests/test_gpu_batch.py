@@ -104,7 +104,8 @@ def test_tma_batch_members_equal_lone_solves_bitwise():
 
     shapes = [((64, 64), "FR4"), ((64, 64), "FR4"), ((128, 64), "SUZUKI6"), ((64, 64, 64), "FR4"),
               ((64, 64, 64), "FR4"), ((64, 128, 64), "FR4"), ((256, 64), "FR4"), ((512, 512), "FR4"),
-              ((512, 512), "FR4"), ((32, 64, 128), "FR4")]
+              ((512, 512), "FR4"), ((32, 64, 128), "FR4"), ((32, 32, 32), "FR4"), ((32, 32, 32), "FR4"),
+              ((32, 64), "FR4")]
     probs = []
     for k, (shape, integ) in enumerate(shapes):
         dims = len(shape)

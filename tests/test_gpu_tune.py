@@ -42,7 +42,8 @@ def schedule_runs(p, precision, steps):
 
 @pytest.mark.parametrize("n,precision", [((128, 64), 32), ((128, 64), 64), ((64, 64, 64), 32),
                                          ((32, 256, 16), 64), ((512, 32), 32), ((64, 512), 32),
-                                         ((16, 32, 512), 32), ((16, 128, 64), 32)])
+                                         ((16, 32, 512), 32), ((16, 128, 64), 32), ((32, 32, 32), 32),
+                                         ((32, 64), 32)])
 def test_every_schedule_same_step(n, precision):
     p = stable(inputs.gaussian_problem(n, steps=12, noise=1e-2))
     cands, runs = schedule_runs(p, precision, p.steps)
