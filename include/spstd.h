@@ -270,13 +270,18 @@ spstd_status spstd_tune(spstd_ctx *ctx, int reps, double *ms);
 spstd_status spstd_set_xy_fusion(spstd_ctx *ctx, int on);
 spstd_status spstd_get_xy_fusion(const spstd_ctx *ctx, int *on);
 
-/* Test hook for the failure path of the bounded device waits: makes the next
- * fused x-y pass skip one y tile of its first plane, so that the x tiles of
- * that plane wait in vain until their bounded waits run out (about a second)
- * and their blocks return early with the device status word set.  The next synchronising call then reports SPSTD_ETIMEOUT
- * and clears the status and the pass's counters; psi_R and psi_I are left
- * partly updated, and the context stays usable (set a state and step again).
- * SPSTD_EUNSUPPORTED when the context has no fused pass. */
+/* Test hook for the failure path of the bounded device waits.  With the
+ * fused x-y pass active: makes its next launch skip one y tile of its first
+ * plane, so that the x tiles of that plane wait in vain until their bounded
+ * waits run out (about a second).  Otherwise, on a context whose x axis runs
+ * the default pipelined (TMA) pass: makes the next x pass leave its first tile
+ * unloaded, so that the wait on that tile's barrier runs out (a few seconds);
+ * the block then waits for the loads it still has in flight and returns.
+ * Either way the blocks return early with the device status word set, the
+ * next synchronising call reports SPSTD_ETIMEOUT and clears the status;
+ * psi_R and psi_I are left partly updated, and the context stays usable (set
+ * a state and step again).  SPSTD_EUNSUPPORTED when the context has neither
+ * pass. */
 spstd_status spstd_inject_wait_timeout(spstd_ctx *ctx);
 
 /* Norm without device allocation (the paper has no counterpart: this is a

@@ -869,6 +869,7 @@ cudaError_t enqueue_apply(spstd_ctx *ctx, int fsrc, int fdst, int table, double 
                 ta.status = status;
                 ta.nx = (int)n0;
                 ta.planes = red_planes(cfg.n, ax);
+                ta.inject = status + 1;
                 if (red) {
                     ta.n_tiles = tmared_tiles(ax, cfg.n, &ta.n_xt);
                     if (ax == 0)
@@ -2554,7 +2555,16 @@ spstd_status spstd_set_xy_fusion(spstd_ctx *ctx, int on)
 spstd_status spstd_inject_wait_timeout(spstd_ctx *ctx)
 {
     if (!ctx) return SPSTD_EINVAL;
-    if (!fused_active(ctx)) return fail(ctx, SPSTD_EUNSUPPORTED, "no fused x-y pass to stall");
+    if (!fused_active(ctx) && ctx->tma[0] && ctx->sched[0] == 0) {
+        // the next default x pass leaves its first tile unloaded: the word after
+        // the status word is its injection flag
+        const int one = 1;
+        SPSTD_CU(ctx, cudaMemcpyAsync((int *)ctx->ptr(ctx->L.status) + 1, &one, sizeof(one), cudaMemcpyHostToDevice,
+                                      ctx->stream));
+        SPSTD_CU(ctx, cudaStreamSynchronize(ctx->stream));
+        return SPSTD_OK;
+    }
+    if (!fused_active(ctx)) return fail(ctx, SPSTD_EUNSUPPORTED, "no pipelined pass to stall");
     // the next fused pass starts its work list at item 1: the first y tile of
     // plane 0 is never claimed, so that plane's x tiles wait in vain
     const unsigned first = 1u;

@@ -22,6 +22,7 @@ struct TmaPassArgs {
     int *status;         // device status word (kStatusTimeout on a timed-out wait)
     int nx;              // reduce-add passes: points along x
     int planes;          // reduce-add strided pass: tmared_planes()
+    int *inject;         // reduce-add x pass: when *inject != 0, clears it and leaves the first tile unloaded
 };
 
 // Tile geometry the tensor maps must use.

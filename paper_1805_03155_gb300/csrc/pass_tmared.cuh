@@ -148,6 +148,18 @@ __device__ __forceinline__ bool red_stage_wait(uint64_t *bar, uint32_t parity)
     return !__syncthreads_or(!ok);
 }
 
+// Thread 0 after a timed-out wait on tile k of a ring of S stages, nk tiles:
+// records the timeout, then waits (bounded) for the loads it issued for tiles
+// k+1 .. k+S-2 and for its bulk reduces, so that nothing still writes into
+// this block's shared memory when it returns.
+template <int S>
+__device__ __forceinline__ void red_timeout_exit(uint64_t *full, int k, int nk, int *status)
+{
+    atomicExch(status, kStatusTimeout);
+    for (int j = k + 1; j <= k + S - 2 && j < nk; ++j) mbar_wait(&full[j % S], (uint32_t)((j / S) & 1));
+    bulk_wait_all();
+}
+
 // One x tile: line pair l (rows 2l, 2l+1 of the tile), thread t.  Reads src
 // (and V), computes a L_x src (+ bV V src) with the multipliers `mult` and
 // leaves it in the src tile.  No block barrier inside: the rows of a line pair
@@ -317,6 +329,9 @@ xpass_tmared_kernel(const __grid_constant__ CUtensorMap msrc, const __grid_const
             bulk_load(m.mult + s * N, ba.pa[c.i].mult, N * sizeof(float), &m.full[s]);
         } else {
             mbar_arrive_expect_tx(&m.full[s], (useV ? 2 : 1) * kTileBytes);
+            // failure-path test hook: the launch's first tile may be left unloaded
+            // (its barrier then never completes and the wait on it times out)
+            if (k == 0 && blockIdx.x == 0 && a.inject && atomicExch(a.inject, 0) != 0) return;
             load_tile(m.src + s * TILE, &msrc, c, &m.full[s]);
             if (useV) load_tile(m.vt + s * TILE, &mV, c, &m.full[s]);
         }
@@ -328,10 +343,7 @@ xpass_tmared_kernel(const __grid_constant__ CUtensorMap msrc, const __grid_const
         const int s = k % S;
         const TileAt c = at(k);
         if (!red_stage_wait(&m.full[s], (uint32_t)((k / S) & 1))) {
-            if (tid == 0) {
-                atomicExch(BATCH ? ba.mem[c.i].status : a.status, kStatusTimeout);
-                bulk_wait_all();
-            }
+            if (tid == 0) red_timeout_exit<S>(m.full, k, nk, BATCH ? ba.mem[c.i].status : a.status);
             return;
         }
         float *src = m.src + s * TILE;
@@ -415,10 +427,7 @@ spass_tmared_kernel(const __grid_constant__ CUtensorMap msrc, const __grid_const
         const int s = kk % S;
         const TileAt c = at(kk);
         if (!red_stage_wait(&m.full[s], (uint32_t)((kk / S) & 1))) {
-            if (tid == 0) {
-                atomicExch(BATCH ? ba.mem[c.i].status : a.status, kStatusTimeout);
-                bulk_wait_all();
-            }
+            if (tid == 0) red_timeout_exit<S>(m.full, kk, nk, BATCH ? ba.mem[c.i].status : a.status);
             return;
         }
         float2 *src = reinterpret_cast<float2 *>(m.src + s * TILE);

@@ -13,9 +13,18 @@ namespace spstd {
 constexpr int kStatusOk = 0;
 constexpr int kStatusTimeout = 1;
 
-// try_wait may suspend for a while before it returns false; this bound is
-// seconds of real time, far beyond any legitimate wait of these kernels.
-constexpr uint32_t kMaxWaitSpins = 1u << 24;
+// A barrier wait gives up after kMaxWaitNs of wall time (the global timer),
+// or after kMaxWaitSpins polls should that timer not advance: far beyond any
+// legitimate wait of these kernels (microseconds).
+constexpr uint64_t kMaxWaitNs = 2000000000ull;
+constexpr uint32_t kMaxWaitSpins = 1u << 26;
+
+__device__ __forceinline__ uint64_t globaltimer_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -56,8 +65,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 // Bounded wait for the phase with the given parity; false on timeout.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
 {
-    for (uint32_t i = 0; i < kMaxWaitSpins; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (uint32_t i = 0; i < kMaxWaitSpins; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 255u) == 255u && globaltimer_ns() - t0 > kMaxWaitNs) return false;
+    }
     return false;
 }
 

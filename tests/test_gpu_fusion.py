@@ -115,3 +115,27 @@ def test_wait_timeout_is_reported_and_recoverable():
     s.close()
     oR, oI, _ = oracle_run(p)
     assert rel_l2(R, Im, oR, oI) <= 1e-4
+
+
+def test_default_pass_wait_timeout_is_reported_and_recoverable():
+    """The default pipelined x pass whose first tile is never loaded: the wait
+    on that tile's barrier runs out, the block drains its other loads and
+    returns with the status word set; the next synchronising call reports
+    SPSTD_ETIMEOUT, and after a fresh state the context steps correctly again."""
+    from paper_1805_03155_gb300 import spstd
+
+    p = stable(inputs.gaussian_problem((64, 64, 64), steps=3))
+    s = gpu_solver(p, 32, cap=8, merge=False)
+    s.spstd_set_xy_fusion(False)
+    assert s.spstd_get_schedule(0) == 0
+    s.spstd_inject_wait_timeout()
+    s.spstd_step(1)
+    with pytest.raises(spstd.SpstdError) as ei:
+        s.spstd_get_state()
+    assert ei.value.status == spstd.SPSTD_ETIMEOUT
+    s.spstd_set_state(p.psiR, p.psiI)
+    s.spstd_step(3)
+    R, Im = s.spstd_get_state()
+    s.close()
+    oR, oI, _ = oracle_run(p)
+    assert rel_l2(R, Im, oR, oI) <= 1e-4
