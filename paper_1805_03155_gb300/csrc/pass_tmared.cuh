@@ -161,50 +161,50 @@ __device__ __forceinline__ void red_timeout_exit(uint64_t *full, int k, int nk, 
 }
 
 // One x tile: line pair l (rows 2l, 2l+1 of the tile), thread t.  Reads src
-// (and V), computes a L_x src (+ bV V src) with the multipliers `mult` and
-// leaves it in the src tile.  No block barrier inside: the rows of a line pair
-// belong to its N/E threads (within one warp) alone.
+// (and V), computes a L_x src (+ bV V src) with the multipliers mr[e] (of
+// element t + e N/E) and leaves it in the src tile.  No block barrier inside:
+// the rows of a line pair belong to its N/E threads (within one warp) alone.
 //
 // Rows are multiples of 32 floats apart, so the G = 32/(N/E) line pairs of a
 // warp would read and write the same banks.  Line pair g of its warp
 // therefore moves element t + TT (e ^ g) through register slot e and the
 // registers are permuted into the FFT's natural order (and back) in between.
+// The V term stays in registers (w) from the loads to the final write.
 template <int N, int E>
-__device__ __forceinline__ void xred_tile(float *src, float *vt, const float *mult, const float2 *tw, float bV,
-                                          bool useV, int t, int l)
+__device__ __forceinline__ void xred_tile(float *src, const float *vt, const float (&mr)[E], const float2 *tw,
+                                          float bV, bool useV, int t, int l)
 {
     constexpr int TT = N / E;
     static_assert(TT <= 32, "a line's threads must share one warp (the exchange uses warp barriers)");
     constexpr int G = TT >= 32 ? 1 : 32 / TT;
     const int g = l & (G - 1);
     const int r0 = 2 * l, r1 = 2 * l + 1;
-    float2 v[E];
+    float2 v[E], w[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         const int i = t + ((TT * e) ^ (TT * g));
         v[e] = make_float2(src[r0 * N + i], src[r1 * N + i]);
-        // the V term of this element, parked in its own V slot
-        if (useV) {
-            vt[r0 * N + i] = bV * vt[r0 * N + i] * v[e].x;
-            vt[r1 * N + i] = bV * vt[r1 * N + i] * v[e].y;
-        }
+        // rounded products (no contraction into the final add), so that every
+        // instantiation of this tile rounds alike
+        w[e] = useV ? make_float2(__fmul_rn(__fmul_rn(bV, vt[r0 * N + i]), v[e].x),
+                                  __fmul_rn(__fmul_rn(bV, vt[r1 * N + i]), v[e].y))
+                    : make_float2(0.f, 0.f);
     }
     xor_permute<E, G>(v, g);
     XcLineR<N> xc{reinterpret_cast<float2 *>(src) + l * N, TT < 16 ? (g & (16 / TT - 1)) * TT : 0};
     fft_line<float, N, E, false>(v, t, xc, tw);
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-        const float mm = mult[t + e * TT];
-        v[e].x *= mm;
-        v[e].y *= mm;
+        v[e].x *= mr[e];
+        v[e].y *= mr[e];
     }
     fft_line<float, N, E, true>(v, t, xc, tw);
     xor_permute<E, G>(v, g);
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         const int i = t + ((TT * e) ^ (TT * g));
-        src[r0 * N + i] = useV ? v[e].x + vt[r0 * N + i] : v[e].x;
-        src[r1 * N + i] = useV ? v[e].y + vt[r1 * N + i] : v[e].y;
+        src[r0 * N + i] = __fadd_rn(v[e].x, w[e].x);
+        src[r1 * N + i] = __fadd_rn(v[e].y, w[e].y);
     }
 }
 
@@ -312,6 +312,10 @@ xpass_tmared_kernel(const __grid_constant__ CUtensorMap msrc, const __grid_const
     tmared_setup<N, S>(m, BATCH ? ba.tw : a.tw, BATCH ? nullptr : a.mult, tid, G::THREADS);
     const bool useV = BATCH || a.use_V != 0;
     const int fsrc = BATCH ? (ba.src >= 0 ? ba.src : 1 - ba.dst) : 0;
+    // single grid: one multiplier row for every tile, held in registers
+    float mrow[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) mrow[e] = BATCH ? 0.f : m.mult[t + e * TT];
 
     const int tiles = BATCH ? ba.tiles : a.n_tiles;
     const int total = BATCH ? ba.members * ba.tiles : a.n_tiles;
@@ -347,10 +351,15 @@ xpass_tmared_kernel(const __grid_constant__ CUtensorMap msrc, const __grid_const
             return;
         }
         float *src = m.src + s * TILE;
-        if constexpr (BATCH)
-            xred_tile<N, E>(src, m.vt + s * TILE, m.mult + s * N, m.tw, ba.pa[c.i].bV, true, t, l);
-        else
-            xred_tile<N, E>(src, m.vt + s * TILE, m.mult, m.tw, a.bV, useV, t, l);
+        if constexpr (BATCH) {
+            // this tile's member's multipliers, from the row its stage carries
+            float mr[E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) mr[e] = m.mult[s * N + t + e * TT];
+            xred_tile<N, E>(src, m.vt + s * TILE, mr, m.tw, ba.pa[c.i].bV, true, t, l);
+        } else {
+            xred_tile<N, E>(src, m.vt + s * TILE, mrow, m.tw, a.bV, useV, t, l);
+        }
         fence_proxy_async();
         __syncthreads();
         if (tid == 0) {
