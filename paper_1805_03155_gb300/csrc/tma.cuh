@@ -95,7 +95,7 @@ __device__ __forceinline__ void bulk_load(void *smem_dst, const void *gsrc, uint
                  : "memory");
 }
 
-// 4D forms of the tile load and of the reduce-add below.
+// 4D tile load (global -> shared), completion counted on bar.
 __device__ __forceinline__ void tma_load_4d(void *smem_dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
                                             uint64_t *bar)
 {
@@ -106,6 +106,9 @@ __device__ __forceinline__ void tma_load_4d(void *smem_dst, const CUtensorMap *m
         : "memory");
 }
 
+// Shared -> global element-wise f32 add of a tile (4D tensor map) into the
+// current bulk group: global[i] += smem[i], performed at L2, so the SM never
+// loads the destination.  Box elements outside the tensor are not touched.
 __device__ __forceinline__ void tma_reduce_add_4d(const CUtensorMap *map, int c0, int c1, int c2, int c3,
                                                   const void *smem_src)
 {
@@ -120,17 +123,6 @@ __device__ __forceinline__ void tma_reduce_add_4d(const CUtensorMap *map, int c0
 __device__ __forceinline__ void tma_store_3d(const CUtensorMap *map, int x, int y, int z, const void *smem_src)
 {
     asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
-                     reinterpret_cast<uint64_t>(map)),
-                 "r"(x), "r"(y), "r"(z), "r"(smem_u32(smem_src))
-                 : "memory");
-}
-
-// Shared -> global element-wise f32 add of a tile (3D tensor map) into the
-// current bulk group: global[i] += smem[i], performed at L2, so the SM never
-// loads the destination.  Box elements outside the tensor are not touched.
-__device__ __forceinline__ void tma_reduce_add_3d(const CUtensorMap *map, int x, int y, int z, const void *smem_src)
-{
-    asm volatile("cp.reduce.async.bulk.tensor.3d.global.shared::cta.add.tile.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
                      reinterpret_cast<uint64_t>(map)),
                  "r"(x), "r"(y), "r"(z), "r"(smem_u32(smem_src))
                  : "memory");
