@@ -1165,7 +1165,6 @@ cudaError_t enqueue_eigen_step(spstd_ctx *ctx, cudaStream_t s, LaunchTimer *time
 template <typename T>
 spstd_status step_impl(spstd_ctx *ctx, int64_t nsteps)
 {
-    const spstd_config &cfg = ctx->cfg;
     T *psi0 = (T *)ctx->ptr(ctx->L.psi[0]);
     T *psi1 = (T *)ctx->ptr(ctx->L.psi[1]);
     if (ctx->rk4 && !ctx->eig_active) {

@@ -176,7 +176,7 @@ xypass_tma_kernel(const __grid_constant__ CUtensorMap msx, const __grid_constant
     if (tid >= NT) {
         // ================= producer warp (lane 0) =================
         if (tid != NT) return;
-        int4 held[kTmaStages];      // item of each stage, loaded and not yet stored
+        int4 held[kTmaStages] = {};  // item of each stage, loaded and not yet stored
         int pend[kTmaStages + 1];   // planes of y tiles stored but not yet counted (oldest first)
         int npend = 0;
         bool newest_y = false;      // the newest committed store is the tail of pend
