@@ -1,5 +1,7 @@
 // Instantiations and launchers of the reduce-add pipelined passes
 // (pass_tmared.cuh): single grids and batches, lines of 32..512 points.
+#include <utility>
+
 #include "pass_tmared.cuh"
 #include "persist.cuh"
 
@@ -9,6 +11,26 @@ namespace {
 // Complex points per thread.  Measured at 256^3: E = 8 (256-thread x blocks,
 // 16 warps per SM) takes 0.054 ms per x pass against 0.047 ms for E = 16.
 constexpr int kRedE = 16;
+
+// Launch with programmatic stream serialisation: the kernel may start while
+// the previous work on the stream finishes; it waits for it (griddepcontrol)
+// after its prologue.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 template <int N, bool BATCH, int EX = kRedE>
 cudaError_t red_x(const CUtensorMap *ms, const CUtensorMap *mv, const CUtensorMap *md, const TmaPassArgs *a,
@@ -24,9 +46,8 @@ cudaError_t red_x(const CUtensorMap *ms, const CUtensorMap *mv, const CUtensorMa
     const CUtensorMap none{};
     const TmaPassArgs a0{};
     const TmaBatchArgs b0{};
-    xpass_tmared_kernel<N, EX, BATCH><<<grid, dim3(G::TT, G::LP), G::SMEM, s>>>(
-        BATCH ? none : *ms, BATCH ? none : *mv, BATCH ? none : *md, BATCH ? a0 : *a, BATCH ? *ba : b0);
-    return cudaGetLastError();
+    return launch_pdl(xpass_tmared_kernel<N, EX, BATCH>, dim3(grid), dim3(G::TT, G::LP), G::SMEM, s,
+                      BATCH ? none : *ms, BATCH ? none : *mv, BATCH ? none : *md, BATCH ? a0 : *a, BATCH ? *ba : b0);
 }
 
 template <int N, int P, int K, bool BATCH>
@@ -43,9 +64,8 @@ cudaError_t red_s(const CUtensorMap *ms, const CUtensorMap *md, const TmaPassArg
     const CUtensorMap none{};
     const TmaPassArgs a0{};
     const TmaBatchArgs b0{};
-    spass_tmared_kernel<N, kRedE, P, K, BATCH><<<grid, dim3(P, G::TT, K), G::SMEM, s>>>(
-        BATCH ? none : *ms, BATCH ? none : *md, BATCH ? a0 : *a, BATCH ? *ba : b0);
-    return cudaGetLastError();
+    return launch_pdl(spass_tmared_kernel<N, kRedE, P, K, BATCH>, dim3(grid), dim3(P, G::TT, K), G::SMEM, s,
+                      BATCH ? none : *ms, BATCH ? none : *md, BATCH ? a0 : *a, BATCH ? *ba : b0);
 }
 
 // Strided pass of N points with P column pairs and K planes per tile (from

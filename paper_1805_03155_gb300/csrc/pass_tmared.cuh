@@ -75,6 +75,13 @@ __device__ __forceinline__ TmaRedSmem tmared_carve(unsigned char *raw)
     return m;
 }
 
+// Block prologue: barriers, twiddles and (single grid) the multiplier row --
+// tables that no kernel writes while steps run -- then the wait for the
+// grids this launch depends on.  Launched with programmatic stream
+// serialisation, the prologue overlaps the previous pass's last tiles; the
+// wait returns once that grid has completed and its writes are visible (at
+// once for an ordinary launch).  The launch then lets its own dependents be
+// scheduled: they start as this grid's blocks exit and wait in turn.
 template <int N, int S>
 __device__ __forceinline__ void tmared_setup(const TmaRedSmem &m, const float2 *tw, const float *mult, int tid,
                                              int nthreads)
@@ -87,6 +94,8 @@ __device__ __forceinline__ void tmared_setup(const TmaRedSmem &m, const float2 *
         m.tw[i] = tw[i];
         if (mult) m.mult[i] = mult[i];
     }
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     __syncthreads();
 }
 
