@@ -130,9 +130,9 @@ def measured_peaks():
 # 256^3 FP32 kernels from one ncu capture (profiles/traffic_aniso_ho_3d_256.md),
 # valid while the kernel sources hash to the recorded value.
 MEASURED_TRAFFIC = {
-    "source_hash": "fca99d1415d0c770",
-    "aniso_ho_3d_256": {"x_pass": 201.364480e6 + 28.128768e6, "y_pass": 134.249216e6 + 5.073408e6,
-                        "z_pass": 134.247680e6 + 5.384960e6},
+    "source_hash": "f28f28bf2ea6692e",
+    "aniso_ho_3d_256": {"x_pass": 201.365504e6 + 27.849728e6, "y_pass": 134.246144e6 + 5.466880e6,
+                        "z_pass": 134.246656e6 + 5.416960e6},
 }
 TRAFFIC_SOURCES = ["paper_1805_03155_gb300/csrc/pass_tmared.cuh", "paper_1805_03155_gb300/csrc/fft_line.cuh",
                    "paper_1805_03155_gb300/csrc/tma.cuh", "paper_1805_03155_gb300/csrc/pass_tma_launch.h"]
@@ -490,6 +490,32 @@ def main():
     nv, ev = s.spstd_energy_norm()
     cc, dd = s.spstd_get_coefficients()
     coeff_halfstages = int(np.count_nonzero(cc) + np.count_nonzero(dd))
+
+    # ---- the other rows of the path, each called as a user would ------------
+    # a7: FP64 norm and energy (H applied to both fields, two fixed-order
+    # reductions; synchronising).  a6: probe-series spectrum and peak fit of the
+    # series recorded so far (2^16-point FP64 FFT for this workload).
+    def host_ms(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t) * 1e3 / reps
+
+    nfft = 1 << 16 if args.workload == "aniso_ho_3d_256" else 0
+    rows = {
+        "a5_probe_ms_per_step": kinds.get("probe", (0.0, 1))[0] / max(1, kinds.get("probe", (0.0, 1))[1]),
+        "a6_nfft": nfft,
+        "what": "a5 from the per-launch events; a6 and a7 by host clock around the synchronising C-ABI calls "
+                "(spstd_spectrum over the sum of the probe series, spstd_energy_norm)",
+    }
+    try:
+        rows["a6_spectrum_ms"] = host_ms(lambda: s.spstd_spectrum(-1, nfft=nfft), 3)
+        rows["a7_energy_norm_ms"] = host_ms(s.spstd_energy_norm, 5)
+    except spstd.SpstdError as e:
+        rows["error"] = str(e)
     s.close()
 
     if rank == 0:
@@ -557,6 +583,7 @@ def main():
                         "probe read back after each chunk, spstd_get_state to pinned FP64 host arrays",
             },
             "check": {"norm_after": nv, "energy_after": ev},
+            "rows": rows,
         }
         if not args.no_batch:
             out["batched_vs_plain"] = batched_vs_plain(local=local)
