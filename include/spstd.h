@@ -232,7 +232,7 @@ spstd_status spstd_profile_steps(spstd_ctx *ctx, int64_t nsteps, double *ms, int
 /* Schedules: the radix and tile plan of an axis's pass kernel (no effect on
  * what is computed; Eq. 10's transform in a different shape).
  *   0  the axis's default kernel (the pipelined TMA pass for FP32 2D/3D axes
- *      of 64..256 points, whose destination field is accumulated at L2 by a
+ *      of 32..512 points, whose destination field is accumulated at L2 by a
  *      TMA reduce-add, else the plain pass: 16 FP32 / 8 FP64 points per
  *      thread, about 256 threads per block)
  *   1  plain pass, half the lines per block
@@ -357,7 +357,7 @@ const char *spstd_batch_last_error(const spstd_batch *b);
 /* Autotunes the batched passes: for every 2D/3D member shape and axis, times
  * the batched pass under schedules 0..4 over all members of that shape
  * (0 = the default: the pipelined TMA reduce-add pass over every member's
- * tiles for FP32 axes of 64..256 points, else the plain plan; 1..3 as for a
+ * tiles for FP32 axes of 32..512 points, else the plain plan; 1..3 as for a
  * lone context; 4 = the plain plan where 0 is the TMA pass) -- H applied into each member's scratch field, once to
  * warm up then reps times -- and keeps the fastest.  The choice is kept per
  * shape (precision, dims, n) for as long as the batch lives, including members

@@ -1,4 +1,5 @@
-// pass_tma.cuh -- pipelined FP32 half-stage passes for line lengths 64..256.
+// pass_tma.cuh -- stored-tile pipelined FP32 half-stage passes for line
+// lengths 64..256 (schedule 5 and the fused x-y pass).
 //
 // One persistent block per SM walks its share of the tiles.  Thread 0 keeps
 // the next tiles in flight with TMA bulk tensor loads into a 3-deep ring of

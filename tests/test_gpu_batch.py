@@ -95,7 +95,7 @@ def test_batch_membership_changes():
 
 
 def test_tma_batch_members_equal_lone_solves_bitwise():
-    """FP32 members whose axes all have 64..256 points run the batched
+    """FP32 members whose axes have 32..512 points run the batched
     pipelined passes (every member's tiles in one launch, its own tensor maps
     and dt-scaled multipliers); they reach bit for bit the state and probes
     of the same solve stepped alone on the single-grid pipelined passes,
