@@ -327,8 +327,8 @@ spstd_status spstd_eigenstates_end(spstd_ctx *ctx);
  * members that share dims, sizes, precision and integrator run every pass of
  * every half-stage as one launch over all their tiles; groups run on parallel
  * branches of a captured CUDA graph, replayed in chunks.  Results equal those
- * of stepping each member alone up to FP rounding order (the single-context
- * FP32 path may use the pipelined TMA passes, a batch the plain passes).
+ * of stepping each member alone up to FP rounding order (bit for bit where
+ * the batch and the lone member run the same pass kernels and plans).
  * Members stay usable (get_state, probe, spectrum, energy_norm) between batch
  * steps; do not call spstd_step on a member while it is in a batch.
  * Device memory: one caller-owned workspace of spstd_batch_workspace_size()

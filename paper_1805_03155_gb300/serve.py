@@ -8,7 +8,9 @@ whose steps are done is retired at the next chunk boundary: its energy, norm
 and probe spectrum are read back, its slot and memory are freed, and its
 latency (retire time minus arrival time) is recorded.  Requests that arrive
 while others run are admitted between chunks, so their work overlaps on the
-device with the running ones.  When a 2D/3D shape joins the batch for the
+device with the running ones.  Setting up a request's context and reading a
+retired member's results happen on a stream of their own while the batch's
+next chunk runs.  When a 2D/3D shape joins the batch for the
 first time, the batch's pass schedules are autotuned (spstd_batch_tune, a few
 milliseconds) before the next chunk; the choice stays for later members.
 """
@@ -41,7 +43,12 @@ class Server:
     def __init__(self, hbm_cap_bytes: float = 150e9, max_slots: int = 1024, chunk_steps: int = 500,
                  precision: int = 32, device: int = 0, keep_state: bool = False, spectrum: bool = True,
                  tune: bool = True):
+        import torch
+
         self.batch = spstd.Batch(max_slots, device=device)
+        # contexts are set up, and their results read, on a stream of their
+        # own, so that this host and device work overlaps the batch's chunks
+        self.setup_stream = torch.cuda.Stream(device=torch.device("cuda", device))
         self.cap = hbm_cap_bytes
         self.chunk = int(chunk_steps)
         self.precision = precision
@@ -49,7 +56,9 @@ class Server:
         self.keep_state = keep_state
         self.spectrum = spectrum
         self.queue: List[Request] = []
+        self.ready: List[Request] = []      # set up, waiting for a batch slot
         self.running: Dict[int, Request] = {}
+        self.retiring: List[Request] = []   # out of the batch, results not read yet
         self.done: List[Request] = []
         self.footprint = 0
         self._next = 0
@@ -77,40 +86,52 @@ class Server:
         self.queue.append(r)
         return r.rid
 
-    def _admit(self, now: float):
+    def _prepare(self, now: float):
+        """Sets up the contexts of arrived requests that fit under the cap."""
         still = []
         for r in self.queue:
             if r.arrival > now or self.footprint + r.need > self.cap:
                 still.append(r)
                 continue
+            r.solver = spstd.solver_for(r.problem, precision=self.precision, probe_capacity=max(1, r.steps),
+                                        device=self.device, stream=self.setup_stream)
+            self.footprint += r.need
+            self.ready.append(r)
+        self.queue = still
+
+    def _admit(self):
+        """Adds set-up requests to the batch (between chunks)."""
+        still = []
+        for r in self.ready:
             try:
-                r.solver = spstd.solver_for(r.problem, precision=self.precision, probe_capacity=max(1, r.steps),
-                                            device=self.device, stream=self.batch.torch_stream)
                 r.slot = self.batch.spstd_batch_add(r.solver)
             except spstd.SpstdError as e:
                 if e.status == spstd.SPSTD_ENOTREADY:  # batch full: wait for a slot
-                    if r.solver is not None:
-                        r.solver.close()
-                        r.solver = None
                     still.append(r)
                     continue
                 raise
             r.admitted = time.perf_counter()
-            self.footprint += r.need
             self.running[r.rid] = r
             shape = (r.problem.dims, tuple(r.problem.n))
             if r.problem.dims > 1 and shape not in self.tuned_shapes:
                 self.tuned_shapes.add(shape)
                 self._untuned = True
-        self.queue = still
+        self.ready = still
         if self.tune and self._untuned:
             self.batch.spstd_batch_tune(reps=2)
             self._untuned = False
 
-    def _retire(self):
+    def _remove_finished(self):
+        """Takes members whose steps are done out of the batch (after a chunk)."""
         for rid in [rid for rid, r in self.running.items() if r.done_steps >= r.steps]:
             r = self.running.pop(rid)
             self.batch.spstd_batch_remove(r.slot)
+            self.retiring.append(r)
+
+    def _collect(self):
+        """Reads the results of retired members (energy, norm, spectrum) and
+        frees them; their work runs on the setup stream."""
+        for r in self.retiring:
             s = r.solver
             r.result["norm"], r.result["energy"] = s.spstd_energy_norm()
             if self.spectrum and r.problem.probes and r.steps >= 2:
@@ -122,30 +143,38 @@ class Server:
             r.finished = time.perf_counter()
             self.footprint -= r.need
             self.done.append(r)
+        self.retiring = []
 
     def step(self):
-        """One scheduling round: admit, advance every member one chunk (or up
-        to the nearest finish), retire."""
-        now = time.perf_counter()
-        self._admit(now)
+        """One scheduling round: admit, start one chunk for every member (or
+        up to the nearest finish), and while it runs read the results of the
+        members retired last round and set up newly arrived requests; then
+        take the finished members out of the batch."""
+        self._prepare(time.perf_counter())
+        self._admit()
         if not self.running:
+            self._collect()
             return False
         n = min(self.chunk, min(r.steps - r.done_steps for r in self.running.values()))
         self.batch.spstd_batch_step(n)
+        self._collect()
+        self._prepare(time.perf_counter())
         self.batch.spstd_batch_sync()
         self.chunks += 1
         for r in self.running.values():
             r.done_steps += n
-        self._retire()
+        self._remove_finished()
         return True
 
     def run(self, until_empty=True, idle_sleep=1e-3):
-        while self.queue or self.running:
+        while self.queue or self.ready or self.running or self.retiring:
             if not self.step():
-                if not self.queue:
+                if not self.queue and not self.ready:
                     break
-                nxt = min(r.arrival for r in self.queue)
-                time.sleep(max(0.0, min(idle_sleep, nxt - time.perf_counter())))
+                if self.queue:
+                    nxt = min(r.arrival for r in self.queue)
+                    time.sleep(max(0.0, min(idle_sleep, nxt - time.perf_counter())))
+        self._collect()
         return self.done
 
     def latencies(self):
@@ -153,7 +182,8 @@ class Server:
         return lat
 
     def close(self):
-        for r in list(self.running.values()):
+        for r in list(self.running.values()) + self.ready + self.retiring:
             if r.solver is not None:
                 r.solver.close()
+                r.solver = None
         self.batch.close()
