@@ -186,7 +186,7 @@ def cpu_baseline(problem, budget_s=20.0):
                       f"{t:.2f} s each, scaled by {h} half-stages per step; single thread, FP64"}
 
 
-def batched_vs_plain(count=512, steps=20, precision=32, local=0):
+def batched_vs_plain(count=512, steps=20, precision=32, local=0, plain=True):
     """The mixed 512-solve workload (1D wells 128..8192, 2D oscillators
     64^2..512^2, 3D oscillators 32^3 and 64^3; FP32 fields, FP64 reductions,
     FR4): `steps` steps of every member through one batch (graph-replayed
@@ -205,16 +205,18 @@ def batched_vs_plain(count=512, steps=20, precision=32, local=0):
     pts = sum(p.n_total for p in probs)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     # plain: one member after another (warm-up captures each member's graph)
-    for s in solvers:
-        s.spstd_step(steps)
-    torch.cuda.synchronize()
-    ev[0].record(stream)
-    for s in solvers:
-        s.spstd_step(steps)
-    ev[1].record(stream)
-    torch.cuda.synchronize()
-    plain_ms = ev[0].elapsed_time(ev[1])
-    plain_launches = sum(s.spstd_launch_count(steps) for s in solvers)
+    plain_ms, plain_launches = float("nan"), 0
+    if plain:
+        for s in solvers:
+            s.spstd_step(steps)
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        for s in solvers:
+            s.spstd_step(steps)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        plain_ms = ev[0].elapsed_time(ev[1])
+        plain_launches = sum(s.spstd_launch_count(steps) for s in solvers)
     # batched
     b = spstd.Batch(count + 1, device=local, stream=stream)
     for s in solvers:
@@ -391,10 +393,20 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-plain and serving legs")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the default pass schedules (no autotuning launches; for profiler launch lists)")
+    ap.add_argument("--batch-only", action="store_true",
+                    help="run only the batched leg of the 512-solve mix and print its numbers (for profiler "
+                         "launch lists of the batched passes)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
+    if args.batch_only:
+        import torch
+        torch.cuda.set_device(0)
+        r = batched_vs_plain(plain=False)
+        print(json.dumps({"batch_only": True, **{k: r[k] for k in ("workload", "members", "grid_points", "steps",
+                                                                    "batched", "unit")}}))
+        return 0
 
     import torch
     ws, rank, local = dist_env()
