@@ -258,15 +258,20 @@ spstd_status spstd_get_schedule(const spstd_ctx *ctx, int axis, int *schedule);
 spstd_status spstd_set_schedule(spstd_ctx *ctx, int axis, int schedule);
 spstd_status spstd_tune(spstd_ctx *ctx, int reps, double *ms);
 
-/* x-y fusion (3D FP32 grids with nx = ny in {64, 128, 256}, x and y on
- * schedule 0; off by default): the x and y passes of each half-stage run
- * as one persistent launch that visits every plane's y tiles and then, while
- * the plane is still in L2, its x tiles, so that HBM carries src, V and dst
- * once for both passes (the sum of Eq. 18's x and y terms, accumulated y then
- * x; FP32 rounding differs from the separate passes).  spstd_tune also times
- * fused against separate and keeps the faster.  spstd_set_xy_fusion returns
- * SPSTD_EUNSUPPORTED when asked to fuse a grid that cannot; *on reports
- * whether steps use the fused launch. */
+/* x-y fusion.  Two fused forms of a half-stage's x and y passes exist, both
+ * for FP32 grids with x and y on schedule 0 (Eq. 18's x and y terms summed in
+ * one launch; FP32 rounding differs from the separate passes):
+ *  - the reduce-add fused pass, for nx = ny in {32, 64} (3D; 2D at 64): a
+ *    unit of planes holds whole x and whole y lines in shared memory, both
+ *    transforms run on it and one reduce-add writes x + y + V terms.  On by
+ *    default where it applies;
+ *  - the stored-tile fused pass (3D, nx = ny in {64, 128, 256}; off by
+ *    default): one persistent launch visits every plane's y tiles and then,
+ *    while the plane is still in L2, its x tiles.
+ * spstd_set_xy_fusion turns the stored-tile form on or off (it takes
+ * precedence) and returns SPSTD_EUNSUPPORTED for a grid that cannot use it;
+ * *on reports whether steps use it.  spstd_tune times separate passes and each
+ * fused form that applies and keeps the fastest. */
 spstd_status spstd_set_xy_fusion(spstd_ctx *ctx, int on);
 spstd_status spstd_get_xy_fusion(const spstd_ctx *ctx, int *on);
 
@@ -274,8 +279,9 @@ spstd_status spstd_get_xy_fusion(const spstd_ctx *ctx, int *on);
  * fused x-y pass active: makes its next launch skip one y tile of its first
  * plane, so that the x tiles of that plane wait in vain until their bounded
  * waits run out (about a second).  Otherwise, on a context whose x axis runs
- * the default pipelined (TMA) pass: makes the next x pass leave its first tile
- * unloaded, so that the wait on that tile's barrier runs out (a few seconds);
+ * the default pipelined (TMA) pass: makes the next x pass (or fused
+ * reduce-add x-y pass) leave its first tile unloaded, so that the wait on
+ * that tile's barrier runs out (about two seconds);
  * the block then waits for the loads it still has in flight and returns.
  * Either way the blocks return early with the device status word set, the
  * next synchronising call reports SPSTD_ETIMEOUT and clears the status;

@@ -375,6 +375,10 @@ struct spstd_ctx {
     int64_t tab_off[3] = {0, 0, 0};         // axis offsets within a multiplier row
     int sched[3] = {0, 0, 0};               // pass schedule per axis (sched.h)
     bool fuse_xy = false;                   // x and y passes as one launch (when both are schedule 0)
+    // fused x-y reduce-add pass for nx = ny in {32, 64}: eligible, in use, maps
+    // (psi_R, psi_I, tmp, V in the unit view)
+    bool fxy_ok = false, fxy_on = false;
+    CUtensorMap fxmap[4];
     // step-boundary merge of the last and first half-stages (same field)
     bool merge = false;
     HalfStage merged{};
@@ -667,6 +671,16 @@ void setup_tma(spstd_ctx *ctx)
         }
         ctx->tma[v] = ok;
     }
+    // fused x-y pass: unit view (x, y, 1, z), box (N, N, 1, K)
+    if (fxy_eligible(cfg.n, cfg.dims) && ctx->tma[0] && ctx->tma[1]) {
+        bool ok = true;
+        const uint64_t d[4] = {n0, n1, 1, n2}, st[3] = {n0, n0 * n1, n0 * n1};
+        const uint32_t box[4] = {(uint32_t)n0, (uint32_t)n1, 1, (uint32_t)fxy_planes((int)n0)};
+        for (int f = 0; f < 4 && ok; ++f)
+            ok = encode_map4(&ctx->fxmap[f], f < 3 ? ctx->ptr(ctx->field_off(f)) : ctx->ptr(ctx->L.V), d, st, box);
+        ctx->fxy_ok = ok;
+        ctx->fxy_on = ok;
+    }
 }
 
 spstd_status set_dt(spstd_ctx *ctx, double vmax)
@@ -760,6 +774,12 @@ double table_scale(const spstd_ctx *ctx, int table)
 // Whether an H-apply between psi_R, psi_I and the scratch field runs x and y as one launch.
 bool fused_active(const spstd_ctx *ctx) { return ctx->fuse_xy && ctx->sched[0] == 0 && ctx->sched[1] == 0; }
 
+// Whether H-applies between the state fields run x and y as the fused reduce-add pass.
+bool fxy_active(const spstd_ctx *ctx)
+{
+    return !fused_active(ctx) && ctx->fxy_ok && ctx->fxy_on && ctx->sched[0] == 0 && ctx->sched[1] == 0;
+}
+
 // dst += a sum_d L_d src + bV V src for fields fsrc -> fdst (0 psi_R, 1 psi_I,
 // 2 scratch), multiplier set `table`; the V term rides on the x pass.
 template <typename T>
@@ -796,6 +816,19 @@ cudaError_t enqueue_apply(spstd_ctx *ctx, int fsrc, int fdst, int table, double 
             SPSTD_TIMED(timer, s, 5,
                         launch_xypass_tma((int)n0, ctx->tmap[fsrc][0], ctx->tmap[fdst][0], ctx->tmap[fsrc][1],
                                           ctx->tmap[fdst][1], xa, s));
+            ax0 = 2;
+        } else if (fxy_active(ctx) && only_axis < 0 && fsrc <= 2 && fdst <= 2) {
+            TmaPassArgs fa{};
+            fa.tw = (const float2 *)ctx->ptr(ctx->L.tw[0]);
+            fa.mult = (const float *)(mult + off[0]);
+            fa.mult_y = (const float *)(mult + off[1]);
+            fa.bV = (float)bV;
+            fa.use_V = 1;
+            fa.n_tiles = fxy_units(cfg.n);
+            fa.status = status;
+            fa.inject = status + 1;
+            SPSTD_TIMED(timer, s, 5,
+                        launch_pass_fxy((int)n0, ctx->fxmap[fsrc], ctx->fxmap[3], ctx->fxmap[fdst], fa, s));
             ax0 = 2;
         }
     }
@@ -1017,7 +1050,7 @@ cudaError_t enqueue_merged_piece(spstd_ctx *ctx, int piece, int64_t units, cudaS
 // for a four-step x axis, one for a fused x-y pair.
 int64_t apply_launches(const spstd_ctx *ctx)
 {
-    return ctx->cfg.dims + (ctx->long_x ? 2 : 0) - (fused_active(ctx) ? 1 : 0);
+    return ctx->cfg.dims + (ctx->long_x ? 2 : 0) - (fused_active(ctx) || fxy_active(ctx) ? 1 : 0);
 }
 
 // A 1D grid runs all steps of a call in one resident launch unless its line
@@ -1103,6 +1136,7 @@ spstd_status prepare_kernels(spstd_ctx *ctx)
     for (int ax = 0; ax < cfg.dims; ++ax) {
         if (ctx->tma[ax]) SPSTD_CU(ctx, prepare_pass_tmared(ax, (int)cfg.n[ax], cfg.n[0], red_planes(cfg.n, ax)));
         if (ctx->tma_st[ax]) SPSTD_CU(ctx, prepare_pass_tma(ax, (int)cfg.n[ax]));
+        if (ax == 0 && ctx->fxy_ok) SPSTD_CU(ctx, prepare_pass_fxy((int)cfg.n[0], false));
         const int sv = ctx->sched[ax];
         if (sv >= 1 && sv <= 3) {
             PassArgs<T> z{};
@@ -1786,6 +1820,7 @@ struct BatchGroupND {
     int tiles[3];
     int sched[3];      // pass schedule per axis (0..4; 0 is the TMA pass where tma[ax])
     bool tma[3];       // axis can run the batched reduce-add TMA pass
+    bool fxy;          // x and y run as the batched fused x-y pass (while both are on schedule 0)
     size_t args_off;   // PassArgs<T> [nh * dims][M]
     size_t probe_off;  // ProbeMember<T> [M]
     size_t tma_off;    // TmaMember [M] (when any tma[ax])
@@ -1983,6 +2018,8 @@ void build_nd_descriptors(spstd_batch *b, BatchGroupND &g, std::vector<unsigned 
         any |= ok;
     }
     g.tma_off = 0;
+    g.fxy = any && g.tma[0] && g.tma[1];
+    for (int i = 0; i < M && g.fxy; ++i) g.fxy = b->slots[g.slots[i]]->fxy_ok && b->slots[g.slots[i]]->fxy_on;
     if (any) {
         std::vector<TmaMember> tm(M);
         for (int i = 0; i < M; ++i) {
@@ -1995,6 +2032,8 @@ void build_nd_descriptors(spstd_batch *b, BatchGroupND &g, std::vector<unsigned 
                 if (g.tma[1]) t.y[f] = ctx->srmap[f][0];
                 if (g.tma[2]) t.z[f] = ctx->srmap[f][1];
             }
+            if (g.fxy)
+                for (int f = 0; f < 4; ++f) t.f[f] = ctx->fxmap[f];
             t.status = (int *)ctx->ptr(ctx->L.status);
         }
         g.tma_off = put(img, tm.data(), sizeof(TmaMember) * tm.size());
@@ -2084,8 +2123,26 @@ cudaError_t enqueue_group_step(spstd_batch *b, const BatchGroupND &g, cudaStream
     const PassArgs<T> *args = (const PassArgs<T> *)(b->ws + g.args_off);
     const TmaMember *mem = (const TmaMember *)(b->ws + g.tma_off);
     const spstd_ctx *first = b->slots[g.slots[0]];
+    const bool fxy = sizeof(T) == 4 && g.fxy && g.sched[0] == 0 && g.sched[1] == 0;
     for (int h = 0; h < g.nh; ++h) {
-        for (int ax = 0; ax < g.dims; ++ax) {
+        int ax0 = 0;
+        if constexpr (sizeof(T) == 4) {
+            if (fxy) {
+                TmaBatchArgs fa{};
+                fa.mem = mem;
+                fa.pa = (const PassArgs<float> *)(args + ((size_t)h * g.dims + 0) * M);
+                fa.pa_y = (const PassArgs<float> *)(args + ((size_t)h * g.dims + 1) * M);
+                fa.tw = (const float2 *)g.tw[0];
+                fa.src = -1;
+                fa.dst = first->hs[h].dst;
+                fa.members = M;
+                fa.tiles = fxy_units(g.n);
+                cudaError_t e = launch_pass_fxy_batch((int)g.n[0], fa, s);
+                if (e != cudaSuccess) return e;
+                ax0 = 2;
+            }
+        }
+        for (int ax = ax0; ax < g.dims; ++ax) {
             const PassArgs<T> *a = args + ((size_t)h * g.dims + ax) * M;
             cudaError_t e = group_pass<T>(g, ax, g.sched[ax], a, M, g.tiles[ax], s, mem, -1, first->hs[h].dst);
             if (e != cudaSuccess) return e;
@@ -2134,6 +2191,10 @@ cudaError_t batch_prepare(spstd_batch *b)
         for (int ax = 0; ax < g.dims; ++ax) {
             cudaError_t e = g.precision == 32 ? group_pass<float>(g, ax, g.sched[ax], nullptr, 0, 0, nullptr)
                                               : group_pass<double>(g, ax, g.sched[ax], nullptr, 0, 0, nullptr);
+            if (e != cudaSuccess) return e;
+        }
+        if (g.fxy) {
+            cudaError_t e = prepare_pass_fxy((int)g.n[0], true);
             if (e != cudaSuccess) return e;
         }
     }
@@ -2321,38 +2382,38 @@ spstd_status spstd_batch_launch_count(const spstd_batch *b, int64_t nsteps, int6
 {
     if (!b || !launches || nsteps < 0) return SPSTD_EINVAL;
     int64_t per_step = 0, per_call = 0;
-    for (auto *c : b->slots) {
-        (void)c;
-    }
-    std::vector<std::pair<int, int64_t>> seen1;
-    int64_t g1 = 0, gnd = 0;
-    // groups are only known after a build; count them the same way
-    std::vector<std::vector<int64_t>> keys;
-    for (auto *c : b->slots) {
-        if (!c) continue;
-        const spstd_config &cfg = c->cfg;
-        std::vector<int64_t> k = {cfg.dims, cfg.precision, cfg.n[0], cfg.n[1], cfg.n[2], (int64_t)c->hs.size(), c->m};
-        for (int l = 0; l < c->m; ++l) {
-            int64_t bc, bd;
-            std::memcpy(&bc, &c->c[l], 8);
-            std::memcpy(&bd, &c->d[l], 8);
-            k.push_back(bc);
-            k.push_back(bd);
+    if (!b->dirty) {
+        // built: the groups as they run
+        per_call = (int64_t)b->g1.size();
+        for (const auto &g : b->gn) {
+            const bool fxy = g.precision == 32 && g.fxy && g.sched[0] == 0 && g.sched[1] == 0;
+            per_step += (int64_t)g.nh * (g.dims - (fxy ? 1 : 0)) + 1;
         }
-        if (cfg.dims == 1) k.resize(3);
-        bool found = false;
-        for (auto &x : keys) found |= x == k;
-        if (found) continue;
-        keys.push_back(k);
-        if (cfg.dims == 1) ++g1;
-        else {
-            ++gnd;
-            per_step += (int64_t)c->hs.size() * cfg.dims + 1;
+    } else {
+        // not built yet: group the members the way a build does (one launch per
+        // axis; the fused x-y pass is known only after the build)
+        std::vector<std::vector<int64_t>> keys;
+        for (auto *c : b->slots) {
+            if (!c) continue;
+            const spstd_config &cfg = c->cfg;
+            std::vector<int64_t> k = {cfg.dims, cfg.precision, cfg.n[0], cfg.n[1], cfg.n[2], (int64_t)c->hs.size(),
+                                      c->m};
+            for (int l = 0; l < c->m; ++l) {
+                int64_t bc, bd;
+                std::memcpy(&bc, &c->c[l], 8);
+                std::memcpy(&bd, &c->d[l], 8);
+                k.push_back(bc);
+                k.push_back(bd);
+            }
+            if (cfg.dims == 1) k.resize(3);
+            bool found = false;
+            for (auto &x : keys) found |= x == k;
+            if (found) continue;
+            keys.push_back(k);
+            if (cfg.dims == 1) ++per_call;
+            else per_step += (int64_t)c->hs.size() * cfg.dims + 1;
         }
     }
-    (void)seen1;
-    (void)gnd;
-    per_call = g1;
     *launches = nsteps ? per_call + nsteps * per_step : 0;
     return SPSTD_OK;
 }
@@ -2428,12 +2489,16 @@ spstd_status tune_impl(spstd_ctx *ctx, int reps, double *ms)
         }
         ctx->sched[ax] = best;
     }
-    // x and y as one launch or two: time a whole H-apply each way
-    if (st == SPSTD_OK && xy_fusable(ctx->cfg) && ctx->tma_st[0] && ctx->tma_st[1] && ctx->sched[0] == 0 &&
-        ctx->sched[1] == 0) {
-        double t2[2] = {0, 0};
-        for (int f = 0; f < 2 && st == SPSTD_OK; ++f) {
+    // x and y as separate passes, the stored-tile fused x-y pass or the fused
+    // reduce-add x-y pass: time a whole H-apply each way and keep the fastest
+    const bool old_ok = xy_fusable(ctx->cfg) && ctx->tma_st[0] && ctx->tma_st[1];
+    if (st == SPSTD_OK && (old_ok || ctx->fxy_ok) && ctx->sched[0] == 0 && ctx->sched[1] == 0) {
+        double best_t = 0.0;
+        int best = 0;
+        for (int f = 0; f < 3 && st == SPSTD_OK; ++f) {
+            if ((f == 1 && !old_ok) || (f == 2 && !ctx->fxy_ok)) continue;
             ctx->fuse_xy = f == 1;
+            ctx->fxy_on = f == 2;
             st = prepare_kernels<T>(ctx);
             if (st != SPSTD_OK) break;
             cudaError_t e = enqueue_apply<T>(ctx, 1, 2, tH, 1.0, 0, s);
@@ -2444,9 +2509,13 @@ spstd_status tune_impl(spstd_ctx *ctx, int reps, double *ms)
             float t = 0.f;
             if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
             if (e != cudaSuccess) st = cuda_fail(ctx, e, "autotune");
-            t2[f] = t;
+            if (f == 0 || t < best_t) {
+                best_t = t;
+                best = f;
+            }
         }
-        ctx->fuse_xy = st == SPSTD_OK ? t2[1] <= t2[0] : true;
+        ctx->fuse_xy = best == 1;
+        ctx->fxy_on = best == 2;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -23,6 +23,7 @@ struct TmaPassArgs {
     int nx;              // reduce-add passes: points along x
     int planes;          // reduce-add strided pass: tmared_planes()
     int *inject;         // reduce-add x pass: when *inject != 0, clears it and leaves the first tile unloaded
+    const float *mult_y; // fused x-y pass: the y axis's multipliers (mult: the x axis's)
 };
 
 // Tile geometry the tensor maps must use.
@@ -95,6 +96,7 @@ struct TmaMember {
     CUtensorMap x[4];  // x view, box N x tmared_rows_x(N)
     CUtensorMap y[3];  // y view, box 2P columns x N
     CUtensorMap z[3];  // z view, box 2P columns x 1 x N
+    CUtensorMap f[4];  // fused x-y view (fxy_eligible grids), box N x N x fxy_planes(N)
     int *status;
 };
 
@@ -105,6 +107,7 @@ struct TmaMember {
 struct TmaBatchArgs {
     const TmaMember *mem;
     const PassArgs<float> *pa;
+    const PassArgs<float> *pa_y;  // fused x-y pass: the members' y-axis descriptors (pa: x axis)
     const float2 *tw;  // W_N, the same for every member
     int src, dst;
     int members;
@@ -116,6 +119,24 @@ struct TmaBatchArgs {
 };
 
 cudaError_t launch_pass_tmared_batch(int axis, int N, const TmaBatchArgs &a, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Fused x + y reduce-add pass (pass_tmared.cuh) for grids with nx = ny = N in
+// {32, 64}: units of fxy_planes(N) planes hold whole x and y lines.  The map
+// views the field as (x, y, 1, z) with box (N, N, 1, fxy_planes(N)).
+// ---------------------------------------------------------------------------
+constexpr int fxy_planes(int N) { return 4096 / (N * N); }
+inline bool fxy_eligible(const int64_t *n, int dims)
+{
+    return dims >= 2 && n[0] == n[1] && (n[0] == 32 || n[0] == 64) && (dims == 3 || fxy_planes((int)n[0]) == 1);
+}
+inline int fxy_units(const int64_t *n) { return (int)((n[2] + fxy_planes((int)n[0]) - 1) / fxy_planes((int)n[0])); }
+// Single grid: a.mult / a.mult_y the x and y multipliers, a.n_tiles = fxy_units.
+cudaError_t launch_pass_fxy(int N, const CUtensorMap &msrc, const CUtensorMap &mV, const CUtensorMap &mdst,
+                            const TmaPassArgs &a, cudaStream_t s);
+// Batched: a.tiles = fxy_units, a.pa / a.pa_y the x and y descriptors.
+cudaError_t launch_pass_fxy_batch(int N, const TmaBatchArgs &a, cudaStream_t s);
+cudaError_t prepare_pass_fxy(int N, bool batch);
 cudaError_t prepare_pass_tmared_batch(int axis, int N, int64_t nx, int planes);
 
 struct XyPassArgs;

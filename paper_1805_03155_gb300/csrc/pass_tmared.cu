@@ -127,7 +127,53 @@ cudaError_t red_any(int axis, int N, int64_t nx, int K, const CUtensorMap *ms, c
     }
 }
 
+template <int N, bool BATCH>
+cudaError_t fxy_n(const CUtensorMap *ms, const CUtensorMap *mv, const CUtensorMap *md, const TmaPassArgs *a,
+                  const TmaBatchArgs *ba, cudaStream_t s)
+{
+    using G = FXy<N, BATCH>;
+    int grid = 0;
+    cudaError_t e = persistent_grid<fxy_tmared_kernel<N, BATCH>>(G::THREADS, G::SMEM, &grid);
+    if (e != cudaSuccess || !(BATCH ? (const void *)ba : (const void *)a)) return e;
+    const int total = BATCH ? ba->members * ba->tiles : a->n_tiles;
+    if (total < grid) grid = total;
+    if (grid <= 0) return cudaSuccess;
+    const CUtensorMap none{};
+    const TmaPassArgs a0{};
+    const TmaBatchArgs b0{};
+    return launch_pdl(fxy_tmared_kernel<N, BATCH>, dim3(grid), dim3(G::THREADS), G::SMEM, s,
+                      BATCH ? none : *ms, BATCH ? none : *mv, BATCH ? none : *md, BATCH ? a0 : *a, BATCH ? *ba : b0);
+}
+
+template <bool BATCH>
+cudaError_t fxy_any(int N, const CUtensorMap *ms, const CUtensorMap *mv, const CUtensorMap *md, const TmaPassArgs *a,
+                    const TmaBatchArgs *ba, cudaStream_t s)
+{
+    switch (N) {
+    case 32: return fxy_n<32, BATCH>(ms, mv, md, a, ba, s);
+    case 64: return fxy_n<64, BATCH>(ms, mv, md, a, ba, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_pass_fxy(int N, const CUtensorMap &msrc, const CUtensorMap &mV, const CUtensorMap &mdst,
+                            const TmaPassArgs &a, cudaStream_t s)
+{
+    return fxy_any<false>(N, &msrc, &mV, &mdst, &a, nullptr, s);
+}
+
+cudaError_t launch_pass_fxy_batch(int N, const TmaBatchArgs &a, cudaStream_t s)
+{
+    return fxy_any<true>(N, nullptr, nullptr, nullptr, nullptr, &a, s);
+}
+
+cudaError_t prepare_pass_fxy(int N, bool batch)
+{
+    return batch ? fxy_any<true>(N, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr)
+                 : fxy_any<false>(N, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+}
 
 cudaError_t launch_pass_tmared(int axis, int N, const CUtensorMap &msrc, const CUtensorMap &mV,
                                const CUtensorMap &mdst, const TmaPassArgs &a, cudaStream_t s)

@@ -179,42 +179,73 @@ __device__ __forceinline__ void red_timeout_exit(uint64_t *full, int k, int nk, 
 // therefore moves element t + TT (e ^ g) through register slot e and the
 // registers are permuted into the FFT's natural order (and back) in between.
 // The V term stays in registers (w) from the loads to the final write.
+// The two halves of an x tile, so that a fused kernel can run other work
+// between them.  Load: this thread's elements of rows 2l, 2l+1 into v (in
+// register-slot order) and the V term into w.  Finish: permute, FFT, k^2,
+// inverse, permute back, and write v + w (+ yadd, another pass's contribution
+// to the same elements, when given) into the src rows.
+template <int N, int E>
+struct XTile {
+    static constexpr int TT = N / E;
+    static_assert(TT <= 32, "a line's threads must share one warp (the exchange uses warp barriers)");
+    static constexpr int G = TT >= 32 ? 1 : 32 / TT;
+    float2 v[E], w[E];
+    int t, l, g;
+
+    __device__ __forceinline__ int pos(int e) const { return t + ((TT * e) ^ (TT * g)); }
+
+    __device__ __forceinline__ void load(const float *src, const float *vt, float bV, bool useV, int t_, int l_)
+    {
+        t = t_;
+        l = l_;
+        g = l & (G - 1);
+        const int r0 = 2 * l, r1 = 2 * l + 1;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int i = pos(e);
+            v[e] = make_float2(src[r0 * N + i], src[r1 * N + i]);
+            // rounded products (no contraction into the final add), so that every
+            // instantiation of this tile rounds alike
+            w[e] = useV ? make_float2(__fmul_rn(__fmul_rn(bV, vt[r0 * N + i]), v[e].x),
+                                      __fmul_rn(__fmul_rn(bV, vt[r1 * N + i]), v[e].y))
+                        : make_float2(0.f, 0.f);
+        }
+    }
+
+    __device__ __forceinline__ void finish(float *src, const float (&mr)[E], const float2 *tw, const float *yadd)
+    {
+        const int r0 = 2 * l, r1 = 2 * l + 1;
+        xor_permute<E, G>(v, g);
+        XcLineR<N> xc{reinterpret_cast<float2 *>(src) + l * N, TT < 16 ? (g & (16 / TT - 1)) * TT : 0};
+        fft_line<float, N, E, false>(v, t, xc, tw);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            v[e].x *= mr[e];
+            v[e].y *= mr[e];
+        }
+        fft_line<float, N, E, true>(v, t, xc, tw);
+        xor_permute<E, G>(v, g);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int i = pos(e);
+            float a = __fadd_rn(v[e].x, w[e].x), b = __fadd_rn(v[e].y, w[e].y);
+            if (yadd) {
+                a = __fadd_rn(a, yadd[r0 * N + i]);
+                b = __fadd_rn(b, yadd[r1 * N + i]);
+            }
+            src[r0 * N + i] = a;
+            src[r1 * N + i] = b;
+        }
+    }
+};
+
 template <int N, int E>
 __device__ __forceinline__ void xred_tile(float *src, const float *vt, const float (&mr)[E], const float2 *tw,
                                           float bV, bool useV, int t, int l)
 {
-    constexpr int TT = N / E;
-    static_assert(TT <= 32, "a line's threads must share one warp (the exchange uses warp barriers)");
-    constexpr int G = TT >= 32 ? 1 : 32 / TT;
-    const int g = l & (G - 1);
-    const int r0 = 2 * l, r1 = 2 * l + 1;
-    float2 v[E], w[E];
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const int i = t + ((TT * e) ^ (TT * g));
-        v[e] = make_float2(src[r0 * N + i], src[r1 * N + i]);
-        // rounded products (no contraction into the final add), so that every
-        // instantiation of this tile rounds alike
-        w[e] = useV ? make_float2(__fmul_rn(__fmul_rn(bV, vt[r0 * N + i]), v[e].x),
-                                  __fmul_rn(__fmul_rn(bV, vt[r1 * N + i]), v[e].y))
-                    : make_float2(0.f, 0.f);
-    }
-    xor_permute<E, G>(v, g);
-    XcLineR<N> xc{reinterpret_cast<float2 *>(src) + l * N, TT < 16 ? (g & (16 / TT - 1)) * TT : 0};
-    fft_line<float, N, E, false>(v, t, xc, tw);
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        v[e].x *= mr[e];
-        v[e].y *= mr[e];
-    }
-    fft_line<float, N, E, true>(v, t, xc, tw);
-    xor_permute<E, G>(v, g);
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const int i = t + ((TT * e) ^ (TT * g));
-        src[r0 * N + i] = __fadd_rn(v[e].x, w[e].x);
-        src[r1 * N + i] = __fadd_rn(v[e].y, w[e].y);
-    }
+    XTile<N, E> x;
+    x.load(src, vt, bV, useV, t, l);
+    x.finish(src, mr, tw, nullptr);
 }
 
 // One line of a strided tile (its first element at `line`, consecutive
@@ -458,6 +489,150 @@ spass_tmared_kernel(const __grid_constant__ CUtensorMap msrc, const __grid_const
             if (kk + S - 1 < nk) {
                 bulk_wait_read<1>();
                 issue(kk + S - 1);
+            }
+        }
+    }
+    if (tid == 0) bulk_wait_all();
+}
+
+// ---------------------------------------------------------------------------
+// Fused x + y pass for grids with nx = ny = N in {32, 64}.  A unit of
+// K = 4096/N^2 planes (16 KB, layout [K][N (y)][N (x)]) holds whole x lines
+// and whole y lines, so both transforms run on it in shared memory and one
+// TMA reduce-add writes the sum of the x term, the V term and the y term:
+// HBM carries src, V and dst once for the two passes (16 B per point instead
+// of 28).  128 threads, two blocks per SM, the same 3-stage ring as the x
+// pass.  Per unit:
+//   1. the x threads load their row-pair elements and the V term (registers);
+//   2. the src unit is copied into the V tile (V is no longer needed);
+//   3. the y transform runs in place in that copy (column lines);
+//   4. the x transform runs in the src rows and adds the V term and the y
+//      result to each element; the unit is reduce-added into dst.
+// The rounding order (x + V, then + y) differs from the separate passes
+// (x + V into dst, then y), so results agree to FP32 rounding.
+// ---------------------------------------------------------------------------
+template <int N, bool BATCH>
+struct FXy {
+    static constexpr int E = 16, TT = N / E, P = N / 2, K = fxy_planes(N);
+    static constexpr int THREADS = P * TT * K;  // also (K N / 2) line pairs x TT
+    static constexpr int UNIT = K * N * N;
+    static constexpr int S = tmared_stages<UNIT, 2, kRedBlocks>();
+    static constexpr size_t SMEM = (size_t)S * (2 * UNIT + (BATCH ? 2 * N : 0)) * sizeof(float) +
+                                   N * sizeof(float2) + (BATCH ? 0 : 2 * N * sizeof(float)) +
+                                   S * sizeof(uint64_t) + 1024;
+    static_assert(THREADS == K * N / 2 * TT, "the x and y mappings use the same threads");
+};
+
+template <int N, bool BATCH>
+__global__ void __launch_bounds__(FXy<N, BATCH>::THREADS, kRedBlocks)
+fxy_tmared_kernel(const __grid_constant__ CUtensorMap msrc, const __grid_constant__ CUtensorMap mV,
+                  const __grid_constant__ CUtensorMap mdst, const TmaPassArgs a, const TmaBatchArgs ba)
+{
+    using G = FXy<N, BATCH>;
+    constexpr int E = G::E, TT = G::TT, P = G::P, K = G::K, UNIT = G::UNIT, S = G::S;
+    constexpr uint32_t kUnitBytes = UNIT * sizeof(float);
+    extern __shared__ unsigned char smem_raw[];
+    const uint32_t pad = (1024u - (smem_u32(smem_raw) & 1023u)) & 1023u;
+    float *s_src = reinterpret_cast<float *>(smem_raw + pad);
+    float *s_vt = s_src + S * UNIT;
+    float *s_mult = s_vt + S * UNIT;  // batched: [S][x row, y row]; single: x row, y row
+    float2 *s_tw = reinterpret_cast<float2 *>(s_mult + (BATCH ? S * 2 * N : 2 * N));
+    uint64_t *full = reinterpret_cast<uint64_t *>(s_tw + N);
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) mbar_init(&full[s], 1);
+        mbar_fence_init();
+    }
+    for (int i = tid; i < N; i += G::THREADS) {
+        s_tw[i] = BATCH ? ba.tw[i] : a.tw[i];
+        if (!BATCH) {
+            s_mult[i] = a.mult[i];
+            s_mult[N + i] = a.mult_y[i];
+        }
+    }
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    __syncthreads();
+    // x mapping: thread tx of line pair lx; y mapping: column pair p, thread ty, plane kk
+    const int tx = tid % TT, lx = tid / TT;
+    const int p = tid % P, ty = (tid / P) % TT, kk = tid / (P * TT);
+    float mrow[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) mrow[e] = BATCH ? 0.f : s_mult[tx + e * TT];
+    const int fsrc = BATCH ? (ba.src >= 0 ? ba.src : 1 - ba.dst) : 0;
+
+    const int units = BATCH ? ba.tiles : a.n_tiles;
+    const int total = BATCH ? ba.members * ba.tiles : a.n_tiles;
+    const int nk = (int)blockIdx.x < total ? (total - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    auto at = [&](int k, int &i, int &z0) {
+        const int g = (int)blockIdx.x + k * (int)gridDim.x;
+        i = g / units;
+        z0 = (g - i * units) * K;
+    };
+    auto issue = [&](int k) {
+        const int s = k % S;
+        int i, z0;
+        at(k, i, z0);
+        if constexpr (BATCH) {
+            const TmaMember *mm = ba.mem + i;
+            mbar_arrive_expect_tx(&full[s], 2 * kUnitBytes + 2 * N * sizeof(float));
+            tma_load_4d(s_src + s * UNIT, &mm->f[fsrc], 0, 0, 0, z0, &full[s]);
+            tma_load_4d(s_vt + s * UNIT, &mm->f[3], 0, 0, 0, z0, &full[s]);
+            bulk_load(s_mult + s * 2 * N, ba.pa[i].mult, N * sizeof(float), &full[s]);
+            bulk_load(s_mult + s * 2 * N + N, ba.pa_y[i].mult, N * sizeof(float), &full[s]);
+        } else {
+            mbar_arrive_expect_tx(&full[s], 2 * kUnitBytes);
+            // failure-path test hook, as in the x pass: the launch's first unit may be left unloaded
+            if (k == 0 && blockIdx.x == 0 && a.inject && atomicExch(a.inject, 0) != 0) return;
+            tma_load_4d(s_src + s * UNIT, &msrc, 0, 0, 0, z0, &full[s]);
+            tma_load_4d(s_vt + s * UNIT, &mV, 0, 0, 0, z0, &full[s]);
+        }
+    };
+    if (tid == 0)
+        for (int k = 0; k < S - 1 && k < nk; ++k) issue(k);
+
+    for (int k = 0; k < nk; ++k) {
+        const int s = k % S;
+        int i, z0;
+        at(k, i, z0);
+        if (!red_stage_wait(&full[s], (uint32_t)((k / S) & 1))) {
+            if (tid == 0) red_timeout_exit<S>(full, k, nk, BATCH ? ba.mem[i].status : a.status);
+            return;
+        }
+        float *src = s_src + s * UNIT;
+        float *vt = s_vt + s * UNIT;
+        const float *multy = BATCH ? s_mult + s * 2 * N + N : s_mult + N;
+        // 1. x elements and the V term into registers
+        XTile<N, E> x;
+        x.load(src, vt, BATCH ? ba.pa[i].bV : a.bV, true, tx, lx);
+        __syncthreads();
+        // 2. the src unit into the V tile
+        {
+            const float4 *from = reinterpret_cast<const float4 *>(src);
+            float4 *to = reinterpret_cast<float4 *>(vt);
+            for (int q = tid; q < UNIT / 4; q += G::THREADS) to[q] = from[q];
+        }
+        __syncthreads();
+        // 3. y lines in place in the copy: [K][N][P] complex pairs
+        sred_tile<N, E>(reinterpret_cast<float2 *>(vt) + kk * N * P + p, P, multy, s_tw, ty);
+        __syncthreads();
+        // 4. x lines, plus the V term and the y result of each element
+        if constexpr (BATCH) {
+            float mr[E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) mr[e] = s_mult[s * 2 * N + tx + e * TT];
+            x.finish(src, mr, s_tw, vt);
+        } else {
+            x.finish(src, mrow, s_tw, vt);
+        }
+        fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+            tma_reduce_add_4d(BATCH ? &ba.mem[i].f[ba.dst] : &mdst, 0, 0, 0, z0, src);
+            bulk_commit();
+            if (k + S - 1 < nk) {
+                bulk_wait_read<1>();
+                issue(k + S - 1);
             }
         }
     }

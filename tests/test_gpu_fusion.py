@@ -1,8 +1,11 @@
-"""The fused x-y pass (3D FP32 grids with nx = ny in {64, 128, 256}): the same
-half-stages as the separate passes to FP32 rounding, the oracle to the FP32
-tolerance, deterministic across chunkings and graph replays (its counters
-reset themselves between launches), and a bounded wait that runs out reports
-SPSTD_ETIMEOUT and leaves the context usable."""
+"""The fused x-y passes.  The stored-tile form (3D FP32 grids with nx = ny in
+{64, 128, 256}): the same half-stages as the separate passes to FP32 rounding,
+the oracle to the FP32 tolerance, deterministic across chunkings and graph
+replays (its counters reset themselves between launches), and a bounded wait
+that runs out reports SPSTD_ETIMEOUT and leaves the context usable.  The
+reduce-add form (nx = ny in {32, 64}, on by default): the oracle to the FP32
+tolerance, the plain passes to FP32 rounding, one launch fewer per
+half-stage, partial plane units."""
 import numpy as np
 import pytest
 
@@ -43,8 +46,10 @@ def test_fused_matches_separate_and_oracle(n):
         assert np.max(np.abs(z - oz[0])) <= 1e-4 * np.max(np.abs(oz))
     (R1, I1, _), (R0, I0, _) = out[True], out[False]
     assert rel_l2(R1, I1, R0, I0) <= 2e-6
-    # one launch fewer per half-stage: 6 steps of SUZUKI6 with fused boundaries apply 6 * 10 + 1
-    assert out[(False, "launches")] - out[(True, "launches")] == 6 * 10 + 1
+    # one launch fewer per half-stage: 6 steps of SUZUKI6 with fused boundaries apply 6 * 10 + 1;
+    # without the stored-tile form, 64-point x-y planes still run the reduce-add fused pass
+    fewer = 0 if n[0] == 64 else 6 * 10 + 1
+    assert out[(False, "launches")] - out[(True, "launches")] == fewer
 
 
 def test_fused_deterministic_over_chunks_and_replays():
@@ -139,3 +144,25 @@ def test_default_pass_wait_timeout_is_reported_and_recoverable():
     s.close()
     oR, oI, _ = oracle_run(p)
     assert rel_l2(R, Im, oR, oI) <= 1e-4
+
+
+@pytest.mark.parametrize("n", [(64, 64, 64), (32, 32, 32), (32, 32, 18), (64, 64), (32, 32, 2), (64, 64, 3)])
+def test_reduce_fused_xy_matches_oracle_and_plain(n):
+    p = stable(inputs.gaussian_problem(n, steps=5, noise=1e-2))
+    runs = {}
+    for plain in (False, True):
+        s = gpu_solver(p, 32, cap=8)
+        if plain:  # plain passes on x and y: no fused pass
+            s.spstd_set_schedule(0, 4)
+            s.spstd_set_schedule(1, 4)
+        s.spstd_step(p.steps)
+        runs[plain] = (*s.spstd_get_state(), s.spstd_probe(0), s.spstd_launch_count(p.steps))
+        s.close()
+    oR, oI, oz = oracle_run(p)
+    R, Im, z, launches = runs[False]
+    assert rel_l2(R, Im, oR, oI) <= 1e-4
+    assert np.max(np.abs(z - oz[0])) <= 1e-4 * np.max(np.abs(oz))
+    R0, I0, _, launches0 = runs[True]
+    assert rel_l2(R, Im, R0, I0) <= 2e-6
+    # FR4 (7 half-stages) with fused step boundaries applies 5 * 6 + 1 half-stages
+    assert launches0 - launches == 5 * 6 + 1
