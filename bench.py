@@ -130,9 +130,9 @@ def measured_peaks():
 # 256^3 FP32 kernels from one ncu capture (profiles/traffic_aniso_ho_3d_256.md),
 # valid while the kernel sources hash to the recorded value.
 MEASURED_TRAFFIC = {
-    "source_hash": "f28f28bf2ea6692e",
-    "aniso_ho_3d_256": {"x_pass": 201.365504e6 + 27.849728e6, "y_pass": 134.246144e6 + 5.466880e6,
-                        "z_pass": 134.246656e6 + 5.416960e6},
+    "source_hash": "36e38ef0b733cd81",
+    "aniso_ho_3d_256": {"x_pass": 201.364480e6 + 27.963392e6, "y_pass": 134.258944e6 + 4.532480e6,
+                        "z_pass": 134.247168e6 + 5.802752e6},
 }
 TRAFFIC_SOURCES = ["paper_1805_03155_gb300/csrc/pass_tmared.cuh", "paper_1805_03155_gb300/csrc/fft_line.cuh",
                    "paper_1805_03155_gb300/csrc/tma.cuh", "paper_1805_03155_gb300/csrc/pass_tma_launch.h"]
