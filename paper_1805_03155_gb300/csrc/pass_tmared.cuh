@@ -251,14 +251,16 @@ __device__ __forceinline__ void xred_tile(float *src, const float *vt, const flo
 // One line of a strided tile (its first element at `line`, consecutive
 // elements rs complex slots apart), thread t.  Computes a L_d src and leaves
 // it in the tile.  Contains block barriers (the column exchange spans the
-// block).
+// block).  The line's values may come from another buffer of the same layout
+// (`in`); `line` then serves only as exchange space and result.
 template <int N, int E>
-__device__ __forceinline__ void sred_tile(float2 *line, int rs, const float *mult, const float2 *tw, int t)
+__device__ __forceinline__ void sred_tile(const float2 *in, float2 *line, int rs, const float *mult, const float2 *tw,
+                                          int t)
 {
     constexpr int TT = N / E;
     float2 v[E];
 #pragma unroll
-    for (int e = 0; e < E; ++e) v[e] = line[(t + e * TT) * rs];
+    for (int e = 0; e < E; ++e) v[e] = in[(t + e * TT) * rs];
     __syncthreads();
     XcColP xc{line, rs};
     fft_line<float, N, E, false>(v, t, xc, tw);
@@ -480,7 +482,7 @@ spass_tmared_kernel(const __grid_constant__ CUtensorMap msrc, const __grid_const
             return;
         }
         float2 *src = reinterpret_cast<float2 *>(m.src + s * TILE);
-        sred_tile<N, E>(src + line0, rs, BATCH ? m.mult + s * N : m.mult, m.tw, t);
+        sred_tile<N, E>(src + line0, src + line0, rs, BATCH ? m.mult + s * N : m.mult, m.tw, t);
         fence_proxy_async();
         __syncthreads();
         if (tid == 0) {
@@ -504,9 +506,9 @@ spass_tmared_kernel(const __grid_constant__ CUtensorMap msrc, const __grid_const
 // of 28).  128 threads, two blocks per SM, the same 3-stage ring as the x
 // pass.  Per unit:
 //   1. the x threads load their row-pair elements and the V term (registers);
-//   2. the src unit is copied into the V tile (V is no longer needed);
-//   3. the y transform runs in place in that copy (column lines);
-//   4. the x transform runs in the src rows and adds the V term and the y
+//   2. the y threads read their column lines from src and transform them
+//      with the V tile (no longer needed) as exchange space and result;
+//   3. the x transform runs in the src rows and adds the V term and the y
 //      result to each element; the unit is reduce-added into dst.
 // The rounding order (x + V, then + y) differs from the separate passes
 // (x + V into dst, then y), so results agree to FP32 rounding.
@@ -606,15 +608,13 @@ fxy_tmared_kernel(const __grid_constant__ CUtensorMap msrc, const __grid_constan
         XTile<N, E> x;
         x.load(src, vt, BATCH ? ba.pa[i].bV : a.bV, true, tx, lx);
         __syncthreads();
-        // 2. the src unit into the V tile
+        // 2.-3. y lines ([K][N][P] complex pairs) read from src, transformed
+        // with the V tile (no longer needed) as exchange space and result
         {
-            const float4 *from = reinterpret_cast<const float4 *>(src);
-            float4 *to = reinterpret_cast<float4 *>(vt);
-            for (int q = tid; q < UNIT / 4; q += G::THREADS) to[q] = from[q];
+            const int l0 = kk * N * P + p;
+            sred_tile<N, E>(reinterpret_cast<const float2 *>(src) + l0, reinterpret_cast<float2 *>(vt) + l0, P, multy,
+                            s_tw, ty);
         }
-        __syncthreads();
-        // 3. y lines in place in the copy: [K][N][P] complex pairs
-        sred_tile<N, E>(reinterpret_cast<float2 *>(vt) + kk * N * P + p, P, multy, s_tw, ty);
         __syncthreads();
         // 4. x lines, plus the V term and the y result of each element
         if constexpr (BATCH) {
