@@ -130,9 +130,9 @@ def measured_peaks():
 # 256^3 FP32 kernels from one ncu capture (profiles/traffic_aniso_ho_3d_256.md),
 # valid while the kernel sources hash to the recorded value.
 MEASURED_TRAFFIC = {
-    "source_hash": "36e38ef0b733cd81",
-    "aniso_ho_3d_256": {"x_pass": 201.364480e6 + 27.963392e6, "y_pass": 134.258944e6 + 4.532480e6,
-                        "z_pass": 134.247168e6 + 5.802752e6},
+    "source_hash": "0e8f1bf293f472e4",
+    "aniso_ho_3d_256": {"x_pass": 201.365760e6 + 28.018432e6, "y_pass": 134.245120e6 + 5.772544e6,
+                        "z_pass": 134.245888e6 + 5.436672e6},
 }
 TRAFFIC_SOURCES = ["paper_1805_03155_gb300/csrc/pass_tmared.cuh", "paper_1805_03155_gb300/csrc/fft_line.cuh",
                    "paper_1805_03155_gb300/csrc/tma.cuh", "paper_1805_03155_gb300/csrc/pass_tma_launch.h"]
