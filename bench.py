@@ -16,6 +16,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -160,6 +161,28 @@ def algorithmic_bytes(kind, n_total, es):
     reads src, V, dst and writes dst; a strided pass reads src, dst and writes
     dst."""
     return (4 if kind in ("x_pass", "xy_pass") else 3) * es * n_total
+
+
+L2_BYTES = 129 * 2 ** 20
+SMS, FP32_LANES, FP64_NOMINAL_TFLOPS, SM_MAX_MHZ = 152, 128, 1.25, 2070.0
+
+
+def algorithmic_flops(kind, n, n_total):
+    """Nominal flops of one launch: 5 log2 N_d + 5 per grid point for each axis
+    d it transforms (forward and inverse FFT of paired real lines, the k^2
+    multiply and the axpy)."""
+    axes = {"x_pass": (0,), "y_pass": (1,), "z_pass": (2,), "xy_pass": (0, 1)}[kind]
+    return sum(5 * math.log2(n[a]) + 5 for a in axes) * n_total
+
+
+def alu_peak_tflops(prec, sm_mhz):
+    """Peak of the non-tensor pipes at the sampled SM clock: FP32 = 152 SMs x
+    128 FMA lanes x 2 flops x clock; FP64 = the part's nominal 1.25 TFLOP/s
+    scaled from its 2070 MHz maximum clock."""
+    mhz = sm_mhz or SM_MAX_MHZ
+    if prec == 32:
+        return SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12
+    return FP64_NOMINAL_TFLOPS * mhz / SM_MAX_MHZ
 
 
 def cpu_baseline(problem, budget_s=20.0):
@@ -531,6 +554,40 @@ def main():
     s.close()
 
     if rank == 0:
+        roofline = {
+            "bound": "hbm",
+            "kernel": dom,
+            "achieved": achieved,
+            "peak": peak,
+            "unit": "GB/s",
+            "frac": achieved / peak,
+            "peak_source": f"{peak_src} hbm_gbs (burst copy)",
+            "traffic": measured_traffic(args.workload, dom, schedules[KIND_AXIS[dom]] if dom in KIND_AXIS else 0),
+            "algorithmic_bytes_per_launch": abytes,
+            "avg_launch_ms": dom_ms,
+            "step_algorithmic_bytes": step_bytes,
+            "step_floor_bytes": 4 * es * N * coeff_halfstages,
+            "step_floor_frac": (4 * es * N * coeff_halfstages) / (ms / args.steps * 1e-3) / 1e9 / peak,
+            "per_kernel_ms": {k: v[0] / v[1] for k, v in kinds.items()},
+            "per_kernel_share": {k: v[0] / sum(x[0] for x in kinds.values()) for k, v in kinds.items()},
+        }
+        if 3 * N * es <= L2_BYTES:
+            # the three fields stay in L2 between passes: HBM does not bound the
+            # kernels, the FFT arithmetic and shared-memory exchanges do
+            aflops = algorithmic_flops(dom, problem.n, N)
+            alu_peak = alu_peak_tflops(prec, clk.get("sm_mhz"))
+            roofline.update({
+                "bound": "alu",
+                "achieved": aflops / (dom_ms * 1e-3) / 1e12,
+                "peak": alu_peak,
+                "unit": "TFLOP/s",
+                "frac": aflops / (dom_ms * 1e-3) / 1e12 / alu_peak,
+                "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 flops x median SM clock" if prec == 32 else
+                                "derived: nominal 1.25 TFLOP/s FP64 x median SM clock / 2070 MHz"),
+                "traffic": None,
+                "algorithmic_flops_per_launch": aflops,
+                "hbm_frac_for_context": achieved / peak,
+            })
         out = {
             "metric": "grid-point-steps/s",
             "value": value,
@@ -568,24 +625,7 @@ def main():
             },
             "clocks": clk,
             "gpu_launches": int(launches),
-            "roofline": {
-                "bound": "hbm",
-                "kernel": dom,
-                "achieved": achieved,
-                "peak": peak,
-                "unit": "GB/s",
-                "frac": achieved / peak,
-                "peak_source": f"{peak_src} hbm_gbs (burst copy)",
-                "traffic": measured_traffic(args.workload, dom,
-                                            schedules[KIND_AXIS[dom]] if dom in KIND_AXIS else 0),
-                "algorithmic_bytes_per_launch": abytes,
-                "avg_launch_ms": dom_ms,
-                "step_algorithmic_bytes": step_bytes,
-                "step_floor_bytes": 4 * es * N * coeff_halfstages,
-                "step_floor_frac": (4 * es * N * coeff_halfstages) / (ms / args.steps * 1e-3) / 1e9 / peak,
-                "per_kernel_ms": {k: v[0] / v[1] for k, v in kinds.items()},
-                "per_kernel_share": {k: v[0] / sum(x[0] for x in kinds.values()) for k, v in kinds.items()},
-            },
+            "roofline": roofline,
             "e2e": {
                 "value": N * args.steps * ws / t_e2e,
                 "unit": "grid-point-steps/s",

@@ -320,6 +320,12 @@ __device__ __forceinline__ void load_tile(void *smem, const CUtensorMap *map, co
     tma_load_4d(smem, map, c.c[0], c.c[1], c.c[2], c.c[3], bar);
 }
 
+// V tiles: read once per pass, so loaded with the evict-first L2 policy.
+__device__ __forceinline__ void load_v_tile(void *smem, const CUtensorMap *map, const TileAt &c, uint64_t *bar)
+{
+    tma_load_4d_hint(smem, map, c.c[0], c.c[1], c.c[2], c.c[3], bar, l2_evict_first_policy());
+}
+
 __device__ __forceinline__ void reduce_tile(const CUtensorMap *map, const TileAt &c, const void *smem)
 {
     tma_reduce_add_4d(map, c.c[0], c.c[1], c.c[2], c.c[3], smem);
@@ -371,7 +377,7 @@ xpass_tmared_kernel(const __grid_constant__ CUtensorMap msrc, const __grid_const
             const TmaMember *mm = ba.mem + c.i;
             mbar_arrive_expect_tx(&m.full[s], 2 * kTileBytes + N * sizeof(float));
             load_tile(m.src + s * TILE, &mm->x[fsrc], c, &m.full[s]);
-            load_tile(m.vt + s * TILE, &mm->x[3], c, &m.full[s]);
+            load_v_tile(m.vt + s * TILE, &mm->x[3], c, &m.full[s]);
             bulk_load(m.mult + s * N, ba.pa[c.i].mult, N * sizeof(float), &m.full[s]);
         } else {
             mbar_arrive_expect_tx(&m.full[s], (useV ? 2 : 1) * kTileBytes);
@@ -379,7 +385,7 @@ xpass_tmared_kernel(const __grid_constant__ CUtensorMap msrc, const __grid_const
             // (its barrier then never completes and the wait on it times out)
             if (k == 0 && blockIdx.x == 0 && a.inject && atomicExch(a.inject, 0) != 0) return;
             load_tile(m.src + s * TILE, &msrc, c, &m.full[s]);
-            if (useV) load_tile(m.vt + s * TILE, &mV, c, &m.full[s]);
+            if (useV) load_v_tile(m.vt + s * TILE, &mV, c, &m.full[s]);
         }
     };
     if (tid == 0)
@@ -579,7 +585,7 @@ fxy_tmared_kernel(const __grid_constant__ CUtensorMap msrc, const __grid_constan
             const TmaMember *mm = ba.mem + i;
             mbar_arrive_expect_tx(&full[s], 2 * kUnitBytes + 2 * N * sizeof(float));
             tma_load_4d(s_src + s * UNIT, &mm->f[fsrc], 0, 0, 0, z0, &full[s]);
-            tma_load_4d(s_vt + s * UNIT, &mm->f[3], 0, 0, 0, z0, &full[s]);
+            tma_load_4d_hint(s_vt + s * UNIT, &mm->f[3], 0, 0, 0, z0, &full[s], l2_evict_first_policy());
             bulk_load(s_mult + s * 2 * N, ba.pa[i].mult, N * sizeof(float), &full[s]);
             bulk_load(s_mult + s * 2 * N + N, ba.pa_y[i].mult, N * sizeof(float), &full[s]);
         } else {
@@ -587,7 +593,7 @@ fxy_tmared_kernel(const __grid_constant__ CUtensorMap msrc, const __grid_constan
             // failure-path test hook, as in the x pass: the launch's first unit may be left unloaded
             if (k == 0 && blockIdx.x == 0 && a.inject && atomicExch(a.inject, 0) != 0) return;
             tma_load_4d(s_src + s * UNIT, &msrc, 0, 0, 0, z0, &full[s]);
-            tma_load_4d(s_vt + s * UNIT, &mV, 0, 0, 0, z0, &full[s]);
+            tma_load_4d_hint(s_vt + s * UNIT, &mV, 0, 0, 0, z0, &full[s], l2_evict_first_policy());
         }
     };
     if (tid == 0)

@@ -106,6 +106,28 @@ __device__ __forceinline__ void tma_load_4d(void *smem_dst, const CUtensorMap *m
         : "memory");
 }
 
+// L2 policy for data that a pass reads once (the potential V): its lines are
+// the first candidates for replacement, so streaming V through L2 displaces
+// less of the two fields, which every pass re-reads.
+__device__ __forceinline__ uint64_t l2_evict_first_policy()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+// tma_load_4d with an L2 cache policy (from createpolicy).
+__device__ __forceinline__ void tma_load_4d_hint(void *smem_dst, const CUtensorMap *map, int c0, int c1, int c2,
+                                                 int c3, uint64_t *bar, uint64_t policy)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6], %7;"
+        ::"r"(smem_u32(smem_dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3),
+        "r"(smem_u32(bar)), "l"(policy)
+        : "memory");
+}
+
 // Shared -> global element-wise f32 add of a tile (4D tensor map) into the
 // current bulk group: global[i] += smem[i], performed at L2, so the SM never
 // loads the destination.  Box elements outside the tensor are not touched.
