@@ -156,10 +156,13 @@ def measured_traffic(workload, kernel, schedule=0):
 KIND_AXIS = {"x_pass": 0, "y_pass": 1, "z_pass": 2, "xy_pass": 0}
 
 
-def algorithmic_bytes(kind, n_total, es):
+def algorithmic_bytes(kind, n_total, es, v_separable=False):
     """Compulsory bytes of one launch: the x pass (and the fused x-y pass)
     reads src, V, dst and writes dst; a strided pass reads src, dst and writes
-    dst."""
+    dst.  With a separable potential the x pass rebuilds V from two tables of
+    n_x and n_y n_z values, so its V field read drops out."""
+    if kind == "x_pass" and v_separable:
+        return 3 * es * n_total
     return (4 if kind in ("x_pass", "xy_pass") else 3) * es * n_total
 
 
@@ -457,6 +460,7 @@ def main():
     tune_ms = s.spstd_tune(reps=10) if not args.no_tune else np.full((3, spstd.SCHEDULES), -1.0)
     schedules = [s.spstd_get_schedule(a) for a in range(problem.dims)]
     xy_fused = s.spstd_get_xy_fusion()
+    v_sep = s.spstd_potential_separable()
 
     # warm-up (also captures the step graph)
     s.spstd_step(args.warmup)
@@ -490,9 +494,9 @@ def main():
     dom = max(kinds, key=lambda k: kinds[k][0])
     dom_ms = kinds[dom][0] / kinds[dom][1]
     peak, peak_src = measured_peaks()
-    abytes = algorithmic_bytes(dom, N, es)
+    abytes = algorithmic_bytes(dom, N, es, v_sep)
     achieved = abytes / (dom_ms * 1e-3) / 1e9
-    step_bytes = sum(algorithmic_bytes(k, N, es) * kinds[k][1] for k in ("x_pass", "y_pass", "z_pass", "xy_pass")
+    step_bytes = sum(algorithmic_bytes(k, N, es, v_sep) * kinds[k][1] for k in ("x_pass", "y_pass", "z_pass", "xy_pass")
                      if k in kinds) / prof_steps
     half_stages = (kinds.get("x_pass", (0, 0))[1] + kinds.get("xy_pass", (0, 0))[1]) / prof_steps
 
@@ -566,8 +570,10 @@ def main():
             "algorithmic_bytes_per_launch": abytes,
             "avg_launch_ms": dom_ms,
             "step_algorithmic_bytes": step_bytes,
-            "step_floor_bytes": 4 * es * N * coeff_halfstages,
-            "step_floor_frac": (4 * es * N * coeff_halfstages) / (ms / args.steps * 1e-3) / 1e9 / peak,
+            # per half-stage: src, V, dst read and dst written (V from tables: 3 arrays)
+            "step_floor_bytes": (3 if v_sep else 4) * es * N * coeff_halfstages,
+            "step_floor_frac": ((3 if v_sep else 4) * es * N * coeff_halfstages) / (ms / args.steps * 1e-3) / 1e9
+                               / peak,
             "per_kernel_ms": {k: v[0] / v[1] for k, v in kinds.items()},
             "per_kernel_share": {k: v[0] / sum(x[0] for x in kinds.values()) for k, v in kinds.items()},
         }
@@ -621,6 +627,7 @@ def main():
                 "parallelism": f"replicas{ws}",
                 "schedules": schedules,
                 "xy_fused": xy_fused,
+                "v_separable": v_sep,
                 "schedule_ms": [[round(float(t), 5) for t in row] for row in tune_ms[: problem.dims]],
             },
             "clocks": clk,

@@ -43,7 +43,7 @@ struct HalfStage {
 };
 
 struct Layout {
-    size_t psi[2], V, tmp, staging, ring, counter, status, snap, partial, dout, tw[3], mult, dense[3], spec;
+    size_t psi[2], V, vsep_x, vsep_yz, tmp, staging, ring, counter, status, snap, partial, dout, tw[3], mult, dense[3], spec;
     size_t eig_acc, eig_theta, eig_step, rk[6], lscr, xy, total;
 };
 
@@ -292,6 +292,8 @@ int64_t effective_max_nfft(const spstd_config &cfg)
     return std::max<int64_t>(4, next_pow2(4 * cfg.probe_capacity));
 }
 
+int64_t vsep_rows_padded(int64_t rows) { return (rows + 127) / 128 * 128; }
+
 Layout make_layout(const spstd_config &cfg, int m)
 {
     Layout L{};
@@ -306,6 +308,11 @@ Layout make_layout(const spstd_config &cfg, int m)
     L.psi[0] = take(es * ntot);
     L.psi[1] = take(es * ntot);
     L.V = take(es * ntot);
+    // separable-potential tables of the FP32 x pass: vx, then vyz padded with
+    // zeros to whole x tiles (at most 128 rows each)
+    const bool sep = cfg.precision == 32 && cfg.dims >= 2;
+    L.vsep_x = take(sep ? 4 * (size_t)cfg.n[0] : 0);
+    L.vsep_yz = take(sep ? 4 * (size_t)vsep_rows_padded(cfg.n[1] * cfg.n[2]) : 0);
     L.tmp = take(es * ntot);
     L.staging = take(cfg.precision == 32 ? 8 * ntot : 0);
     L.ring = take(16 * (size_t)std::max(cfg.n_probe, 1) * cfg.probe_capacity);
@@ -379,6 +386,9 @@ struct spstd_ctx {
     // (psi_R, psi_I, tmp, V in the unit view)
     bool fxy_ok = false, fxy_on = false;
     CUtensorMap fxmap[4];
+    // the potential is separable, V = vx(x) + vyz(y, z): the reduce-add x pass
+    // rebuilds the V term from the tables at L.vsep_x / L.vsep_yz
+    bool vsep = false;
     // step-boundary merge of the last and first half-stages (same field)
     bool merge = false;
     HalfStage merged{};
@@ -903,6 +913,10 @@ cudaError_t enqueue_apply(spstd_ctx *ctx, int fsrc, int fdst, int table, double 
                 ta.nx = (int)n0;
                 ta.planes = red_planes(cfg.n, ax);
                 ta.inject = status + 1;
+                if (ax == 0 && red && ta.use_V && ctx->vsep) {
+                    ta.vx = (const float *)ctx->ptr(ctx->L.vsep_x);
+                    ta.vyz = (const float *)ctx->ptr(ctx->L.vsep_yz);
+                }
                 if (red) {
                     ta.n_tiles = tmared_tiles(ax, cfg.n, &ta.n_xt);
                     if (ax == 0)
@@ -1424,6 +1438,34 @@ spstd_status spstd_destroy(spstd_ctx *ctx)
 }  // extern "C"
 
 namespace {
+// Tables of a separable potential V(x_i, row r) = vx[i] + vyz[r] (r = the
+// flattened (y, z) index), when the FP32 sum of the two reproduces every
+// value of V to 4 units in the last place.  The reference point of the split
+// is the smallest |V|: for a potential of one sign (a harmonic well) both
+// tables then keep that sign and the sum does not cancel.  vyz is padded with
+// zeros to `padded` rows.
+bool separable_tables(const double *V, int64_t n0, int64_t rows, int64_t padded, std::vector<float> &vx,
+                      std::vector<float> &vyz)
+{
+    int64_t ref = 0;
+    for (int64_t p = 1; p < n0 * rows; ++p)
+        if (std::fabs(V[p]) < std::fabs(V[ref])) ref = p;
+    const int64_t i0 = ref % n0, r0 = ref / n0;
+    vx.assign(n0, 0.f);
+    vyz.assign(padded, 0.f);
+    for (int64_t i = 0; i < n0; ++i) vx[i] = (float)(V[r0 * n0 + i] - V[ref]);
+    for (int64_t r = 0; r < rows; ++r) vyz[r] = (float)V[r * n0 + i0];
+    for (int64_t r = 0; r < rows; ++r) {
+        const float b = vyz[r];
+        const double *row = V + r * n0;
+        for (int64_t i = 0; i < n0; ++i) {
+            const float sum = vx[i] + b;  // IEEE single, rounded to nearest, as on the device
+            if (!(std::fabs((double)sum - row[i]) <= 0x1p-22 * std::fabs(row[i]))) return false;
+        }
+    }
+    return true;
+}
+
 template <typename T>
 spstd_status upload_field(spstd_ctx *ctx, const double *host, size_t off)
 {
@@ -1461,8 +1503,25 @@ spstd_status spstd_set_potential(spstd_ctx *ctx, const double *V)
         if (!std::isfinite(V[i])) return fail(ctx, SPSTD_EINVAL, "V has a non-finite value");
         vmax = std::max(vmax, V[i]);
     }
-    spstd_status s = ctx->cfg.precision == 32 ? upload_field<float>(ctx, V, ctx->L.V)
-                                              : upload_field<double>(ctx, V, ctx->L.V);
+    // kernel arguments name the tables (or not): replayed graphs are rebuilt
+    drop_graph(ctx);
+    ctx->vsep = false;
+    if (ctx->cfg.precision == 32 && ctx->tma[0]) {
+        const int64_t n0 = ctx->cfg.n[0], rows = ctx->cfg.n[1] * ctx->cfg.n[2];
+        std::vector<float> vx, vyz;
+        if (separable_tables(V, n0, rows, vsep_rows_padded(rows), vx, vyz)) {
+            float *dvx = (float *)ctx->ptr(ctx->L.vsep_x), *dvyz = (float *)ctx->ptr(ctx->L.vsep_yz);
+            SPSTD_CU(ctx, cudaMemcpyAsync(dvx, vx.data(), 4 * vx.size(), cudaMemcpyHostToDevice, ctx->stream));
+            SPSTD_CU(ctx, cudaMemcpyAsync(dvyz, vyz.data(), 4 * vyz.size(), cudaMemcpyHostToDevice, ctx->stream));
+            // the V field holds the same FP32 sums, for every other pass
+            SPSTD_CU(ctx, build_separable_v(dvx, dvyz, (float *)ctx->ptr(ctx->L.V), n0, rows, ctx->stream));
+            SPSTD_CU(ctx, cudaStreamSynchronize(ctx->stream));
+            ctx->vsep = true;
+        }
+    }
+    spstd_status s = ctx->vsep ? SPSTD_OK
+                     : ctx->cfg.precision == 32 ? upload_field<float>(ctx, V, ctx->L.V)
+                                                : upload_field<double>(ctx, V, ctx->L.V);
     if (s != SPSTD_OK) return s;
     ctx->vmax = vmax;
     return set_dt(ctx, vmax);
@@ -1734,6 +1793,13 @@ spstd_status spstd_get_dt(const spstd_ctx *ctx, double *dt)
 {
     if (!ctx || !dt) return SPSTD_EINVAL;
     *dt = ctx->dt;
+    return SPSTD_OK;
+}
+
+spstd_status spstd_potential_separable(const spstd_ctx *ctx, int *separable)
+{
+    if (!ctx || !separable) return SPSTD_EINVAL;
+    *separable = ctx->vsep ? 1 : 0;
     return SPSTD_OK;
 }
 

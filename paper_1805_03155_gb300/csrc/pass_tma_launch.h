@@ -24,6 +24,11 @@ struct TmaPassArgs {
     int planes;          // reduce-add strided pass: tmared_planes()
     int *inject;         // reduce-add x pass: when *inject != 0, clears it and leaves the first tile unloaded
     const float *mult_y; // fused x-y pass: the y axis's multipliers (mult: the x axis's)
+    // Reduce-add x pass with a separable potential V(x, y, z) = vx(x) + vyz(y, z):
+    // the V term is rebuilt from these tables (vx: nx floats; vyz: one float per
+    // x line, padded with zeros to a whole number of tiles) instead of read
+    // from the V field.  Null: the V field is used.
+    const float *vx, *vyz;
 };
 
 // Tile geometry the tensor maps must use.
@@ -119,6 +124,11 @@ struct TmaBatchArgs {
 };
 
 cudaError_t launch_pass_tmared_batch(int axis, int N, const TmaBatchArgs &a, cudaStream_t s);
+
+// V[r nx + i] = vx[i] + vyz[r] in FP32 (rounded to nearest), the values the x
+// pass rebuilds from the tables of a separable potential; rows = ny nz.
+cudaError_t build_separable_v(const float *vx, const float *vyz, float *V, int64_t nx, int64_t rows,
+                              cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Fused x + y reduce-add pass (pass_tmared.cuh) for grids with nx = ny = N in

@@ -1,5 +1,6 @@
 // Instantiations and launchers of the reduce-add pipelined passes
 // (pass_tmared.cuh): single grids and batches, lines of 32..512 points.
+#include <algorithm>
 #include <utility>
 
 #include "pass_tmared.cuh"
@@ -32,13 +33,13 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
     return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
-template <int N, bool BATCH, int EX = kRedE>
+template <int N, bool BATCH, bool VSEP = false, int EX = kRedE>
 cudaError_t red_x(const CUtensorMap *ms, const CUtensorMap *mv, const CUtensorMap *md, const TmaPassArgs *a,
                   const TmaBatchArgs *ba, cudaStream_t s)
 {
-    using G = XRed<N, EX, BATCH>;
+    using G = XRed<N, EX, BATCH, VSEP>;
     int grid = 0;
-    cudaError_t e = persistent_grid<xpass_tmared_kernel<N, EX, BATCH>>(G::THREADS, G::SMEM, &grid);
+    cudaError_t e = persistent_grid<xpass_tmared_kernel<N, EX, BATCH, VSEP>>(G::THREADS, G::SMEM, &grid);
     if (e != cudaSuccess || !(BATCH ? (const void *)ba : (const void *)a)) return e;
     const int total = BATCH ? ba->members * ba->tiles : a->n_tiles;
     if (total < grid) grid = total;
@@ -46,7 +47,7 @@ cudaError_t red_x(const CUtensorMap *ms, const CUtensorMap *mv, const CUtensorMa
     const CUtensorMap none{};
     const TmaPassArgs a0{};
     const TmaBatchArgs b0{};
-    return launch_pdl(xpass_tmared_kernel<N, EX, BATCH>, dim3(grid), dim3(G::TT, G::LP), G::SMEM, s,
+    return launch_pdl(xpass_tmared_kernel<N, EX, BATCH, VSEP>, dim3(grid), dim3(G::TT, G::LP), G::SMEM, s,
                       BATCH ? none : *ms, BATCH ? none : *mv, BATCH ? none : *md, BATCH ? a0 : *a, BATCH ? *ba : b0);
 }
 
@@ -102,6 +103,19 @@ cudaError_t red_s_p(int P, int K, const CUtensorMap *ms, const CUtensorMap *md, 
     return cudaErrorInvalidValue;
 }
 
+template <bool BATCH, bool VSEP>
+cudaError_t red_x_n(int N, const CUtensorMap *ms, const CUtensorMap *mv, const CUtensorMap *md, const TmaPassArgs *a,
+                    const TmaBatchArgs *ba, cudaStream_t s)
+{
+    switch (N) {
+    case 32: return red_x<32, BATCH, VSEP>(ms, mv, md, a, ba, s);
+    case 64: return red_x<64, BATCH, VSEP>(ms, mv, md, a, ba, s);
+    case 128: return red_x<128, BATCH, VSEP>(ms, mv, md, a, ba, s);
+    case 256: return red_x<256, BATCH, VSEP>(ms, mv, md, a, ba, s);
+    default: return red_x<512, BATCH, VSEP>(ms, mv, md, a, ba, s);
+    }
+}
+
 template <bool BATCH>
 cudaError_t red_any(int axis, int N, int64_t nx, int K, const CUtensorMap *ms, const CUtensorMap *mv,
                     const CUtensorMap *md, const TmaPassArgs *a, const TmaBatchArgs *ba, cudaStream_t s)
@@ -109,13 +123,18 @@ cudaError_t red_any(int axis, int N, int64_t nx, int K, const CUtensorMap *ms, c
     if (!tmared_eligible(N)) return cudaErrorInvalidValue;
     if (axis == 0) {
         if (nx != N) return cudaErrorInvalidValue;
-        switch (N) {
-        case 32: return red_x<32, BATCH>(ms, mv, md, a, ba, s);
-        case 64: return red_x<64, BATCH>(ms, mv, md, a, ba, s);
-        case 128: return red_x<128, BATCH>(ms, mv, md, a, ba, s);
-        case 256: return red_x<256, BATCH>(ms, mv, md, a, ba, s);
-        default: return red_x<512, BATCH>(ms, mv, md, a, ba, s);
+        if constexpr (!BATCH) {
+            // a single grid with a separable potential takes the table form; the
+            // set-up call (no args) prepares both forms
+            if (!a) {
+                const cudaError_t e = red_x_n<false, true>(N, ms, mv, md, a, ba, s);
+                if (e != cudaSuccess) return e;
+            } else if (a->vyz) {
+                if (!a->vx) return cudaErrorInvalidValue;
+                return red_x_n<false, true>(N, ms, mv, md, a, ba, s);
+            }
         }
+        return red_x_n<BATCH, false>(N, ms, mv, md, a, ba, s);
     }
     const int P = tmared_pairs(N, nx);
     switch (N) {
@@ -156,7 +175,23 @@ cudaError_t fxy_any(int N, const CUtensorMap *ms, const CUtensorMap *mv, const C
     }
 }
 
+__global__ void separable_v_kernel(const float *vx, const float *vyz, float *V, int64_t nx, int64_t n)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x)
+        V[p] = __fadd_rn(vx[p % nx], vyz[p / nx]);
+}
+
 }  // namespace
+
+cudaError_t build_separable_v(const float *vx, const float *vyz, float *V, int64_t nx, int64_t rows,
+                              cudaStream_t s)
+{
+    const int64_t n = nx * rows;
+    if (n <= 0) return cudaSuccess;
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);
+    separable_v_kernel<<<(unsigned)blocks, 256, 0, s>>>(vx, vyz, V, nx, n);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_pass_fxy(int N, const CUtensorMap &msrc, const CUtensorMap &mV, const CUtensorMap &mdst,
                             const TmaPassArgs &a, cudaStream_t s)

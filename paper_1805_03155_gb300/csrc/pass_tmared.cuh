@@ -212,6 +212,26 @@ struct XTile {
         }
     }
 
+    // As load, for a separable potential: the V term of row r at x index i is
+    // vx[i] + vyz_r rounded to FP32 -- the value the V field holds for such a
+    // potential -- so both forms give the same bits.
+    __device__ __forceinline__ void load_sep(const float *src, const float *vx, float vyz0, float vyz1, float bV,
+                                             int t_, int l_)
+    {
+        t = t_;
+        l = l_;
+        g = l & (G - 1);
+        const int r0 = 2 * l, r1 = 2 * l + 1;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int i = pos(e);
+            v[e] = make_float2(src[r0 * N + i], src[r1 * N + i]);
+            const float x = vx[i];
+            w[e] = make_float2(__fmul_rn(__fmul_rn(bV, __fadd_rn(x, vyz0)), v[e].x),
+                               __fmul_rn(__fmul_rn(bV, __fadd_rn(x, vyz1)), v[e].y));
+        }
+    }
+
     __device__ __forceinline__ void finish(float *src, const float (&mr)[E], const float2 *tw, const float *yadd)
     {
         const int r0 = 2 * l, r1 = 2 * l + 1;
@@ -335,30 +355,41 @@ __device__ __forceinline__ void reduce_tile(const CUtensorMap *map, const TileAt
 // x pass.  Single grid (BATCH = false): maps msrc / mV / mdst, a.mult, a.bV.
 // Batched: member i's maps in ba.mem[i], its multipliers and bV in ba.pa[i].
 // ---------------------------------------------------------------------------
-template <int N, int E, bool BATCH>
+template <int N, int E, bool BATCH, bool VSEP = false>
 struct XRed {
+    static_assert(!(BATCH && VSEP), "batches read the V field");
     static constexpr int TT = N / E;
     static constexpr int ROWS = tmared_rows_x(N);
     static constexpr int LP = ROWS / 2;
     static constexpr int THREADS = LP * TT;
     static constexpr int TILE = ROWS * N;
-    static constexpr int S = tmared_stages<TILE, 2, kRedBlocks>();
-    static constexpr size_t SMEM = tmared_smem<N, TILE, 2, S, BATCH>();
+    // stage: src (+ V) tile; with a separable potential, src and the tile's
+    // ROWS values of vyz, so twice as many stages fit
+    static constexpr int PARTS = VSEP ? 1 : 2;
+    static constexpr int BLOCKS = VSEP ? 3 : kRedBlocks;
+    static constexpr int S = tmared_stages<TILE, PARTS, BLOCKS>();
+    static constexpr size_t SEP_SMEM = VSEP ? 16 + (size_t)S * ROWS * sizeof(float) + N * sizeof(float) : 0;
+    static constexpr size_t SMEM = tmared_smem<N, TILE, PARTS, S, BATCH>() + SEP_SMEM;
 };
 
-template <int N, int E, bool BATCH>
-__global__ void __launch_bounds__(XRed<N, E, BATCH>::THREADS, kRedBlocks)
+template <int N, int E, bool BATCH, bool VSEP = false>
+__global__ void __launch_bounds__(XRed<N, E, BATCH, VSEP>::THREADS, XRed<N, E, BATCH, VSEP>::BLOCKS)
 xpass_tmared_kernel(const __grid_constant__ CUtensorMap msrc, const __grid_constant__ CUtensorMap mV,
                     const __grid_constant__ CUtensorMap mdst, const TmaPassArgs a, const TmaBatchArgs ba)
 {
-    using G = XRed<N, E, BATCH>;
+    using G = XRed<N, E, BATCH, VSEP>;
     constexpr int TT = G::TT, ROWS = G::ROWS, TILE = G::TILE, S = G::S;
     constexpr uint32_t kTileBytes = TILE * sizeof(float);
     extern __shared__ unsigned char smem_raw[];
-    const TmaRedSmem m = tmared_carve<N, TILE, 2, S, BATCH>(smem_raw);
+    const TmaRedSmem m = tmared_carve<N, TILE, G::PARTS, S, BATCH>(smem_raw);
     const int t = threadIdx.x, l = threadIdx.y, tid = l * TT + t;
+    // separable potential: [S][ROWS] vyz values (one bulk copy per stage), then vx
+    float *vrow = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(m.full + S) + 15) & ~uintptr_t(15));
+    float *vxt = vrow + S * ROWS;
+    if constexpr (VSEP)
+        for (int i = tid; i < N; i += G::THREADS) vxt[i] = a.vx[i];
     tmared_setup<N, S>(m, BATCH ? ba.tw : a.tw, BATCH ? nullptr : a.mult, tid, G::THREADS);
-    const bool useV = BATCH || a.use_V != 0;
+    const bool useV = BATCH || VSEP || a.use_V != 0;
     const int fsrc = BATCH ? (ba.src >= 0 ? ba.src : 1 - ba.dst) : 0;
     // single grid: one multiplier row for every tile, held in registers
     float mrow[E];
@@ -380,12 +411,15 @@ xpass_tmared_kernel(const __grid_constant__ CUtensorMap msrc, const __grid_const
             load_v_tile(m.vt + s * TILE, &mm->x[3], c, &m.full[s]);
             bulk_load(m.mult + s * N, ba.pa[c.i].mult, N * sizeof(float), &m.full[s]);
         } else {
-            mbar_arrive_expect_tx(&m.full[s], (useV ? 2 : 1) * kTileBytes);
+            mbar_arrive_expect_tx(&m.full[s], VSEP ? kTileBytes + ROWS * sizeof(float) : (useV ? 2 : 1) * kTileBytes);
             // failure-path test hook: the launch's first tile may be left unloaded
             // (its barrier then never completes and the wait on it times out)
             if (k == 0 && blockIdx.x == 0 && a.inject && atomicExch(a.inject, 0) != 0) return;
             load_tile(m.src + s * TILE, &msrc, c, &m.full[s]);
-            if (useV) load_v_tile(m.vt + s * TILE, &mV, c, &m.full[s]);
+            if constexpr (VSEP)
+                bulk_load(vrow + s * ROWS, a.vyz + c.c[2], ROWS * sizeof(float), &m.full[s]);
+            else if (useV)
+                load_v_tile(m.vt + s * TILE, &mV, c, &m.full[s]);
         }
     };
     if (tid == 0)
@@ -405,6 +439,10 @@ xpass_tmared_kernel(const __grid_constant__ CUtensorMap msrc, const __grid_const
 #pragma unroll
             for (int e = 0; e < E; ++e) mr[e] = m.mult[s * N + t + e * TT];
             xred_tile<N, E>(src, m.vt + s * TILE, mr, m.tw, ba.pa[c.i].bV, true, t, l);
+        } else if constexpr (VSEP) {
+            XTile<N, E> x;
+            x.load_sep(src, vxt, vrow[s * ROWS + 2 * l], vrow[s * ROWS + 2 * l + 1], a.bV, t, l);
+            x.finish(src, mrow, m.tw, nullptr);
         } else {
             xred_tile<N, E>(src, m.vt + s * TILE, mrow, m.tw, a.bV, useV, t, l);
         }

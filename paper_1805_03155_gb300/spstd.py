@@ -96,6 +96,7 @@ def lib():
         "spstd_apply_hamiltonian": (C.c_int, [vp, C.c_int, dp]),
         "spstd_get_dt": (C.c_int, [vp, dp]),
         "spstd_steps_taken": (C.c_int, [vp, ip]),
+        "spstd_potential_separable": (C.c_int, [vp, C.POINTER(C.c_int)]),
         "spstd_get_coefficients": (C.c_int, [vp, C.POINTER(C.c_int), dp, dp]),
         "spstd_launch_count": (C.c_int, [vp, C.c_int64, ip]),
         "spstd_profile_steps": (C.c_int, [vp, C.c_int64, dp, ip]),
@@ -273,6 +274,11 @@ class Solver:
         v = C.c_double(0)
         self._check(self.L.spstd_get_dt(self.ctx, C.byref(v)))
         return v.value
+
+    def spstd_potential_separable(self):
+        v = C.c_int(0)
+        self._check(self.L.spstd_potential_separable(self.ctx, C.byref(v)))
+        return bool(v.value)
 
     def spstd_steps_taken(self):
         v = C.c_int64(0)

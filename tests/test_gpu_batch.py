@@ -117,6 +117,9 @@ def test_tma_batch_members_equal_lone_solves_bitwise():
     alone = []
     for p in probs:
         s = gpu_solver(p, 32, cap=steps, merge=False)
+        # harmonic potentials: the lone x pass rebuilds V from separable tables,
+        # the batched one reads the V field, which holds the same FP32 sums
+        assert s.spstd_potential_separable()
         s.spstd_step(steps)
         R, Im = s.spstd_get_state()
         alone.append((R, Im, np.array([s.spstd_probe(q) for q in range(2)])))

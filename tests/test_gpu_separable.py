@@ -1,0 +1,115 @@
+"""Separable potentials (FP32, x axis of 32..512 points): detection, the x pass
+that rebuilds Eq. 16's V term from the tables vx(x) + vyz(y, z) against the
+oracle, the general form for potentials that do not separate, and a context
+whose potential is replaced (the tables must not go stale)."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from paper_1805_03155_gb300 import inputs, spstd
+from helpers import gpu_solver, oracle_run, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def stable(p, frac=0.4):
+    cfg = spstd.make_config(p.dims, p.n[: p.dims], p.lo[: p.dims], p.hi[: p.dims], integrator=p.integrator)
+    _, dt_max = spstd.stability_limit(cfg, float(np.max(p.V)))
+    return dataclasses.replace(p, dt=frac * dt_max)
+
+
+def coupled(p, eps=0.05):
+    """The problem's potential plus eps x y: not a sum of an x part and a (y, z) part."""
+    xs = p.coords()
+    Z, Y, X = np.meshgrid(xs[2], xs[1], xs[0], indexing="ij")
+    return dataclasses.replace(p, V=p.V + eps * (X * Y).ravel())
+
+
+def separable(p, precision=32):
+    s = gpu_solver(p, precision, cap=1)
+    f = s.spstd_potential_separable()
+    s.close()
+    return f
+
+
+def test_detection():
+    ho3 = stable(inputs.gaussian_problem((64, 32, 16), omega=[1.0, 1.3, 1.7], steps=1))
+    assert separable(ho3)
+    assert not separable(ho3, 64)                     # FP64 fields read the V field
+    assert separable(stable(inputs.gaussian_problem((128, 64), steps=1)))
+    assert separable(stable(inputs.gaussian_problem((512, 32), omega=[0.0, 0.0], steps=1)))   # V = 0
+    assert not separable(stable(coupled(ho3)))
+    assert not separable(stable(inputs.gaussian_problem((64, 32, 16), well=(5.0, 1.5), steps=1)))
+    assert not separable(stable(inputs.gaussian_problem((16, 64, 32), steps=1)))   # no pipelined x pass
+
+
+@pytest.mark.parametrize("n", [(64, 32, 16), (256, 64), (512, 32), (32, 64, 8), (128, 16, 4)])
+def test_separable_matches_oracle(n):
+    p = stable(inputs.gaussian_problem(n, omega=[1.0, 1.3, 1.7][: len(n)], steps=12, noise=1e-2))
+    s = gpu_solver(p, 32, cap=p.steps, merge=False)
+    assert s.spstd_potential_separable()
+    s.spstd_step(p.steps)
+    R, Im = s.spstd_get_state()
+    nv, ev = s.spstd_energy_norm()
+    s.close()
+    oR, oI, _ = oracle_run(p)
+    assert rel_l2(R, Im, oR, oI) <= 1e-4
+
+
+@pytest.mark.parametrize("n,kind", [((64, 32, 16), "well"), ((64, 32, 16), "coupled"), ((128, 64), "coupled"),
+                                    ((256, 16, 8), "well")])
+def test_nonseparable_matches_oracle(n, kind):
+    if kind == "well":
+        p = inputs.gaussian_problem(n, well=(5.0, 1.5), steps=12, noise=1e-2)
+    else:
+        p = coupled(inputs.gaussian_problem(n, steps=12, noise=1e-2))
+    p = stable(p)
+    s = gpu_solver(p, 32, cap=p.steps, merge=False)
+    assert not s.spstd_potential_separable()
+    s.spstd_step(p.steps)
+    R, Im = s.spstd_get_state()
+    s.close()
+    oR, oI, _ = oracle_run(p)
+    assert rel_l2(R, Im, oR, oI) <= 1e-4
+
+
+@pytest.mark.parametrize("order", ["sep_then_not", "not_then_sep"])
+def test_replaced_potential(order):
+    """set_potential on a context that has already stepped: the new potential's
+    form (tables or field) is the one used from then on."""
+    base = stable(inputs.gaussian_problem((64, 32, 16), steps=8, noise=1e-2), frac=0.3)
+    first, second = (base, coupled(base)) if order == "sep_then_not" else (coupled(base), base)
+    s = gpu_solver(first, 32, cap=16, merge=False, dt=base.dt)
+    s.spstd_step(4)
+    R4, I4 = s.spstd_get_state()
+    s.spstd_set_potential(second.V)
+    assert s.spstd_potential_separable() == (order == "not_then_sep")
+    s.spstd_step(4)
+    R, Im = s.spstd_get_state()
+    s.close()
+    aR, aI, _ = oracle_run(first, steps=4)
+    assert rel_l2(R4, I4, aR, aI) <= 1e-4
+    bR, bI, _ = oracle_run(second, steps=4, psiR=aR, psiI=aI)
+    assert rel_l2(R, Im, bR, bI) <= 1e-4
+
+
+def test_field_form_wait_timeout_is_reported_and_recoverable():
+    """The x pass that reads the V field (a potential that does not separate),
+    with its first tile never loaded: the wait runs out, the status is
+    reported, and a fresh state steps correctly again."""
+    p = stable(coupled(inputs.gaussian_problem((64, 64, 64), steps=3)))
+    s = gpu_solver(p, 32, cap=8, merge=False)
+    s.spstd_set_xy_fusion(False)
+    assert s.spstd_get_schedule(0) == 0 and not s.spstd_potential_separable()
+    s.spstd_inject_wait_timeout()
+    s.spstd_step(1)
+    with pytest.raises(spstd.SpstdError) as ei:
+        s.spstd_get_state()
+    assert ei.value.status == spstd.SPSTD_ETIMEOUT
+    s.spstd_set_state(p.psiR, p.psiI)
+    s.spstd_step(3)
+    R, Im = s.spstd_get_state()
+    s.close()
+    oR, oI, _ = oracle_run(p)
+    assert rel_l2(R, Im, oR, oI) <= 1e-4
