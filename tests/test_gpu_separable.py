@@ -113,3 +113,45 @@ def test_field_form_wait_timeout_is_reported_and_recoverable():
     s.close()
     oR, oI, _ = oracle_run(p)
     assert rel_l2(R, Im, oR, oI) <= 1e-4
+
+
+def test_batch_mixed_separability_equals_lone():
+    """Batched passes read every member's V field; for a member with a
+    separable potential that field holds the FP32 sums of the tables its lone
+    x pass uses.  Groups with separable members only, and groups that mix them
+    with potentials that do not separate, end bit for bit where the lone solves
+    do."""
+    shapes = [((64, 64, 64), "ho"), ((64, 64, 64), "ho"), ((32, 32, 32), "ho"), ((32, 32, 32), "coupled"),
+              ((256, 64), "ho"), ((256, 64), "well"), ((128, 32, 16), "ho"), ((128, 32, 16), "ho"),
+              ((512, 64), "ho")]
+    probs = []
+    for k, (shape, kind) in enumerate(shapes):
+        dims = len(shape)
+        lo, hi = [-5.0 - 0.3 * k] * dims, [5.0 + 0.2 * k] * dims
+        if kind == "well":
+            p = inputs.gaussian_problem(shape, lo, hi, seed=400 + k, well=(5.0, 1.5), dt=0.0, steps=0, n_probe=2)
+        else:
+            p = inputs.gaussian_problem(shape, lo, hi, seed=400 + k, dt=0.0, steps=0, n_probe=2)
+            if kind == "coupled":
+                p = coupled(p)
+        probs.append(p)
+    steps = 13
+    alone = []
+    for p, (_, kind) in zip(probs, shapes):
+        s = gpu_solver(p, 32, cap=steps, merge=False)
+        assert s.spstd_potential_separable() == (kind == "ho")
+        s.spstd_step(steps)
+        alone.append(s.spstd_get_state())
+        s.close()
+    batch = spstd.Batch(len(probs))
+    solvers = [gpu_solver(p, 32, cap=steps) for p in probs]
+    for s in solvers:
+        batch.spstd_batch_add(s)
+    batch.spstd_batch_step(steps)
+    batch.spstd_batch_sync()
+    for i, (s, (R, Im)) in enumerate(zip(solvers, alone)):
+        bR, bI = s.spstd_get_state()
+        assert np.array_equal(bR, R) and np.array_equal(bI, Im), i
+    batch.close()
+    for s in solvers:
+        s.close()
