@@ -182,6 +182,16 @@ spstd_status spstd_set_potential(spstd_ctx *ctx, const double *V);
  * (see spstd_set_potential), else 0. */
 spstd_status spstd_potential_separable(const spstd_ctx *ctx, int *separable);
 
+/* Host only (no device work, no context): the split spstd_set_potential
+ * tries.  V: host, nx * rows values, x fastest (rows = ny nz).  vx (nx floats)
+ * and vyz (rows floats) are caller-owned outputs.  *separable = 1 when the
+ * FP32 sum vx[i] + vyz[r] is within 4 units in the last place of
+ * V[r nx + i] at every point (the tables are then the ones the x pass uses),
+ * else 0 (vx and vyz then hold the rejected split).  SPSTD_EINVAL for null
+ * pointers or nx, rows < 1. */
+spstd_status spstd_separable_split(const double *V, int64_t nx, int64_t rows, float *vx, float *vyz,
+                                   int *separable);
+
 /* Copies the state (host, FP64, n_total values each) to the device and resets
  * the probe recorder (step counter 0, no samples). */
 spstd_status spstd_set_state(spstd_ctx *ctx, const double *psiR, const double *psiI);

@@ -1796,6 +1796,18 @@ spstd_status spstd_get_dt(const spstd_ctx *ctx, double *dt)
     return SPSTD_OK;
 }
 
+spstd_status spstd_separable_split(const double *V, int64_t nx, int64_t rows, float *vx, float *vyz,
+                                   int *separable)
+{
+    if (!V || !vx || !vyz || !separable || nx < 1 || rows < 1) return SPSTD_EINVAL;
+    std::vector<float> tx, tyz;
+    const bool ok = separable_tables(V, nx, rows, rows, tx, tyz);
+    std::memcpy(vx, tx.data(), sizeof(float) * nx);
+    std::memcpy(vyz, tyz.data(), sizeof(float) * rows);
+    *separable = ok ? 1 : 0;
+    return SPSTD_OK;
+}
+
 spstd_status spstd_potential_separable(const spstd_ctx *ctx, int *separable)
 {
     if (!ctx || !separable) return SPSTD_EINVAL;

@@ -97,6 +97,8 @@ def lib():
         "spstd_get_dt": (C.c_int, [vp, dp]),
         "spstd_steps_taken": (C.c_int, [vp, ip]),
         "spstd_potential_separable": (C.c_int, [vp, C.POINTER(C.c_int)]),
+        "spstd_separable_split": (C.c_int, [dp, C.c_int64, C.c_int64, C.POINTER(C.c_float), C.POINTER(C.c_float),
+                                            C.POINTER(C.c_int)]),
         "spstd_get_coefficients": (C.c_int, [vp, C.POINTER(C.c_int), dp, dp]),
         "spstd_launch_count": (C.c_int, [vp, C.c_int64, ip]),
         "spstd_profile_steps": (C.c_int, [vp, C.c_int64, dp, ip]),
@@ -368,6 +370,22 @@ def stability_limit(cfg: spstd_config, vmax=0.0):
     if st != SPSTD_OK:
         raise SpstdError(st, lib().spstd_status_string(st).decode())
     return s.value, dtm.value
+
+
+def separable_split(V, nx):
+    """(separable, vx, vyz): the host-side split of V (nx points along x,
+    x fastest) that spstd_set_potential tries; see spstd_separable_split."""
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    rows = V.size // nx
+    assert rows * nx == V.size
+    vx = np.empty(nx, dtype=np.float32)
+    vyz = np.empty(rows, dtype=np.float32)
+    ok = C.c_int(0)
+    st = lib().spstd_separable_split(_dp(V), int(nx), int(rows), vx.ctypes.data_as(C.POINTER(C.c_float)),
+                                     vyz.ctypes.data_as(C.POINTER(C.c_float)), C.byref(ok))
+    if st != SPSTD_OK:
+        raise SpstdError(st, lib().spstd_status_string(st).decode())
+    return bool(ok.value), vx, vyz
 
 
 class Batch:
