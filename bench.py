@@ -131,7 +131,7 @@ def measured_peaks():
 # 256^3 FP32 kernels from one ncu capture (profiles/traffic_aniso_ho_3d_256.md),
 # valid while the kernel sources hash to the recorded value.
 MEASURED_TRAFFIC = {
-    "source_hash": "c9d80d1d1f4aa4dd",
+    "source_hash": "ab0ffb8547adb27e",
     # x pass: the separable-potential form (V rebuilt from tables, no V field read)
     "aniso_ho_3d_256": {"x_pass": 134.529024e6 + 6.635264e6, "y_pass": 134.248448e6 + 4.725248e6,
                         "z_pass": 134.261248e6 + 5.904384e6},

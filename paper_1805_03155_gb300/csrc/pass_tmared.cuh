@@ -14,7 +14,9 @@
 // Tile geometry (sizes are fixed per line length N so that every block has
 // 128 (x) or 256 (strided) threads and a 16 KB / 32 KB tile part):
 //   x pass:        ROWS = 4096/N contiguous rows of N points, ROWS/2 line
-//                  pairs, block (N/E, ROWS/2), stage = src + V tiles;
+//                  pairs, block (N/E, ROWS/2), stage = src + V tiles; with a
+//                  separable potential (single grids) stage = src tile + the
+//                  tile's ROWS values of vyz, three blocks per SM;
 //   strided pass:  K planes of N points along y or z x 2P adjacent x columns
 //                  (P column pairs, P = min(4096/N, n_x/2); K = 256/(P N/E)
 //                  planes, at least 1), block (P, N/E, K).
