@@ -47,7 +47,7 @@ typedef enum {
     SPSTD_ENOMEM = 2,       /* workspace too small, or host allocation failed */
     SPSTD_ECUDA = 3,        /* a CUDA runtime call failed (message in last_error) */
     SPSTD_EUNSTABLE = 4,    /* dt above the stability limit s_star/w_max (Eq. 25/30) */
-    SPSTD_EDIVERGED = 5,    /* norm or energy is NaN/Inf */
+    SPSTD_EDIVERGED = 5,    /* norm or energy is NaN/Inf, or the norm drifted past cfg.norm_drift_limit */
     SPSTD_ETIMEOUT = 6,     /* a bounded device wait gave up (reported at the next synchronising call) */
     SPSTD_ENOTREADY = 7,    /* nothing to return yet (no probe samples) */
     SPSTD_EUNSUPPORTED = 8  /* valid request this build does not implement */
@@ -124,6 +124,20 @@ typedef struct {
                              exp((a+b)A)); the probe at that step boundary is
                              recovered exactly from the fields before and after.
                              1: always run every half-stage of every step. */
+    int no_graph;         /* 0 (default): spstd_step replays captured CUDA graphs
+                             of 16-step units; 1: it launches every kernel
+                             directly.  Both enqueue the same kernels with the
+                             same arguments in the same order, so the results
+                             are the same bits (a check of the replay). */
+    double norm_drift_limit; /* divergence rule: spstd_energy_norm returns
+                             SPSTD_EDIVERGED (after writing its outputs) when
+                             |N / N0 - 1| exceeds this, N0 being the norm of the
+                             state last given to spstd_set_state.  The schemes
+                             of Eq. 17 conserve the norm to rounding (a bounded
+                             oscillation), so a larger drift means an unstable
+                             dt or corrupted fields.  spstd_config_init sets
+                             1e-3; <= 0 turns the check off (e.g. for the RK4
+                             comparison, whose norm decays by design). */
 } spstd_config;
 
 /* Boundary conditions (Section 2.2).  Periodic axes whose length is a power of
@@ -299,20 +313,6 @@ spstd_status spstd_tune(spstd_ctx *ctx, int reps, double *ms);
 spstd_status spstd_set_xy_fusion(spstd_ctx *ctx, int on);
 spstd_status spstd_get_xy_fusion(const spstd_ctx *ctx, int *on);
 
-/* Test hook for the failure path of the bounded device waits.  With the
- * fused x-y pass active: makes its next launch skip one y tile of its first
- * plane, so that the x tiles of that plane wait in vain until their bounded
- * waits run out (about a second).  Otherwise, on a context whose x axis runs
- * the default pipelined (TMA) pass: makes the next x pass (or fused
- * reduce-add x-y pass) leave its first tile unloaded, so that the wait on
- * that tile's barrier runs out (about two seconds);
- * the block then waits for the loads it still has in flight and returns.
- * Either way the blocks return early with the device status word set, the
- * next synchronising call reports SPSTD_ETIMEOUT and clears the status;
- * psi_R and psi_I are left partly updated, and the context stays usable (set
- * a state and step again).  SPSTD_EUNSUPPORTED when the context has neither
- * pass. */
-spstd_status spstd_inject_wait_timeout(spstd_ctx *ctx);
 
 /* Norm without device allocation (the paper has no counterpart: this is a
  * service for callers that may not allocate device memory where they call).
@@ -344,10 +344,16 @@ spstd_status spstd_norm_noalloc(const void *psiR, const void *psiI, int64_t n, i
  * eigenstate at E_k up to normalisation and phase (components at other
  * energies are suppressed by the window).  While a window is open steps run
  * without fused boundaries or the resident 1D solver (every step ends at a
- * full state).  spstd_eigenstate_get copies accumulator k (unnormalised) to
- * the host and synchronises; spstd_eigenstates_end closes the window. */
+ * full state).  spstd_eigenstate_get copies accumulator k to the caller's
+ * host arrays re, im (n_total doubles each) and synchronises; with normalise =
+ * 0 they hold the raw accumulator, with normalise = 1 it is scaled to
+ * sum |phi|^2 = 1 and its phase turned so that its largest-modulus entry (the
+ * first, if several) is real and positive -- the form in which eigenstates are
+ * compared and plotted (Figs. 1, 2, 4); an all-zero accumulator stays zero.
+ * *samples (may be NULL) receives the steps accumulated so far.
+ * spstd_eigenstates_end closes the window. */
 spstd_status spstd_eigenstates_begin(spstd_ctx *ctx, int n_target, const double *E, int64_t window);
-spstd_status spstd_eigenstate_get(spstd_ctx *ctx, int k, double *re, double *im, int64_t *samples);
+spstd_status spstd_eigenstate_get(spstd_ctx *ctx, int k, int normalise, double *re, double *im, int64_t *samples);
 spstd_status spstd_eigenstates_end(spstd_ctx *ctx);
 
 /* ---- Batches: many independent solves advanced by one call ---------------
@@ -355,8 +361,9 @@ spstd_status spstd_eigenstates_end(spstd_ctx *ctx);
  * its own grid, V, dt, integrator and probes.  1D members of one length run all
  * steps of a call in one resident block each (one launch per length); 2D/3D
  * members that share dims, sizes, precision and integrator run every pass of
- * every half-stage as one launch over all their tiles; groups run on parallel
- * branches of a captured CUDA graph, replayed in chunks.  Results equal those
+ * every half-stage as one launch over all their tiles; the 2D/3D groups follow
+ * one another in a captured CUDA graph, replayed in chunks, while the 1D
+ * resident launches run beside them on a second stream.  Results equal those
  * of stepping each member alone up to FP rounding order (bit for bit where
  * the batch and the lone member run the same pass kernels and plans).
  * Members stay usable (get_state, probe, spectrum, energy_norm) between batch
@@ -366,16 +373,24 @@ spstd_status spstd_eigenstates_end(spstd_ctx *ctx);
 typedef struct spstd_batch spstd_batch;
 spstd_status spstd_batch_workspace_size(int max_members, size_t *bytes);
 /* stream: cudaStream_t for all batch work (NULL = legacy default stream);
- * device: the CUDA device every member lives on. */
-spstd_status spstd_batch_create(int max_members, int device, void *stream, void *d_workspace,
-                                size_t workspace_bytes, spstd_batch **out);
+ * device: the CUDA device every member lives on.  hbm_cap_bytes: admission by
+ * device footprint -- the members' workspaces (spstd_workspace_size of each
+ * member's config) may sum to at most this many bytes; 0 = no cap. */
+spstd_status spstd_batch_create(int max_members, size_t hbm_cap_bytes, int device, void *stream,
+                                void *d_workspace, size_t workspace_bytes, spstd_batch **out);
 spstd_status spstd_batch_destroy(spstd_batch *b);
-/* Adds ctx (waits for ctx's own stream first); *slot receives its index.
- * SPSTD_ENOTREADY when the batch is full, SPSTD_EINVAL if ctx is already in a
- * batch or on another device. */
+/* Admits ctx as a member (waits for ctx's own stream first); *slot receives
+ * its index.  SPSTD_ENOTREADY when the batch is full or the member's workspace
+ * would take the batch over its HBM cap (retry after a removal);
+ * SPSTD_EINVAL if ctx is already in a batch, lives on another device or alone
+ * exceeds the cap; SPSTD_EUNSUPPORTED for members a batch cannot step (wall or
+ * dense axes, long lines, RK4). */
 spstd_status spstd_batch_add(spstd_batch *b, spstd_ctx *ctx, int *slot);
-/* Removes the member in slot after the batch stream has drained. */
+/* Retires the member in slot after the batch stream has drained; its
+ * footprint leaves the batch's total. */
 spstd_status spstd_batch_remove(spstd_batch *b, int slot);
+/* Bytes of member workspaces admitted now, and the cap (0 = none). */
+spstd_status spstd_batch_footprint(const spstd_batch *b, size_t *in_use, size_t *cap);
 spstd_status spstd_batch_size(const spstd_batch *b, int *members);
 /* Enqueues nsteps steps of every member on the batch stream (asynchronous). */
 spstd_status spstd_batch_step(spstd_batch *b, int64_t nsteps);

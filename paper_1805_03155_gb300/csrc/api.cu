@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "../../include/spstd.h"
+#include "../../include/spstd_testing.h"
 #include "launch.cuh"
 #include "longline.h"
 #include "pass_tma_launch.h"
@@ -47,12 +48,18 @@ struct Layout {
     size_t eig_acc, eig_theta, eig_step, rk[6], lscr, xy, total;
 };
 
+// Periodic lengths 3 * 2^k that the 2D/3D pass kernels transform with a
+// radix-3 first stage (line_e and the plans of fft_line.cuh).
+bool is_radix3_len(int64_t n) { return n == 24 || n == 48 || n == 96 || n == 192 || n == 384; }
+
 // An axis uses the FFT passes when it is periodic with a power-of-two length
-// within the FFT limits; otherwise the dense operator (n <= SPSTD_MAX_DENSE_N).
+// within the FFT limits, or (2D/3D grids) one of the radix-3 lengths;
+// otherwise the dense operator (n <= SPSTD_MAX_DENSE_N).
 bool axis_is_fft(const spstd_config &cfg, int a)
 {
     const int64_t n = cfg.n[a];
-    if (cfg.bc[a] != SPSTD_PERIODIC || (n & (n - 1)) != 0) return false;
+    if (cfg.bc[a] != SPSTD_PERIODIC) return false;
+    if ((n & (n - 1)) != 0) return cfg.dims > 1 && is_radix3_len(n);
     const int64_t lim = cfg.dims == 1 ? (cfg.precision == 32 ? 8192 : 4096) : 1024;
     return n >= 2 && n <= lim;
 }
@@ -252,8 +259,8 @@ spstd_status validate(const spstd_config *cfg, std::string *why, int *m, double 
     for (int a = 0; a < cfg->dims; ++a) {
         if (!axis_is_fft(*cfg, a) && !axis_is_long(*cfg, a) && cfg->n[a] > SPSTD_MAX_DENSE_N) {
             if (why)
-                *why = "axis not supported: FFT axes are periodic powers of two (x <= 4194304; y, z <= 1024); "
-                       "other axes need n <= 256";
+                *why = "axis not supported: FFT axes are periodic powers of two (x <= 4194304; y, z <= 1024) "
+                       "or, in 2D/3D, 3 * 2^k for 24 <= n <= 384; other axes need n <= 256";
             return SPSTD_EUNSUPPORTED;
         }
     }
@@ -283,6 +290,7 @@ spstd_status validate(const spstd_config *cfg, std::string *why, int *m, double 
     if (cfg->max_nfft > 0 && (!is_pow2(cfg->max_nfft) || cfg->max_nfft < 4)) return bad("max_nfft must be a power of two >= 4");
     if (cfg->max_eigenstates < 0 || cfg->max_eigenstates > SPSTD_MAX_EIGENSTATES) return bad("max_eigenstates must be 0..4");
     if (!std::isfinite(cfg->dt)) return bad("dt is not finite");
+    if (std::isnan(cfg->norm_drift_limit)) return bad("norm_drift_limit is NaN");
     return SPSTD_OK;
 }
 
@@ -364,6 +372,7 @@ struct spstd_ctx {
     cudaStream_t cap_stream = nullptr;
     std::vector<HalfStage> hs;
     int64_t steps_taken = 0;
+    double norm0 = 0.0;  // norm of the state last set (divergence rule)
     cudaGraphExec_t gexec = nullptr;
     std::string err;
     // pipelined FP32 passes: tensor maps [field: psi_R, psi_I, tmp][view: x, y, z]
@@ -1236,7 +1245,7 @@ spstd_status step_impl(spstd_ctx *ctx, int64_t nsteps)
         const int64_t units = nsteps - 1;
         SPSTD_CU(ctx, enqueue_merged_piece<T>(ctx, 0, 0, ctx->stream));
         int64_t done = 0;
-        if (units >= kGraphSteps) {
+        if (units >= kGraphSteps && !ctx->cfg.no_graph) {
             if (!ctx->gexec) {
                 spstd_status ps = prepare_kernels<T>(ctx);
                 if (ps != SPSTD_OK) return ps;
@@ -1263,7 +1272,7 @@ spstd_status step_impl(spstd_ctx *ctx, int64_t nsteps)
         ctx->steps_taken += nsteps;
         return SPSTD_OK;
     }
-    if (nsteps >= kGraphSteps) {
+    if (nsteps >= kGraphSteps && !ctx->cfg.no_graph) {
         if (!ctx->gexec) {
             spstd_status ps = prepare_kernels<T>(ctx);
             if (ps != SPSTD_OK) return ps;
@@ -1320,6 +1329,7 @@ void spstd_config_init(spstd_config *cfg)
     cfg->preset = SPSTD_FR4;
     cfg->dt = 0.0;
     cfg->probe_capacity = 1024;
+    cfg->norm_drift_limit = 1e-3;
 }
 
 const char *spstd_status_string(spstd_status s)
@@ -1538,6 +1548,11 @@ spstd_status spstd_set_state(spstd_ctx *ctx, const double *psiR, const double *p
     if (s != SPSTD_OK) return s;
     SPSTD_CU(ctx, cudaMemsetAsync(ctx->ptr(ctx->L.counter), 0, 8, ctx->stream));
     ctx->steps_taken = 0;
+    // N0 = dV sum(psi_R^2 + psi_I^2) of the given state, for the divergence rule
+    double acc = 0.0, dV = 1.0;
+    for (int64_t i = 0; i < ctx->ntot; ++i) acc += psiR[i] * psiR[i] + psiI[i] * psiI[i];
+    for (int a = 0; a < ctx->cfg.dims; ++a) dV *= axis_spacing(ctx->cfg, a);
+    ctx->norm0 = dV * acc;
     return SPSTD_OK;
 }
 
@@ -1669,6 +1684,13 @@ spstd_status energy_norm_impl(spstd_ctx *ctx, double *norm, double *energy)
     *norm = dV * h[0];
     *energy = dV * (h[1] + h[2]);
     if (!std::isfinite(*norm) || !std::isfinite(*energy)) return fail(ctx, SPSTD_EDIVERGED, "norm or energy is not finite");
+    const double lim = ctx->cfg.norm_drift_limit;
+    if (lim > 0 && ctx->norm0 > 0 && std::fabs(*norm / ctx->norm0 - 1.0) > lim) {
+        char msg[160];
+        std::snprintf(msg, sizeof(msg), "norm drifted by %.3e relative (limit %.1e): N = %.12g, N0 = %.12g",
+                      *norm / ctx->norm0 - 1.0, lim, *norm, ctx->norm0);
+        return fail(ctx, SPSTD_EDIVERGED, msg);
+    }
     return SPSTD_OK;
 }
 
@@ -1765,7 +1787,7 @@ spstd_status spstd_eigenstates_begin(spstd_ctx *ctx, int n_target, const double 
     return SPSTD_OK;
 }
 
-spstd_status spstd_eigenstate_get(spstd_ctx *ctx, int k, double *re, double *im, int64_t *samples)
+spstd_status spstd_eigenstate_get(spstd_ctx *ctx, int k, int normalise, double *re, double *im, int64_t *samples)
 {
     if (!ctx || !re || !im || k < 0 || k >= ctx->eig_n) return SPSTD_EINVAL;
     std::vector<double2> acc(ctx->ntot);
@@ -1774,10 +1796,31 @@ spstd_status spstd_eigenstate_get(spstd_ctx *ctx, int k, double *re, double *im,
                                   sizeof(double2) * ctx->ntot, cudaMemcpyDeviceToHost, ctx->stream));
     SPSTD_CU(ctx, cudaMemcpyAsync(&n, ctx->ptr(ctx->L.eig_step), 8, cudaMemcpyDeviceToHost, ctx->stream));
     SPSTD_CU(ctx, cudaStreamSynchronize(ctx->stream));
-    for (int64_t p = 0; p < ctx->ntot; ++p) {
-        re[p] = acc[p].x;
-        im[p] = acc[p].y;
+    // optional normalisation: sum |phi|^2 = 1, and the phase turned so that the
+    // entry of largest modulus (the first such) is real and positive
+    double ss = 0.0, amax = -1.0, cr = 1.0, ci = 0.0;
+    int64_t jmax = 0;
+    if (normalise) {
+        for (int64_t p = 0; p < ctx->ntot; ++p) {
+            const double a2 = acc[p].x * acc[p].x + acc[p].y * acc[p].y;
+            ss += a2;
+            if (a2 > amax) {
+                amax = a2;
+                jmax = p;
+            }
+        }
+        if (ss > 0) {
+            // multiply by conj(z_j)/|z_j| / sqrt(ss)
+            const double aj = std::sqrt(amax), inv = 1.0 / std::sqrt(ss);
+            cr = acc[jmax].x / aj * inv;
+            ci = -acc[jmax].y / aj * inv;
+        }
     }
+    for (int64_t p = 0; p < ctx->ntot; ++p) {
+        re[p] = acc[p].x * cr - acc[p].y * ci;
+        im[p] = acc[p].x * ci + acc[p].y * cr;
+    }
+    if (normalise && ss > 0) im[jmax] = 0.0;
     if (samples) *samples = n;
     return SPSTD_OK;
 }
@@ -1925,6 +1968,8 @@ struct spstd_batch {
     cudaEvent_t ev_branch[kBatchStreams] = {nullptr};
     unsigned char *ws = nullptr;
     size_t ws_bytes = 0;
+    size_t hbm_cap = 0;     // cap on the members' workspaces (0: none)
+    size_t in_use = 0;      // sum of the members' workspace bytes
     std::vector<spstd_ctx *> slots;
     bool dirty = true;
     std::vector<BatchGroup1D> g1;
@@ -2295,8 +2340,8 @@ spstd_status spstd_batch_workspace_size(int max_members, size_t *bytes)
     return SPSTD_OK;
 }
 
-spstd_status spstd_batch_create(int max_members, int device, void *stream, void *d_workspace, size_t workspace_bytes,
-                                spstd_batch **out)
+spstd_status spstd_batch_create(int max_members, size_t hbm_cap_bytes, int device, void *stream, void *d_workspace,
+                                size_t workspace_bytes, spstd_batch **out)
 {
     if (!out || max_members < 1) return SPSTD_EINVAL;
     *out = nullptr;
@@ -2311,6 +2356,7 @@ spstd_status spstd_batch_create(int max_members, int device, void *stream, void 
     b->stream = (cudaStream_t)stream;
     b->ws = (unsigned char *)d_workspace;
     b->ws_bytes = workspace_bytes;
+    b->hbm_cap = hbm_cap_bytes;
     b->slots.assign(max_members, nullptr);
     bool ok = cudaSetDevice(device) == cudaSuccess &&
               cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) == cudaSuccess &&
@@ -2357,15 +2403,21 @@ spstd_status spstd_batch_add(spstd_batch *b, spstd_ctx *ctx, int *slot)
     if (ctx->cfg.device != b->device) return bfail(b, SPSTD_EINVAL, "context lives on another device");
     for (int a = 0; a < ctx->cfg.dims; ++a)
         if (ctx->dense[a])
-            return bfail(b, SPSTD_EUNSUPPORTED, "batches take FFT axes only (periodic, power-of-two lengths)");
+            return bfail(b, SPSTD_EUNSUPPORTED, "batches take FFT axes only (periodic; powers of two, or 3 * 2^k "
+                                                "for 24..384 in 2D/3D)");
     if (ctx->rk4) return bfail(b, SPSTD_EUNSUPPORTED, "batches take the partitioned symplectic schemes only");
     if (ctx->long_x) return bfail(b, SPSTD_EUNSUPPORTED, "batches take lines of at most 8192 (1D) / 1024 points");
+    // admission by device footprint: the member's workspace must fit under the cap
+    const size_t need = ctx->L.total;
+    if (b->hbm_cap && need > b->hbm_cap) return bfail(b, SPSTD_EINVAL, "member workspace exceeds the batch's HBM cap");
+    if (b->hbm_cap && b->in_use + need > b->hbm_cap) return bfail(b, SPSTD_ENOTREADY, "HBM cap reached");
     for (int s = 0; s < (int)b->slots.size(); ++s) {
         if (!b->slots[s]) {
             // the member's own pending work comes first
             SPSTD_BCU(b, cudaStreamSynchronize(ctx->stream));
             b->slots[s] = ctx;
             ctx->batch = b;
+            b->in_use += need;
             b->dirty = true;
             *slot = s;
             return SPSTD_OK;
@@ -2378,9 +2430,18 @@ spstd_status spstd_batch_remove(spstd_batch *b, int slot)
 {
     if (!b || slot < 0 || slot >= (int)b->slots.size() || !b->slots[slot]) return SPSTD_EINVAL;
     SPSTD_BCU(b, cudaStreamSynchronize(b->stream));
+    b->in_use -= b->slots[slot]->L.total;
     b->slots[slot]->batch = nullptr;
     b->slots[slot] = nullptr;
     b->dirty = true;
+    return SPSTD_OK;
+}
+
+spstd_status spstd_batch_footprint(const spstd_batch *b, size_t *in_use, size_t *cap)
+{
+    if (!b || !in_use || !cap) return SPSTD_EINVAL;
+    *in_use = b->in_use;
+    *cap = b->hbm_cap;
     return SPSTD_OK;
 }
 

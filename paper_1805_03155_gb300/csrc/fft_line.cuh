@@ -2,7 +2,9 @@
 // the building block of every spectral-derivative kernel (Eq. 7-10).
 //
 // A line of N complex points is held by TT = N/E threads, thread t owning the
-// elements t + e*TT (e < E) in registers ("natural layout").  The transform is
+// elements t + e*TT (e < E) in registers ("natural layout").  N is a power of
+// two, or three times one (then E is a multiple of 3 and the first stage's
+// radix carries the factor 3).  The transform is
 // a Stockham autosort sequence of radix-R stages (R divides E): stage s with
 // span Ns (product of the earlier radices) takes butterfly j's inputs from
 // j + r*N/R, multiplies them by W_N^{(j mod Ns) r N/(Ns R)}, applies a radix-R
@@ -72,6 +74,26 @@ __host__ __device__ constexpr double c16(int k)
 }
 __host__ __device__ constexpr double s16(int k) { return k <= 4 ? c16(4 - k) : c16(k - 4); }
 
+// cos(2 pi k/24) for k = 0..6: 1, (sqrt 6 + sqrt 2)/4, sqrt 3/2, sqrt 2/2, 1/2,
+// (sqrt 6 - sqrt 2)/4, 0; the rest of the circle by symmetry.  The twiddles of
+// the radix-3, 6, 12 and 24 DFTs are multiples of 2 pi/24.
+__host__ __device__ constexpr double c24q(int k)
+{
+    return k == 0 ? 1.0
+         : k == 1 ? 0.96592582628906828675
+         : k == 2 ? 0.86602540378443864676
+         : k == 3 ? 0.70710678118654752440
+         : k == 4 ? 0.5
+         : k == 5 ? 0.25881904510252076235
+                  : 0.0;
+}
+__host__ __device__ constexpr double c24(int k)
+{
+    return k < 0 ? c24(k + 24) : k >= 24 ? c24(k - 24)
+         : k <= 6 ? c24q(k) : k <= 12 ? -c24q(12 - k) : k <= 18 ? -c24q(k - 12) : c24q(24 - k);
+}
+__host__ __device__ constexpr double s24(int k) { return c24(k - 6); }
+
 // v * exp(-+ 2 pi i k/R) with k, R compile-time (R | 16).
 template <typename T, bool INV, int R, int K>
 __device__ __forceinline__ cpx<T> twc(cpx<T> v)
@@ -92,9 +114,71 @@ __device__ __forceinline__ cpx<T> twc(cpx<T> v)
     }
 }
 
-// In-register radix-R DFT of u[0], u[S], ..., u[(R-1)S] (stride S), in place,
-// natural output order.  R in {1, 2, 4, 8, 16}.  Split radix-2 recursion.
+// v * exp(-+ 2 pi i k/R) with k, R compile-time (R | 24).
+template <typename T, bool INV, int R, int K>
+__device__ __forceinline__ cpx<T> twc24(cpx<T> v)
+{
+    constexpr int k24 = (K * (24 / R)) % 24;
+    if constexpr (k24 == 0) {
+        return v;
+    } else if constexpr (k24 == 6) {
+        return rot90<T, INV>(v);
+    } else if constexpr (k24 == 12) {
+        return mk<T>(-v.x, -v.y);
+    } else {
+        constexpr T cr = (T)c24(k24);
+        constexpr T sr = (T)s24(k24);
+        if constexpr (INV)
+            return mk<T>(fma(v.x, cr, -v.y * sr), fma(v.x, sr, v.y * cr));
+        else
+            return mk<T>(fma(v.x, cr, v.y * sr), fma(v.y, cr, -v.x * sr));
+    }
+}
+
 template <typename T, bool INV, int R, int S = 1>
+struct DFT;
+
+// Radix R = 3P (P a power of two, R | 24): decimation in time into three
+// interleaved sequences of length P, their DFTs, the twiddles W_R^{r k}, and a
+// 3-point DFT for each k:  X[k + P s] = sum_r W_3^{r s} (W_R^{r k} A_r[k]).
+template <typename T, bool INV, int R, int S>
+struct DFT3 {
+    static constexpr int P = R / 3;
+    template <int K>
+    __device__ __forceinline__ static void combine(cpx<T> *u, cpx<T> *out)
+    {
+        if constexpr (K < P) {
+            // 3-point DFT with W_3 = exp(-+ 2 pi i/3) = -1/2 -+ i sqrt3/2
+            const cpx<T> a = u[(3 * K) * S];
+            const cpx<T> b = twc24<T, INV, R, K>(u[(3 * K + 1) * S]);
+            const cpx<T> c = twc24<T, INV, R, 2 * K>(u[(3 * K + 2) * S]);
+            const cpx<T> t1 = cadd<T>(b, c), t2 = csub<T>(b, c);
+            constexpr T h = (T)c24q(2);  // sqrt 3 / 2
+            const cpx<T> m = mk<T>(fma((T)-0.5, t1.x, a.x), fma((T)-0.5, t1.y, a.y));
+            out[K] = cadd<T>(a, t1);
+            // forward: X1 = m - i h t2, X2 = m + i h t2 (inverse: the signs swap)
+            const cpx<T> iht = mk<T>(-h * t2.y, h * t2.x);  // i h t2
+            out[K + P] = INV ? cadd<T>(m, iht) : csub<T>(m, iht);
+            out[K + 2 * P] = INV ? csub<T>(m, iht) : cadd<T>(m, iht);
+            combine<K + 1>(u, out);
+        }
+    }
+    __device__ __forceinline__ static void run(cpx<T> *u)
+    {
+        DFT<T, INV, P, 3 * S>::run(u);
+        DFT<T, INV, P, 3 * S>::run(u + S);
+        DFT<T, INV, P, 3 * S>::run(u + 2 * S);
+        cpx<T> out[R];
+        combine<0>(u, out);
+#pragma unroll
+        for (int k = 0; k < R; ++k) u[k * S] = out[k];
+    }
+};
+
+// In-register radix-R DFT of u[0], u[S], ..., u[(R-1)S] (stride S), in place,
+// natural output order.  R in {1, 2, 4, 8, 16} (split radix-2 recursion) or
+// R in {3, 6, 12, 24} (DFT3 above).
+template <typename T, bool INV, int R, int S>
 struct DFT {
     template <int K>
     __device__ __forceinline__ static void combine(cpx<T> *u)
@@ -110,7 +194,9 @@ struct DFT {
     }
     __device__ __forceinline__ static void run(cpx<T> *u)
     {
-        if constexpr (R == 1) {
+        if constexpr (R % 3 == 0) {
+            DFT3<T, INV, R, S>::run(u);
+        } else if constexpr (R == 1) {
             return;
         } else if constexpr (R == 2) {
             cpx<T> a = u[0], b = u[S];
@@ -137,22 +223,25 @@ struct DFT {
 };
 
 // ---------------------------------------------------------------------------
-// Stage plans.  E = elements per thread (a power of two), N = E * TT.  The
-// first stage has radix min(N, E); the rest of N/E is split into as many
-// radix-E stages as fit plus one smaller remainder stage placed second.
+// Stage plans.  E = elements per thread (a power of two, or 3 times one),
+// N = E * TT with TT a power of two.  The first stage has radix min(N, E); the
+// rest of N/E is split into as many stages of radix P = the largest power of
+// two dividing E as fit, plus one smaller remainder stage placed second.
 // ---------------------------------------------------------------------------
 __host__ __device__ constexpr int ilog2c(int x) { return x <= 1 ? 0 : 1 + ilog2c(x / 2); }
+__host__ __device__ constexpr int p2div(int x) { return x & -x; }
 
 __host__ __device__ constexpr int plan_stages(int N, int E)
 {
-    return N <= E ? 1 : 1 + ((ilog2c(N / E) % ilog2c(E)) ? 1 : 0) + ilog2c(N / E) / ilog2c(E);
+    return N <= E ? 1
+                  : 1 + ((ilog2c(N / E) % ilog2c(p2div(E))) ? 1 : 0) + ilog2c(N / E) / ilog2c(p2div(E));
 }
 __host__ __device__ constexpr int plan_radix(int N, int E, int s)
 {
     return N <= E ? N
          : s == 0 ? E
-         : (s == 1 && (ilog2c(N / E) % ilog2c(E))) ? (1 << (ilog2c(N / E) % ilog2c(E)))
-                                                   : E;
+         : (s == 1 && (ilog2c(N / E) % ilog2c(p2div(E)))) ? (1 << (ilog2c(N / E) % ilog2c(p2div(E))))
+                                                          : p2div(E);
 }
 __host__ __device__ constexpr int plan_span(int N, int E, int s)
 {
@@ -176,6 +265,7 @@ __device__ __forceinline__ void fft_stage(cpx<T> (&v)[E], const int t, XC &xc,
         constexpr int TT = N / E;
         constexpr int Q = E / R;
         static_assert(E % R == 0, "stage radix must divide the elements per thread");
+        static_assert(N % E == 0 && ((N / E) & (N / E - 1)) == 0, "N/E must be a power of two");
         if constexpr (S > 0) {
             xc.sync();
 #pragma unroll
@@ -188,7 +278,7 @@ __device__ __forceinline__ void fft_stage(cpx<T> (&v)[E], const int t, XC &xc,
             cpx<T> u[R];
 #pragma unroll
             for (int r = 0; r < R; ++r) u[r] = v[q + r * Q];
-            const int jm = j & (Ns - 1);
+            const int jm = j % Ns;
             if constexpr (S > 0) {
                 constexpr int step = N / (Ns * R);
 #pragma unroll
@@ -220,13 +310,15 @@ __device__ __forceinline__ void fft_line(cpx<T> (&v)[E], const int t, XC &xc,
     fft_stage<T, N, E, INV, 0>(v, t, xc, tw);
 }
 
-// Elements per thread for a line of N points in precision T.
+// Elements per thread for a line of N points in precision T: 16 FP32 / 8
+// FP64 for a power-of-two N; 12 (or N, below that) for N = 3 * 2^k, so that
+// the first stage takes the factor 3.
 template <typename T> struct max_e;
 template <> struct max_e<float> { static constexpr int value = 16; };
 template <> struct max_e<double> { static constexpr int value = 8; };
 template <typename T, int N>
 struct line_e {
-    static constexpr int value = N < max_e<T>::value ? N : max_e<T>::value;
+    static constexpr int value = N % 3 == 0 ? (N < 12 ? N : 12) : (N < max_e<T>::value ? N : max_e<T>::value);
 };
 
 }  // namespace spstd

@@ -21,6 +21,11 @@ cudaError_t Launch<T>::xpass(int N, const PassArgs<T> &a, cudaStream_t s)
     case 256: return SPSTD_X(256);
     case 512: return SPSTD_X(512);
     case 1024: return SPSTD_X(1024);
+    case 24: return SPSTD_X(24);
+    case 48: return SPSTD_X(48);
+    case 96: return SPSTD_X(96);
+    case 192: return SPSTD_X(192);
+    case 384: return SPSTD_X(384);
     case 2048: return SPSTD_X(2048);
     case 4096: return SPSTD_X(4096);
     case 8192: return SPSTD_X(8192);
@@ -44,6 +49,11 @@ cudaError_t Launch<T>::spass(int N, const PassArgs<T> &a, cudaStream_t s)
     case 256: return SPSTD_S(256);
     case 512: return SPSTD_S(512);
     case 1024: return SPSTD_S(1024);
+    case 24: return SPSTD_S(24);
+    case 48: return SPSTD_S(48);
+    case 96: return SPSTD_S(96);
+    case 192: return SPSTD_S(192);
+    case 384: return SPSTD_S(384);
     default: return cudaErrorInvalidValue;
     }
 #undef SPSTD_S
@@ -81,8 +91,10 @@ cudaError_t Launch<T>::resident1d(int N, const ResidentArgs<T> &a, cudaStream_t 
 #undef SPSTD_R
 }
 
+// line lengths of the 2D/3D passes: powers of two and 3 * 2^k (radix-3 first stage)
 #define SPSTD_CASES(M)                                                     \
-    M(2) M(4) M(8) M(16) M(32) M(64) M(128) M(256) M(512) M(1024)
+    M(2) M(4) M(8) M(16) M(32) M(64) M(128) M(256) M(512) M(1024)        \
+    M(24) M(48) M(96) M(192) M(384)
 
 template <typename T>
 int Launch<T>::xpass_tiles(int N, int64_t n_rows)
@@ -141,7 +153,9 @@ cudaError_t Launch<T>::resident_batch(int N, const ResidentArgs<T> *args, int me
     switch (N) {
 #define SPSTD_C(n) \
     case n: return resident_batch_n<T, n>(args, members, nsteps, s);
-        SPSTD_CASES(SPSTD_C)
+        // 1D grids: power-of-two lengths only
+        SPSTD_C(2) SPSTD_C(4) SPSTD_C(8) SPSTD_C(16) SPSTD_C(32) SPSTD_C(64) SPSTD_C(128) SPSTD_C(256)
+        SPSTD_C(512) SPSTD_C(1024)
 #undef SPSTD_C
     case 2048: return resident_batch_n<T, 2048>(args, members, nsteps, s);
     case 4096: return resident_batch_n<T, 4096>(args, members, nsteps, s);

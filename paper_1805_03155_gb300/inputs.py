@@ -263,15 +263,16 @@ def gaussian_problem(n, lo=None, hi=None, seed: int = 7, omega=None, integrator=
                    integrator, dt, steps, 0, bc=bcc)
 
 
-def batch_mix(count: int = 512, seed: int = 4, steps: int = 5000, sizes3d=(32, 64)) -> List[Problem]:
+def batch_mix(count: int = 512, seed: int = 4, steps: int = 5000, sizes3d=(32, 48, 64, 96)) -> List[Problem]:
     """Seeded mix of uneven solves, one third each of:
 
     * 1D finite wells: N a uniform power of two in 128..8192 on [-20, 20],
       half-width 2, V0 ~ U(1, 10);
     * 2D isotropic oscillators: n^2 with n uniform in {64, 128, 256, 512} on
       [-8, 8]^2, omega = 1;
-    * 3D isotropic oscillators: n^3 with n uniform in ``sizes3d`` (powers of
-      two) on [-8, 8]^3, omega = 1.
+    * 3D isotropic oscillators: n^3 with n uniform in ``sizes3d`` on
+      [-8, 8]^3, omega = 1 (32^3..96^3 read as the FFT-friendly sizes
+      32, 48, 64 and 96).
 
     Each gets the gaussian_problem start (psi_R and psi_I displaced Gaussians,
     seeded per member), 2 probes, FR4, dt = 0 (half the stability limit, chosen

@@ -6,7 +6,11 @@ context workspace) fits under the HBM cap; its state then stays on the device
 while the batch advances every member in chunks of `chunk_steps`.  A member
 whose steps are done is retired at the next chunk boundary: its energy, norm
 and probe spectrum are read back, its slot and memory are freed, and its
-latency (retire time minus arrival time) is recorded.  Requests that arrive
+latency (retire time minus arrival time) is recorded.  A request whose
+footprint alone exceeds the cap is refused at submit().  The batch itself
+enforces the cap on its members (spstd_batch_add refuses a member that would
+take it over); the server checks the same sum, plus the contexts it has set up
+but not yet admitted, before it allocates a context.  Requests that arrive
 while others run are admitted between chunks, so their work overlaps on the
 device with the running ones.  Setting up a request's context and reading a
 retired member's results happen on a stream of their own while the batch's
@@ -43,13 +47,12 @@ class Server:
     def __init__(self, hbm_cap_bytes: float = 150e9, max_slots: int = 1024, chunk_steps: int = 500,
                  precision: int = 32, device: int = 0, keep_state: bool = False, spectrum: bool = True,
                  tune: bool = True):
-        import torch
-
-        self.batch = spstd.Batch(max_slots, device=device)
-        # contexts are set up, and their results read, on a stream of their
-        # own, so that this host and device work overlaps the batch's chunks
-        self.setup_stream = torch.cuda.Stream(device=torch.device("cuda", device))
-        self.cap = hbm_cap_bytes
+        # the batch and the setup stream are made on first use (the device is
+        # touched only once there is work)
+        self.batch = None
+        self.setup_stream = None
+        self.max_slots = int(max_slots)
+        self.cap = int(hbm_cap_bytes)
         self.chunk = int(chunk_steps)
         self.precision = precision
         self.device = device
@@ -67,11 +70,24 @@ class Server:
         self.tuned_shapes = set()
         self._untuned = False
 
-    def footprint_of(self, problem) -> int:
+    def _device(self):
+        if self.batch is None:
+            import torch
+
+            self.batch = spstd.Batch(self.max_slots, device=self.device, hbm_cap_bytes=self.cap)
+            # contexts are set up, and their results read, on a stream of their
+            # own, so that this host and device work overlaps the batch's chunks
+            self.setup_stream = torch.cuda.Stream(device=torch.device("cuda", self.device))
+
+    def footprint_of(self, problem, steps=None) -> int:
+        """Device bytes of the context a request of `steps` steps (default:
+        problem.steps) needs: its workspace, with a probe ring of one sample
+        per step."""
+        steps = problem.steps if steps is None else steps
         cfg = spstd.make_config(problem.dims, problem.n[: problem.dims], problem.lo[: problem.dims],
                                 problem.hi[: problem.dims], precision=self.precision,
                                 integrator=problem.integrator, dt=problem.dt, probes=problem.probes,
-                                probe_capacity=max(1, problem.steps))
+                                probe_capacity=max(1, int(steps)))
         import ctypes as C
         n = C.c_size_t(0)
         st = spstd.lib().spstd_workspace_size(C.byref(cfg), C.byref(n))
@@ -80,8 +96,13 @@ class Server:
         return int(n.value)
 
     def submit(self, problem, steps: int, arrival: Optional[float] = None) -> int:
+        need = self.footprint_of(problem, steps)
+        if need > self.cap:
+            # it could never be admitted: refuse it now rather than queue it for good
+            raise spstd.SpstdError(spstd.SPSTD_EINVAL, f"request needs {need} bytes of device memory, more than "
+                                                       f"the HBM cap of {self.cap} bytes")
         r = Request(self._next, problem, int(steps), time.perf_counter() if arrival is None else arrival)
-        r.need = self.footprint_of(problem)
+        r.need = need
         self._next += 1
         self.queue.append(r)
         return r.rid
@@ -93,6 +114,7 @@ class Server:
             if r.arrival > now or self.footprint + r.need > self.cap:
                 still.append(r)
                 continue
+            self._device()
             r.solver = spstd.solver_for(r.problem, precision=self.precision, probe_capacity=max(1, r.steps),
                                         device=self.device, stream=self.setup_stream)
             self.footprint += r.need
@@ -133,7 +155,16 @@ class Server:
         frees them; their work runs on the setup stream."""
         for r in self.retiring:
             s = r.solver
-            r.result["norm"], r.result["energy"] = s.spstd_energy_norm()
+            try:
+                r.result["norm"], r.result["energy"] = s.spstd_energy_norm()
+                r.result["status"] = "ok"
+            except spstd.SpstdError as e:
+                if e.status != spstd.SPSTD_EDIVERGED:
+                    raise
+                # the divergence rule: a non-finite or drifted norm marks the request failed
+                r.result["norm"], r.result["energy"] = e.norm, e.energy
+                r.result["status"] = "diverged"
+            r.result["dt"] = s.spstd_get_dt()
             if self.spectrum and r.problem.probes and r.steps >= 2:
                 r.result["E"], r.result["amp"] = s.spstd_spectrum(-1, max_peaks=4)
             if self.keep_state:
@@ -186,4 +217,5 @@ class Server:
             if r.solver is not None:
                 r.solver.close()
                 r.solver = None
-        self.batch.close()
+        if self.batch is not None:
+            self.batch.close()

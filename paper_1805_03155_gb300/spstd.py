@@ -15,7 +15,8 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libspstd.so")
-HEADER = os.path.join(os.path.dirname(HERE), "include", "spstd.h")
+INCLUDE = os.path.join(os.path.dirname(HERE), "include")
+HEADER = os.path.join(INCLUDE, "spstd.h")
 
 SPSTD_OK, SPSTD_EINVAL, SPSTD_ENOMEM, SPSTD_ECUDA, SPSTD_EUNSTABLE = 0, 1, 2, 3, 4
 SPSTD_EDIVERGED, SPSTD_ETIMEOUT, SPSTD_ENOTREADY, SPSTD_EUNSUPPORTED = 5, 6, 7, 8
@@ -56,6 +57,8 @@ class spstd_config(C.Structure):
         ("bc", C.c_int * 3),
         ("max_eigenstates", C.c_int),
         ("unmerged_steps", C.c_int),
+        ("no_graph", C.c_int),
+        ("norm_drift_limit", C.c_double),
     ]
 
 
@@ -63,8 +66,9 @@ _lib = None
 
 
 def declared_functions():
-    """Names of the entry points include/spstd.h declares."""
-    txt = open(HEADER).read()
+    """Names of the entry points the headers in include/ declare (the API in
+    spstd.h, the test hooks in spstd_testing.h)."""
+    txt = "".join(open(os.path.join(INCLUDE, f)).read() for f in sorted(os.listdir(INCLUDE)) if f.endswith(".h"))
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
     return sorted(set(re.findall(r"\b(spstd_[a-z0-9_]+)\s*\(", txt)))
 
@@ -104,10 +108,11 @@ def lib():
         "spstd_profile_steps": (C.c_int, [vp, C.c_int64, dp, ip]),
         "spstd_norm_noalloc": (C.c_int, [vp, vp, C.c_int64, C.c_int, C.c_double, vp, vp]),
         "spstd_eigenstates_begin": (C.c_int, [vp, C.c_int, dp, C.c_int64]),
-        "spstd_eigenstate_get": (C.c_int, [vp, C.c_int, dp, dp, ip]),
+        "spstd_eigenstate_get": (C.c_int, [vp, C.c_int, C.c_int, dp, dp, ip]),
         "spstd_eigenstates_end": (C.c_int, [vp]),
         "spstd_batch_workspace_size": (C.c_int, [C.c_int, C.POINTER(C.c_size_t)]),
-        "spstd_batch_create": (C.c_int, [C.c_int, C.c_int, vp, vp, C.c_size_t, C.POINTER(vp)]),
+        "spstd_batch_create": (C.c_int, [C.c_int, C.c_size_t, C.c_int, vp, vp, C.c_size_t, C.POINTER(vp)]),
+        "spstd_batch_footprint": (C.c_int, [vp, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]),
         "spstd_batch_destroy": (C.c_int, [vp]),
         "spstd_batch_add": (C.c_int, [vp, vp, C.POINTER(C.c_int)]),
         "spstd_batch_remove": (C.c_int, [vp, C.c_int]),
@@ -142,7 +147,7 @@ def _dp(a):
 
 def make_config(dims, n, lo, hi, precision=64, integrator="FR4", dt=0.0, probes=(), probe_capacity=1024,
                 max_nfft=0, hbar=1.0, mass=1.0, nyquist_zero=False, c=None, d=None, device=0, stream=None,
-                bc=(0, 0, 0), merge=True, max_eigenstates=0):
+                bc=(0, 0, 0), merge=True, max_eigenstates=0, no_graph=False, norm_drift_limit=1e-3):
     cfg = spstd_config()
     lib().spstd_config_init(C.byref(cfg))
     cfg.dims = int(dims)
@@ -178,6 +183,8 @@ def make_config(dims, n, lo, hi, precision=64, integrator="FR4", dt=0.0, probes=
         cfg.bc[a] = int(bb[a])
     cfg.unmerged_steps = 0 if merge else 1
     cfg.max_eigenstates = int(max_eigenstates)
+    cfg.no_graph = int(bool(no_graph))
+    cfg.norm_drift_limit = float(norm_drift_limit)
     return cfg
 
 
@@ -262,9 +269,16 @@ class Solver:
         return E[: n.value].copy(), A[: n.value].copy()
 
     def spstd_energy_norm(self):
+        """(norm, energy).  On SPSTD_EDIVERGED the SpstdError carries both
+        values as .norm and .energy (the C call writes them before it returns)."""
         nv = C.c_double(0)
         ev = C.c_double(0)
-        self._check(self.L.spstd_energy_norm(self.ctx, C.byref(nv), C.byref(ev)))
+        st = self.L.spstd_energy_norm(self.ctx, C.byref(nv), C.byref(ev))
+        try:
+            self._check(st)
+        except SpstdError as e:
+            e.norm, e.energy = nv.value, ev.value
+            raise
         return nv.value, ev.value
 
     def spstd_apply_hamiltonian(self, which):
@@ -299,18 +313,14 @@ class Solver:
         self._check(self.L.spstd_eigenstates_begin(self.ctx, len(E), _dp(E), int(window)))
 
     def spstd_eigenstate_get(self, k, normalise=True):
-        """Accumulator k as a complex array; normalised to sum |phi|^2 = 1 and
-        rotated so that its largest entry is real positive when normalise."""
+        """Accumulator k as a complex array (normalised in the library when
+        normalise: sum |phi|^2 = 1, largest entry real positive)."""
         re_ = np.empty(self.n_total)
         im_ = np.empty(self.n_total)
         n = C.c_int64(0)
-        self._check(self.L.spstd_eigenstate_get(self.ctx, int(k), _dp(re_), _dp(im_), C.byref(n)))
-        z = re_ + 1j * im_
-        if normalise and np.any(z):
-            z = z / np.linalg.norm(z)
-            j = np.argmax(np.abs(z))
-            z = z * np.exp(-1j * np.angle(z[j]))
-        return z
+        self._check(self.L.spstd_eigenstate_get(self.ctx, int(k), int(bool(normalise)), _dp(re_), _dp(im_),
+                                                C.byref(n)))
+        return re_ + 1j * im_
 
     def spstd_eigenstates_end(self):
         self._check(self.L.spstd_eigenstates_end(self.ctx))
@@ -392,7 +402,7 @@ class Batch:
     """Many independent solves advanced by one call (spstd_batch_*); the
     descriptor workspace is a torch uint8 tensor."""
 
-    def __init__(self, max_members, device=0, stream=None):
+    def __init__(self, max_members, device=0, stream=None, hbm_cap_bytes=0):
         import torch
 
         self.L = lib()
@@ -405,8 +415,9 @@ class Batch:
         self._ws = torch.empty(nbytes.value + 256, dtype=torch.uint8, device=dev)
         aligned = (self._ws.data_ptr() + 255) // 256 * 256
         self.b = C.c_void_p(0)
-        self._check(self.L.spstd_batch_create(int(max_members), int(device), C.c_void_p(stream.cuda_stream),
-                                              C.c_void_p(aligned), nbytes.value, C.byref(self.b)))
+        self._check(self.L.spstd_batch_create(int(max_members), int(hbm_cap_bytes), int(device),
+                                              C.c_void_p(stream.cuda_stream), C.c_void_p(aligned), nbytes.value,
+                                              C.byref(self.b)))
         self.members = {}
 
     def _check(self, st):
@@ -425,6 +436,13 @@ class Batch:
     def spstd_batch_remove(self, slot):
         self._check(self.L.spstd_batch_remove(self.b, int(slot)))
         return self.members.pop(slot)
+
+    def spstd_batch_footprint(self):
+        """(bytes of member workspaces admitted, cap); cap 0 = none."""
+        used = C.c_size_t(0)
+        cap = C.c_size_t(0)
+        self._check(self.L.spstd_batch_footprint(self.b, C.byref(used), C.byref(cap)))
+        return int(used.value), int(cap.value)
 
     def spstd_batch_size(self):
         n = C.c_int(0)
@@ -475,7 +493,7 @@ def spstd_norm_noalloc(psiR_ptr, psiI_ptr, n, precision, cell_volume, out_ptr, s
 
 
 def solver_for(problem, precision=64, probe_capacity=None, stream=None, device=0, dt=None, merge=True,
-               max_eigenstates=0):
+               max_eigenstates=0, no_graph=False, norm_drift_limit=1e-3):
     """Creates a Solver for an inputs.Problem and uploads V and the state."""
     cap = probe_capacity if probe_capacity is not None else max(1, problem.steps)
     cfg = make_config(problem.dims, problem.n[: problem.dims], problem.lo[: problem.dims],
@@ -483,7 +501,7 @@ def solver_for(problem, precision=64, probe_capacity=None, stream=None, device=0
                       dt=problem.dt if dt is None else dt, probes=problem.probes, probe_capacity=cap,
                       max_nfft=problem.nfft if problem.nfft else 0, hbar=problem.hbar, mass=problem.mass,
                       device=device, bc=getattr(problem, "bc", (0, 0, 0)), merge=merge,
-                      max_eigenstates=max_eigenstates)
+                      max_eigenstates=max_eigenstates, no_graph=no_graph, norm_drift_limit=norm_drift_limit)
     s = Solver(cfg, stream=stream)
     s.spstd_set_potential(problem.V)
     s.spstd_set_state(problem.psiR, problem.psiI)

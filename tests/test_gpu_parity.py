@@ -17,6 +17,8 @@ SHAPES = [
     (8,), (64,), (256,), (1024,), (4096,),
     (32, 64), (128, 16), (4, 8), (256, 64),
     (16, 32, 8), (32, 32, 32), (8, 4, 64), (64, 16, 16),
+    # radix-3 line lengths (3 * 2^k) on every axis
+    (96, 48), (384, 24), (48, 24, 96), (24, 192, 8),
 ]
 
 

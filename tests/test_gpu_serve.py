@@ -60,18 +60,23 @@ def test_served_results_equal_lone_solves(precision, tune):
 
 
 def test_admission_respects_hbm_cap():
+    """With the cap at the largest request's footprint every request still
+    runs, but never more at once than fit: the server's total of set-up
+    contexts and the batch's own total of members stay under the cap."""
     from paper_1805_03155_gb300 import serve
 
     reqs = requests()[:4]
-    srv = serve.Server(hbm_cap_bytes=1.0, max_slots=8, chunk_steps=5, precision=32)  # nothing fits
+    probe = serve.Server(hbm_cap_bytes=1 << 50)
+    cap = max(probe.footprint_of(p, steps) for p, steps in reqs)
+    srv = serve.Server(hbm_cap_bytes=cap, max_slots=8, chunk_steps=5, precision=32)
     for p, steps in reqs:
         srv.submit(p, steps)
-    assert not srv.step()
-    assert len(srv.running) == 0 and len(srv.queue) == 4
-    cap = max(srv.footprint_of(p) for p, _ in reqs)
-    srv.cap = cap  # now the largest request fits, alone
-    srv.step()
-    assert len(srv.running) >= 1 and srv.footprint <= cap
+    most = 0
+    while srv.step() or srv.queue or srv.ready:
+        used, bcap = srv.batch.spstd_batch_footprint()
+        assert bcap == cap and used <= cap and srv.footprint <= cap
+        most = max(most, len(srv.running))
     srv.run()
-    assert len(srv.done) == 4
+    assert len(srv.done) == 4 and most >= 1
+    assert all(r.result["status"] == "ok" for r in srv.done)
     srv.close()
