@@ -1,0 +1,146 @@
+"""Long-run parity: the CUDA path against the FP64 oracle over the step counts
+of the workloads, and the timed 256^3 path over whole grids.
+
+* 1D finite well (256 points, FR4, 20000 steps) in FP32: psi and the probe
+  series against the oracle run live; every spectral peak (dispersion-
+  corrected, Tables 2-4's energy read-out) to 1e-5 relative of the oracle's
+  peak from the oracle's own series.
+* 64^3 isotropic oscillator (FR4) after 2000 and 10000 steps, FP64 and FP32,
+  against the oracle's run stored in tests/golden/ho_3d_64_fr4_oracle.npz
+  (written by tests/golden/make_ho_3d_64_golden.py, which calls only the
+  oracle; two hours of one core): psi element by element, the probe series,
+  and the peak energies.
+* 256^3 anisotropic oscillator (SUZUKI6) in the configuration the benchmark
+  times (FP32, fused step boundaries, the separable-potential x pass): two
+  full steps against the oracle over the whole grid, and graph replay against
+  direct launches bit for bit over 17 steps.
+
+Tolerances (the benchmark spec): FP64 psi 1e-10 relative, FP32 psi 1e-4 relative L2,
+eigen-energies 1e-5 relative per peak.  The FP32 error after n steps is
+printed so that its growth with the step count is on record.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1805_03155_gb300 import inputs
+from helpers import gpu_solver, oracle_grid, oracle_run, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "ho_3d_64_fr4_oracle.npz")
+
+
+def peak_energies(z, p, max_peaks=8):
+    """The oracle's dispersion-corrected peak energies of a probe series."""
+    c, d = oracle.preset(p.integrator)
+    th, _, amp = oracle.spectrum(z, p.dt, max_peaks=max_peaks, thresh=1e-3)
+    return np.array([oracle.phase_correct(t, c, d) / p.dt for t in th]), amp
+
+
+def match_peaks(E, oE):
+    """Relative error of each oracle peak against the nearest device peak."""
+    return np.array([np.min(np.abs(E - e)) / abs(e) for e in oE])
+
+
+def elem_err(aR, aI, bR, bI):
+    scale = max(np.max(np.abs(bR)), np.max(np.abs(bI)))
+    return max(np.max(np.abs(aR - bR)), np.max(np.abs(aI - bI))) / scale
+
+
+@pytest.mark.slow
+def test_well_1d_full_run_fp32():
+    p = inputs.well_1d()
+    s = gpu_solver(p, 32, cap=p.steps)
+    s.spstd_step(p.steps)
+    R, Im = s.spstd_get_state()
+    z = np.array([s.spstd_probe(q) for q in range(len(p.probes))])
+    E, A = s.spstd_spectrum(-1, max_peaks=8, thresh=1e-3, phase_correct=True)
+    s.close()
+    oR, oI, opr = oracle_run(p)
+    err = rel_l2(R, Im, oR, oI)
+    print(f"well_1d FP32 after {p.steps} steps: psi rel L2 {err:.3e}, element {elem_err(R, Im, oR, oI):.3e}")
+    assert err <= 1e-4
+    assert np.max(np.abs(z - opr)) <= 1e-4 * np.max(np.abs(opr))
+    oE, oA = peak_energies(opr.sum(axis=0), p)
+    rel = match_peaks(E, oE)
+    print("well_1d FP32 peak energy rel err:", rel)
+    assert len(E) == len(oE)
+    assert np.max(rel) <= 1e-5
+
+
+@pytest.fixture(scope="module")
+def golden():
+    assert os.path.exists(GOLDEN), "tests/golden/ho_3d_64_fr4_oracle.npz missing (make_ho_3d_64_golden.py)"
+    return np.load(GOLDEN)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("precision,tol", [(64, 1e-10), (32, 1e-4)])
+def test_ho_3d_64_long_run_vs_oracle(golden, precision, tol):
+    p = inputs.ho_3d()
+    assert list(golden["probe_idx"]) == list(p.probes) and float(golden["dt"]) == p.dt
+    s = gpu_solver(p, precision, cap=p.steps)
+    done = 0
+    for n in (2000, 10000):
+        s.spstd_step(n - done)
+        done = n
+        R, Im = s.spstd_get_state()
+        oR, oI = golden[f"psiR_{n}"], golden[f"psiI_{n}"]
+        err, el = rel_l2(R, Im, oR, oI), elem_err(R, Im, oR, oI)
+        print(f"ho_3d_64 FP{precision} after {n} steps: psi rel L2 {err:.3e}, element {el:.3e}")
+        assert err <= tol
+        if precision == 64:
+            assert el <= tol
+    z = np.array([s.spstd_probe(q) for q in range(len(p.probes))])
+    E, A = s.spstd_spectrum(-1, max_peaks=8, thresh=1e-3, phase_correct=True)
+    s.close()
+    opr = golden["probes"]
+    assert np.max(np.abs(z - opr)) <= tol * np.max(np.abs(opr))
+    oE, oA = peak_energies(opr.sum(axis=0), p)
+    rel = match_peaks(E, oE)
+    print(f"ho_3d_64 FP{precision} peaks {np.round(oE, 6)} rel err {rel}")
+    assert len(E) == len(oE)
+    assert np.max(rel) <= (1e-9 if precision == 64 else 1e-5)
+
+
+@pytest.fixture(scope="module")
+def aniso2():
+    return inputs.aniso_ho_3d(steps=2)
+
+
+@pytest.mark.slow
+def test_aniso_256_two_steps_whole_grid(aniso2):
+    """Two SUZUKI6 steps at 256^3 (a merged step boundary with its interpolated
+    probe, the separable-V x pass, y and z reduce-add passes) against the
+    oracle over all 16.8 M points; the oracle takes about a minute and a half."""
+    p = aniso2
+    s = gpu_solver(p, 32, cap=4)
+    assert s.spstd_potential_separable()
+    s.spstd_step(2)
+    R, Im = s.spstd_get_state()
+    z = np.array([s.spstd_probe(q) for q in range(len(p.probes))])
+    s.close()
+    oR, oI, opr = oracle_run(p, steps=2)
+    err, el = rel_l2(R, Im, oR, oI), elem_err(R, Im, oR, oI)
+    print(f"aniso_ho_3d_256 FP32 after 2 steps: psi rel L2 {err:.3e}, element {el:.3e}")
+    assert err <= 1e-4 and el <= 1e-4
+    assert np.max(np.abs(z - opr)) <= 1e-4 * np.max(np.abs(opr))
+
+
+def test_aniso_256_graph_replay_is_bitwise(aniso2):
+    """17 steps in one call replay the captured 16-unit graph; the same call
+    with every kernel launched directly gives the same bits."""
+    p = aniso2
+    out = []
+    for no_graph in (False, True):
+        s = gpu_solver(p, 32, cap=32, no_graph=no_graph)
+        s.spstd_step(17)
+        R, Im = s.spstd_get_state()
+        z = s.spstd_probe(0)
+        s.close()
+        out.append((R, Im, z))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    assert np.array_equal(out[0][2], out[1][2])
