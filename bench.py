@@ -128,7 +128,7 @@ def measured_peaks():
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
-# 256^3 FP32 kernels from one ncu capture (profiles/traffic_aniso_ho_3d_256.md),
+# 256^3 FP32 kernels from one ncu capture (its summary is kept under profiles/),
 # valid while the kernel sources hash to the recorded value.
 MEASURED_TRAFFIC = {
     "source_hash": "ab0ffb8547adb27e",
@@ -140,16 +140,21 @@ TRAFFIC_SOURCES = ["paper_1805_03155_gb300/csrc/pass_tmared.cuh", "paper_1805_03
                    "paper_1805_03155_gb300/csrc/tma.cuh", "paper_1805_03155_gb300/csrc/pass_tma_launch.h"]
 
 
-def measured_traffic(workload, kernel, schedule=0):
-    """Recorded traffic of the default (pipelined) kernel; None for another
-    schedule or once the kernel sources have changed."""
+def traffic_source_hash():
+    """First 16 hex digits of the SHA-256 of the sources of the recorded kernels."""
     import hashlib
-    if schedule != 0:
-        return None
     h = hashlib.sha256()
     for f in TRAFFIC_SOURCES:
         h.update(open(os.path.join(ROOT, f), "rb").read())
-    if h.hexdigest()[:16] != MEASURED_TRAFFIC["source_hash"]:
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(workload, kernel, schedule=0):
+    """Recorded traffic of the default (pipelined) kernel; None for another
+    schedule or once the kernel sources have changed."""
+    if schedule != 0:
+        return None
+    if traffic_source_hash() != MEASURED_TRAFFIC["source_hash"]:
         return None
     return MEASURED_TRAFFIC.get(workload, {}).get(kernel)
 
@@ -189,10 +194,34 @@ def alu_peak_tflops(prec, sm_mhz):
     return FP64_NOMINAL_TFLOPS * mhz / SM_MAX_MHZ
 
 
+def host_cpu():
+    """The host's CPU model and core count (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu part")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    import platform
+    return {"nproc": os.cpu_count(), "cpu": model, "arch": platform.machine()}
+
+
 def cpu_baseline(problem, budget_s=20.0):
     """The FP64 oracle on the host: one half-stage (K apply + axpy) on the
     full grid, repeated while the budget lasts, scaled to grid-point-steps/s
-    with the integrator's half-stages per step."""
+    with the integrator's half-stages per step (an extrapolation from that
+    sample, not a timed full step)."""
     import oracle
 
     g = oracle.make_grid(problem.dims, problem.n[: problem.dims], problem.lo[: problem.dims],
@@ -209,25 +238,94 @@ def cpu_baseline(problem, budget_s=20.0):
             break
     t = (time.perf_counter() - t0) / reps
     return {"value": problem.n_total / (h * t), "unit": "grid-point-steps/s", "cores": 1, "kind": "oracle",
+            "extrapolated": True, "host": host_cpu(),
             "sample": f"{reps} half-stage(s) (K apply + axpy) on the full {problem.n_total}-point grid, "
                       f"{t:.2f} s each, scaled by {h} half-stages per step; single thread, FP64"}
 
 
-def batched_vs_plain(count=512, steps=20, precision=32, local=0, plain=True):
+def _oracle_member_step_time(args):
+    """Seconds per oracle step of one batch member (a worker of the spawn pool)."""
+    import oracle
+    from paper_1805_03155_gb300 import inputs  # noqa: F401  (the member arrives pickled)
+    p, dt, steps = args
+    g = oracle.make_grid(p.dims, p.n[: p.dims], p.lo[: p.dims], p.hi[: p.dims], p.hbar, p.mass)
+    c, d = oracle.preset(p.integrator)
+    t0 = time.perf_counter()
+    oracle.run(p.psiR, p.psiI, p.V, g, c, d, dt, steps, p.probes)
+    return (time.perf_counter() - t0) / steps
+
+
+def batched_cpu_baseline(probs, dts, steps=2):
+    """The FP64 oracle on the host for the mixed workload, one instance per
+    core: one member of every shape stepped `steps` times in a spawn pool (all
+    shapes at once, one process each), each shape's time per step weighted by
+    its count in the mix, the total spread over the cores.  Sampled and
+    extrapolated to 5000-step solves."""
+    import multiprocessing as mp
+    by_shape = {}
+    for p, dt in zip(probs, dts):
+        key = (p.dims, tuple(p.n))
+        by_shape.setdefault(key, [p, dt, 0])[2] += 1
+    items = list(by_shape.values())
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(min(cores, len(items))) as pool:
+        per_step = pool.map(_oracle_member_step_time, [(p, dt, steps) for p, dt, _ in items])
+    wall = time.perf_counter() - t0
+    cpu_s_per_step = sum(t * cnt for t, (_, _, cnt) in zip(per_step, items))
+    pts = sum(p.n_total * cnt for p, _, cnt in items)
+    value = pts / (cpu_s_per_step / cores)
+    count = sum(cnt for _, _, cnt in items)
+    return {"value": value, "unit": "grid-point-steps/s", "cores": cores, "kind": "oracle", "extrapolated": True,
+            "solves_per_s_5000_steps": count / (cpu_s_per_step / cores * 5000), "host": host_cpu(),
+            "sample": f"one member of each of the {len(items)} shapes, {steps} oracle steps each, in a spawn pool "
+                      f"({wall:.1f} s wall); per-step times weighted by the shape counts of the {count}-solve mix "
+                      f"and divided over {cores} cores (one instance per core); FP64"}
+
+
+def peak_energy_errors(cases, local, stream, min_amp=1e-2):
+    """The accuracy gate of the batched and served forms.  Each case is
+    (label, problem, dt, steps taken, probe capacity, spectrum kwargs, FP32
+    peak energies): the FP32 member's probe-spectrum peak energies against
+    those of a lone FP64 solve of the same problem, dt and step count on the
+    device -- the FP64 path that the parity tests hold to 1e-10 of the FP64
+    oracle.  Peaks of at least min_amp of the largest are compared, each
+    against the nearest FP32 peak; returns the largest relative error per case."""
+    from paper_1805_03155_gb300 import spstd
+    out = {}
+    for label, p, dt, taken, cap, kw, E32 in cases:
+        ref = spstd.solver_for(p, precision=64, probe_capacity=cap, stream=stream, device=local, dt=dt)
+        ref.spstd_step(taken)
+        E64, A64 = ref.spstd_spectrum(-1, **kw)
+        ref.close()
+        keep = E64[A64 >= min_amp * A64.max()] if len(A64) else E64
+        if len(keep) == 0 or len(E32) == 0:
+            out[label] = None
+            continue
+        out[label] = float(max(np.min(np.abs(E32 - e)) / abs(e) for e in keep))
+    return out
+
+
+def batched_vs_plain(count=512, steps=400, plain_steps=40, precision=32, local=0, plain=True, check=True):
     """The mixed 512-solve workload (1D wells 128..8192, 2D oscillators
-    64^2..512^2, 3D oscillators 32^3 and 64^3; FP32 fields, FP64 reductions,
-    FR4): `steps` steps of every member through one batch (graph-replayed
+    64^2..512^2, 3D oscillators 32^3, 48^3, 64^3 and 96^3; FP32 fields, FP64
+    reductions, FR4): every member stepped through one batch (graph-replayed
     chunks, 1D members resident) vs the same members stepped one after another
     with spstd_step on one stream (plain).  Device-resident inputs; CUDA-event
-    time on the batch stream; solves/s is extrapolated to 5000-step solves."""
+    time on the batch stream.  The batch is timed over `steps` steps (after a
+    warm-up of as many, which captures its graph), the plain leg over
+    `plain_steps` steps per member; solves/s is extrapolated to the 5000-step
+    solves of the workload.  Accuracy gate: one member of every shape, after
+    the batch's 2 * steps steps, against a lone FP64 solve (peak_energy_errors)."""
     import torch
     from paper_1805_03155_gb300 import inputs, spstd
 
     probs = inputs.batch_mix(count, steps=steps)
     stream = torch.cuda.current_stream(local)
+    cap = 2 * steps + 8
     # both legs run every half-stage of every step (batches do not fuse step
     # boundaries), so they do the same arithmetic
-    solvers = [spstd.solver_for(p, precision=precision, probe_capacity=4 * steps + 8, stream=stream,
+    solvers = [spstd.solver_for(p, precision=precision, probe_capacity=cap, stream=stream,
                                 device=local, merge=False) for p in probs]
     pts = sum(p.n_total for p in probs)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
@@ -235,30 +333,32 @@ def batched_vs_plain(count=512, steps=20, precision=32, local=0, plain=True):
     plain_ms, plain_launches = float("nan"), 0
     if plain:
         for s in solvers:
-            s.spstd_step(steps)
+            s.spstd_step(plain_steps)
         torch.cuda.synchronize()
         ev[0].record(stream)
         for s in solvers:
-            s.spstd_step(steps)
+            s.spstd_step(plain_steps)
         ev[1].record(stream)
         torch.cuda.synchronize()
         plain_ms = ev[0].elapsed_time(ev[1])
-        plain_launches = sum(s.spstd_launch_count(steps) for s in solvers)
+        plain_launches = sum(s.spstd_launch_count(plain_steps) for s in solvers)
+        # back to the initial states (and empty probe rings) for the batch
+        for p, s in zip(probs, solvers):
+            s.spstd_set_state(p.psiR, p.psiI)
+        torch.cuda.synchronize()
     # batched
     b = spstd.Batch(count + 1, device=local, stream=stream)
     for s in solvers:
         b.spstd_batch_add(s)
 
     def timed_batch():
-        b.spstd_batch_step(steps)  # warm-up: captures the batch graph
-        torch.cuda.synchronize()
         ev[2].record(stream)
         b.spstd_batch_step(steps)
         ev[3].record(stream)
         torch.cuda.synchronize()
         return ev[2].elapsed_time(ev[3])
 
-    default_ms = timed_batch()
+    default_ms = timed_batch()  # also the warm-up: captures the batch graph
     # autotuned schedules per member shape (timed on the members' scratch fields)
     t_tune = time.perf_counter()
     b.spstd_batch_tune(reps=3)
@@ -268,25 +368,53 @@ def batched_vs_plain(count=512, steps=20, precision=32, local=0, plain=True):
              for d, n in shapes}
     batch_ms = timed_batch()
     launches = b.spstd_batch_launch_count(steps)
-    norms = [s.spstd_energy_norm()[0] for s in solvers[:: max(1, count // 16)]]
     b.close()
+    norms = []
+    for s in solvers[:: max(1, count // 16)]:
+        try:
+            norms.append(s.spstd_energy_norm()[0])
+        except spstd.SpstdError as e:
+            norms.append(getattr(e, "norm", float("nan")))
+    errs = {}
+    if check:
+        seen, cases = set(), []
+        for p, s in zip(probs, solvers):
+            key = "%dd:%s" % (p.dims, "x".join(str(v) for v in p.n[: p.dims]))
+            if key not in seen:
+                seen.add(key)
+                kw = dict(max_peaks=8, thresh=1e-3, phase_correct=True)
+                cases.append((key, p, s.spstd_get_dt(), 2 * steps, cap, kw, s.spstd_spectrum(-1, **kw)[0]))
+        errs = peak_energy_errors(cases, local, stream)
+    dts = [s.spstd_get_dt() for s in solvers]
     for s in solvers:
         s.close()
+    worst = max((v for v in errs.values() if v is not None), default=None)
     return {
         "workload": f"batch_mix_{count}",
         "members": count,
         "grid_points": pts,
+        "shapes3d": sorted({p.n[0] for p in probs if p.dims == 3}),
         "steps": steps,
-        "batched": {"value": pts * steps / (batch_ms * 1e-3), "ms": batch_ms,
-                    "solves_per_s_5000_steps": count / (batch_ms * 1e-3 * 5000 / steps), "gpu_launches": launches,
-                    "schedules": tuned, "tune_s": tune_s,
+        "batched": {"value": pts * steps / (batch_ms * 1e-3), "ms": batch_ms, "steps_timed": steps,
+                    "solves_per_s_5000_steps": count / (batch_ms * 1e-3 * 5000 / steps),
+                    "extrapolated_from": f"{steps} steps of every member in {batch_ms:.0f} ms",
+                    "gpu_launches": launches, "schedules": tuned, "tune_s": tune_s,
                     "default_schedule_ms": default_ms,
                     "default_schedule_value": pts * steps / (default_ms * 1e-3)},
-        "plain": {"value": pts * steps / (plain_ms * 1e-3), "ms": plain_ms,
-                  "solves_per_s_5000_steps": count / (plain_ms * 1e-3 * 5000 / steps), "gpu_launches": plain_launches},
-        "speedup": plain_ms / batch_ms,
+        "plain": {"value": pts * plain_steps / (plain_ms * 1e-3), "ms": plain_ms, "steps_timed": plain_steps,
+                  "solves_per_s_5000_steps": count / (plain_ms * 1e-3 * 5000 / plain_steps),
+                  "extrapolated_from": f"{plain_steps} steps of every member, one after another, in {plain_ms:.0f} ms",
+                  "gpu_launches": plain_launches},
+        "speedup": (plain_ms / plain_steps) / (batch_ms / steps),
         "unit": "grid-point-steps/s",
         "norm_drift_max": float(max(abs(n - 1.0) for n in norms)),
+        "energy_rel_err_max": worst,
+        "energy_rel_err": errs,
+        "energy_check": "one member per shape after the batch's %d steps: probe-spectrum peak energies (>= 1e-2 of "
+                        "the largest peak, dispersion-corrected) vs a lone FP64 device solve of the same member "
+                        "(the FP64 path matches the FP64 oracle to 1e-10 in the parity tests)" % (2 * steps),
+        "_dts": dts,
+        "_probs": probs,
     }
 
 
@@ -325,7 +453,19 @@ def serving(rate=200.0, duration=1.0, steps=1000, chunk=500, precision=32, seed=
     lat = srv.latencies()
     pts = sum(p.n_total for p in probs) * steps
     chunks = srv.chunks
+    diverged = sum(1 for r in srv.done if r.result.get("status") != "ok")
+    # accuracy gate: the first finished request of every shape against a lone FP64 solve
+    seen, cases = set(), []
+    for r in sorted(srv.done, key=lambda r: r.rid):
+        p = r.problem
+        key = "%dd:%s" % (p.dims, "x".join(str(v) for v in p.n[: p.dims]))
+        if key in seen or "E" not in r.result:
+            continue
+        seen.add(key)
+        cases.append((key, p, r.result["dt"], r.steps, max(1, r.steps), dict(max_peaks=4), r.result["E"]))
     srv.close()
+    errs = peak_energy_errors(cases, local, torch.cuda.current_stream(local))
+    worst = max((v for v in errs.values() if v is not None), default=None)
     # plain: the same requests one at a time, each stepped alone
     torch.cuda.synchronize()
     t1 = time.perf_counter()
@@ -350,7 +490,57 @@ def serving(rate=200.0, duration=1.0, steps=1000, chunk=500, precision=32, seed=
         "plain": {"solves_per_s": n / plain_wall, "grid_point_steps_per_s": pts / plain_wall,
                   "p50_s": float(np.percentile(plain_lat, 50)), "p99_s": float(np.percentile(plain_lat, 99)),
                   "wall_s": plain_wall},
+        "diverged_requests": diverged,
+        "energy_rel_err_max": worst,
+        "energy_rel_err": errs,
+        "energy_check": "the first finished request of every shape: probe-spectrum peak energies (>= 1e-2 of the "
+                        "largest peak) vs a lone FP64 device solve of the same request (the FP64 path matches the "
+                        "FP64 oracle to 1e-10 in the parity tests)",
+        "latency_note": "wall clock from arrival to retirement, host-side admission included; the arrival rate "
+                        "exceeds the service rate, so the latency is mostly queueing",
     }
+
+
+def general_v_leg(steps, warmup, peak, local=0):
+    """The same 256^3 workload with a potential that does not separate: the
+    oscillator plus 0.01 x y.  Eq. 16's V term then needs the V field at every
+    point, so the x pass reads it (16 B/pt) instead of rebuilding V from two
+    tables.  Timed like the main line (one call of `steps` steps, CUDA events
+    on the solver's stream)."""
+    import dataclasses
+
+    import torch
+    from paper_1805_03155_gb300 import inputs, spstd
+
+    p = inputs.aniso_ho_3d(steps=steps)
+    x, y, _ = p.coords()
+    nx, ny, nz = p.n
+    V = (p.V.reshape(nz, ny, nx) + 0.01 * y[None, :, None] * x[None, None, :]).ravel()
+    p = dataclasses.replace(p, V=V)
+    stream = torch.cuda.Stream(device=local)
+    s = spstd.solver_for(p, precision=32, probe_capacity=warmup + steps + 8, stream=stream, device=local)
+    sep = s.spstd_potential_separable()
+    s.spstd_step(warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.spstd_step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    prof = s.spstd_profile_steps(4)
+    s.close()
+    N = p.n_total
+    xms = prof["x_pass"][0] / max(1, prof["x_pass"][1])
+    hs = (steps * 10 + 1) / steps  # SUZUKI6 with fused step boundaries: 10 half-stages a step within a call
+    half_ms = ms / steps / hs
+    return {"workload": "aniso_ho_3d_256 with V + 0.01 x y (not separable)", "v_separable": sep,
+            "value": N * steps / (ms * 1e-3), "unit": "grid-point-steps/s", "ms_per_step": ms / steps,
+            "steps": steps, "x_pass_ms": xms, "x_pass_frac": 16 * N / (xms * 1e-3) / 1e9 / peak,
+            "half_stage_ms_in_graph": half_ms,
+            "half_stage_frac": 16 * N / (half_ms * 1e-3) / 1e9 / peak,
+            "what": "x pass fraction: its 16 B/pt (src, V, dst read, dst written) over its event-timed launch; "
+                    "half-stage fraction: 16 B/pt over the in-graph step time per applied half-stage"}
 
 
 def run_reference(args):
@@ -396,14 +586,19 @@ def run_reference(args):
     value = S * args.steps / (h * t)
     what = (f"each step: the oracle's x, y and z line transforms over {side * side} full-length lines per axis "
             f"({S} grid points, the per-point work of one half-stage) plus the V term and axpy, scaled by "
-            f"{h} half-stages per step; single thread, FP64")
+            f"{h} half-stages per step; single thread, FP64; the value is extrapolated from this sample to the "
+            f"full {problem.n_total}-point grid")
     out = {"impl": "reference", "metric": "grid-point-steps/s", "value": value, "unit": "grid-point-steps/s",
            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-           "ms_per_step": 1e3 * t * h * (problem.n_total / S) / args.steps, "higher_is_better": True,
+           "ms_per_step": 1e3 * t / args.steps,
+           "ms_per_step_is": f"the measured time of one timed sample step ({S} points, one half-stage's work); a "
+                             f"full {problem.n_total}-point step of {h} half-stages would take "
+                             f"{1e3 * t * h * (problem.n_total / S) / args.steps:.0f} ms (extrapolated)",
+           "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": args.workload, "grid": list(problem.n), "integrator": problem.integrator},
            "cpu_baseline": {"value": value, "unit": "grid-point-steps/s", "cores": 1, "kind": "oracle",
-                            "sample": what},
+                            "extrapolated": True, "host": host_cpu(), "sample": what},
            "e2e": {"value": value, "unit": "grid-point-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
     return 0
@@ -418,6 +613,7 @@ def main():
     ap.add_argument("--workload", default="aniso_ho_3d_256", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-plain and serving legs")
+    ap.add_argument("--no-general-v", action="store_true", help="skip the leg with a potential that does not separate")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the default pass schedules (no autotuning launches; for profiler launch lists)")
     ap.add_argument("--batch-only", action="store_true",
@@ -430,9 +626,9 @@ def main():
     if args.batch_only:
         import torch
         torch.cuda.set_device(0)
-        r = batched_vs_plain(plain=False)
+        r = batched_vs_plain(plain=False, check=False)
         print(json.dumps({"batch_only": True, **{k: r[k] for k in ("workload", "members", "grid_points", "steps",
-                                                                    "batched", "unit")}}))
+                                                                    "shapes3d", "batched", "unit")}}))
         return 0
 
     import torch
@@ -530,6 +726,9 @@ def main():
     nv, ev = s.spstd_energy_norm()
     cc, dd = s.spstd_get_coefficients()
     coeff_halfstages = int(np.count_nonzero(cc) + np.count_nonzero(dd))
+    # half-stages the timed call applied per step (fused step boundaries: K (h - 1) + 1 in K steps)
+    half_applied = ((args.steps * (coeff_halfstages - 1) + 1) / args.steps if half_stages < coeff_halfstages
+                    else coeff_halfstages)
 
     # ---- the other rows of the path, each called as a user would ------------
     # a7: FP64 norm and energy (H applied to both fields, two fixed-order
@@ -575,7 +774,17 @@ def main():
             "step_floor_bytes": (3 if v_sep else 4) * es * N * coeff_halfstages,
             "step_floor_frac": ((3 if v_sep else 4) * es * N * coeff_halfstages) / (ms / args.steps * 1e-3) / 1e9
                                / peak,
+            # the unit of the measurement definition: 16 B (FP32) per grid point per half-stage --
+            # read src, V, dst and write dst -- whatever the kernels actually move
+            "half_stage_ms_in_graph": ms / args.steps / half_applied,
+            "half_stage_frac": 4 * es * N / (ms / args.steps / half_applied * 1e-3) / 1e9 / peak,
+            "step_frac": 4 * es * N * coeff_halfstages / (ms / args.steps * 1e-3) / 1e9 / peak,
+            "fractions_are": "of measured hbm_gbs; frac: the dominant kernel's own algorithmic bytes per launch; "
+                             "half_stage_frac: 4 x (field bytes) per point over the in-graph time of one applied "
+                             "half-stage; step_frac: the same over the step (h half-stages of the integrator)",
             "per_kernel_ms": {k: v[0] / v[1] for k, v in kinds.items()},
+            "per_kernel_ms_are": "per launch, each launch timed alone by an event pair outside the captured "
+                                 "graph (spstd_profile_steps); their per-step sum exceeds the in-graph step time",
             "per_kernel_share": {k: v[0] / sum(x[0] for x in kinds.values()) for k, v in kinds.items()},
         }
         if 3 * N * es <= L2_BYTES:
@@ -616,8 +825,7 @@ def main():
                 "half_stages_per_step": coeff_halfstages,
                 # the timed call of K steps applies K (h - 1) + 1 half-stages when step
                 # boundaries are fused, K h otherwise
-                "half_stages_applied_per_step": ((args.steps * (coeff_halfstages - 1) + 1) / args.steps
-                                                 if half_stages < coeff_halfstages else coeff_halfstages),
+                "half_stages_applied_per_step": half_applied,
                 "merged_step_boundaries": bool(half_stages < coeff_halfstages),
                 "fields": "fp32" if prec == 32 else "fp64",
                 "reductions": "fp64",
@@ -645,8 +853,14 @@ def main():
             "check": {"norm_after": nv, "energy_after": ev},
             "rows": rows,
         }
+        if args.workload == "aniso_ho_3d_256" and not args.no_general_v:
+            out["general_v"] = general_v_leg(args.steps, args.warmup, peak, local=local)
         if not args.no_batch:
-            out["batched_vs_plain"] = batched_vs_plain(local=local)
+            bvp = batched_vs_plain(local=local)
+            probs, dts = bvp.pop("_probs"), bvp.pop("_dts")
+            if not args.no_cpu_baseline:
+                bvp["cpu_baseline"] = batched_cpu_baseline(probs, dts)
+            out["batched_vs_plain"] = bvp
             out["serving"] = serving(local=local)
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(problem)
