@@ -1516,7 +1516,8 @@ spstd_status spstd_set_potential(spstd_ctx *ctx, const double *V)
     // kernel arguments name the tables (or not): replayed graphs are rebuilt
     drop_graph(ctx);
     ctx->vsep = false;
-    if (ctx->cfg.precision == 32 && ctx->tma[0]) {
+    // the table form of the x pass exists for power-of-two lines
+    if (ctx->cfg.precision == 32 && ctx->tma[0] && is_pow2(ctx->cfg.n[0])) {
         const int64_t n0 = ctx->cfg.n[0], rows = ctx->cfg.n[1] * ctx->cfg.n[2];
         std::vector<float> vx, vyz;
         if (separable_tables(V, n0, rows, vsep_rows_padded(rows), vx, vyz)) {

@@ -45,25 +45,40 @@ cudaError_t prepare_pass_tma(int axis, int N);
 
 // ---------------------------------------------------------------------------
 // Reduce-add passes (pass_tmared.cuh), the default for FP32 lines of 32..512
-// points: the destination is accumulated at L2 by a TMA reduce-add.
+// points and of 48 and 96 points (3 * 2^k: a radix-3 first stage): the
+// destination is accumulated at L2 by a TMA reduce-add.
 // ---------------------------------------------------------------------------
-constexpr bool tmared_eligible(int64_t N) { return N == 32 || N == 64 || N == 128 || N == 256 || N == 512; }
+constexpr bool tmared_eligible(int64_t N)
+{
+    return N == 32 || N == 64 || N == 128 || N == 256 || N == 512 || N == 48 || N == 96;
+}
+// Complex points per thread: 16, or 12 for N = 3 * 2^k.
+constexpr int tmared_e(int N) { return N % 3 ? 16 : 12; }
+// Floats of one x tile or strided tile part: 4096 (16 KB) for power-of-two
+// lines, 3072 (12 KB) for 3 * 2^k lines, so that an x block has 128 threads
+// and a strided block of K planes 256.
+constexpr int tmared_unit(int N) { return N % 3 ? 4096 : 3072; }
 // x pass: rows per tile (the box height of its x-view maps).
-constexpr int tmared_rows_x(int N) { return 4096 / N; }
+constexpr int tmared_rows_x(int N) { return tmared_unit(N) / N; }
 // Strided pass over N points along y or z with nx points along x: column
-// pairs per tile, at most 64 (its y/z-view maps' box is 2P columns wide); 0
-// if nx < 16.
+// pairs per tile, at most 64 (its y/z-view maps' box is 2P columns wide) and
+// at least 8; the largest such P whose 2P columns divide nx, else the largest
+// with 2P <= nx (the last tile across x then runs past the grid: its loads
+// read zeros there and its reduce-add skips those columns); 0 if nx < 16.
 constexpr int tmared_pairs(int N, int64_t nx)
 {
-    int P = 4096 / N < 64 ? 4096 / N : 64;
+    int P = tmared_unit(N) / N < 64 ? tmared_unit(N) / N : 64;
     while (P > 8 && 2 * (int64_t)P > nx) P /= 2;
+    int Q = P;
+    while (Q > 8 && nx % (2 * Q) != 0) Q /= 2;
+    if (nx % (2 * Q) == 0) P = Q;
     return nx >= 16 ? P : 0;
 }
 // Strided pass: planes of the outer axis per tile -- enough for 256 threads
 // per block (tmared_max_planes), or 1 when the outer axis is shorter than that.
 constexpr int tmared_max_planes(int N, int P)
 {
-    return P > 0 && 256 / (P * (N / 16)) > 1 ? 256 / (P * (N / 16)) : 1;
+    return P > 0 && 256 / (P * (N / tmared_e(N))) > 1 ? 256 / (P * (N / tmared_e(N))) : 1;
 }
 constexpr int tmared_planes(int N, int P, int64_t outer)
 {

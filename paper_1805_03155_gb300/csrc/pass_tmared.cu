@@ -9,9 +9,9 @@
 namespace spstd {
 namespace {
 
-// Complex points per thread.  Measured at 256^3: E = 8 (256-thread x blocks,
-// 16 warps per SM) takes 0.054 ms per x pass against 0.047 ms for E = 16.
-constexpr int kRedE = 16;
+// Complex points per thread: tmared_e(N), 16 for power-of-two lines.
+// Measured at 256^3: E = 8 (256-thread x blocks, 16 warps per SM) takes
+// 0.054 ms per x pass against 0.047 ms for E = 16.
 
 // Launch with programmatic stream serialisation: the kernel may start while
 // the previous work on the stream finishes; it waits for it (griddepcontrol)
@@ -33,7 +33,7 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
     return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
-template <int N, bool BATCH, bool VSEP = false, int EX = kRedE>
+template <int N, bool BATCH, bool VSEP = false, int EX = tmared_e(N)>
 cudaError_t red_x(const CUtensorMap *ms, const CUtensorMap *mv, const CUtensorMap *md, const TmaPassArgs *a,
                   const TmaBatchArgs *ba, cudaStream_t s)
 {
@@ -55,9 +55,10 @@ template <int N, int P, int K, bool BATCH>
 cudaError_t red_s(const CUtensorMap *ms, const CUtensorMap *md, const TmaPassArgs *a, const TmaBatchArgs *ba,
                   cudaStream_t s)
 {
-    using G = SRed<N, kRedE, P, K, BATCH>;
+    constexpr int EX = tmared_e(N);
+    using G = SRed<N, EX, P, K, BATCH>;
     int grid = 0;
-    cudaError_t e = persistent_grid<spass_tmared_kernel<N, kRedE, P, K, BATCH>>(G::THREADS, G::SMEM, &grid);
+    cudaError_t e = persistent_grid<spass_tmared_kernel<N, EX, P, K, BATCH>>(G::THREADS, G::SMEM, &grid);
     if (e != cudaSuccess || !(BATCH ? (const void *)ba : (const void *)a)) return e;
     const int total = BATCH ? ba->members * ba->tiles : a->n_tiles;
     if (total < grid) grid = total;
@@ -65,7 +66,7 @@ cudaError_t red_s(const CUtensorMap *ms, const CUtensorMap *md, const TmaPassArg
     const CUtensorMap none{};
     const TmaPassArgs a0{};
     const TmaBatchArgs b0{};
-    return launch_pdl(spass_tmared_kernel<N, kRedE, P, K, BATCH>, dim3(grid), dim3(P, G::TT, K), G::SMEM, s,
+    return launch_pdl(spass_tmared_kernel<N, EX, P, K, BATCH>, dim3(grid), dim3(P, G::TT, K), G::SMEM, s,
                       BATCH ? none : *ms, BATCH ? none : *md, BATCH ? a0 : *a, BATCH ? *ba : b0);
 }
 
@@ -87,16 +88,17 @@ template <int N, bool BATCH>
 cudaError_t red_s_p(int P, int K, const CUtensorMap *ms, const CUtensorMap *md, const TmaPassArgs *a,
                     const TmaBatchArgs *ba, cudaStream_t s)
 {
+    constexpr int PM = tmared_unit(N) / N;  // largest P of this line length
     switch (P) {
     case 8: return red_s_k<N, 8, BATCH>(K, ms, md, a, ba, s);
     case 16:
-        if constexpr (4096 / N >= 16) return red_s_k<N, 16, BATCH>(K, ms, md, a, ba, s);
+        if constexpr (PM >= 16) return red_s_k<N, 16, BATCH>(K, ms, md, a, ba, s);
         break;
     case 32:
-        if constexpr (4096 / N >= 32) return red_s_k<N, 32, BATCH>(K, ms, md, a, ba, s);
+        if constexpr (PM >= 32) return red_s_k<N, 32, BATCH>(K, ms, md, a, ba, s);
         break;
     case 64:
-        if constexpr (4096 / N >= 64) return red_s_k<N, 64, BATCH>(K, ms, md, a, ba, s);
+        if constexpr (PM >= 64) return red_s_k<N, 64, BATCH>(K, ms, md, a, ba, s);
         break;
     default: break;
     }
@@ -112,8 +114,15 @@ cudaError_t red_x_n(int N, const CUtensorMap *ms, const CUtensorMap *mv, const C
     case 64: return red_x<64, BATCH, VSEP>(ms, mv, md, a, ba, s);
     case 128: return red_x<128, BATCH, VSEP>(ms, mv, md, a, ba, s);
     case 256: return red_x<256, BATCH, VSEP>(ms, mv, md, a, ba, s);
-    default: return red_x<512, BATCH, VSEP>(ms, mv, md, a, ba, s);
+    case 512: return red_x<512, BATCH, VSEP>(ms, mv, md, a, ba, s);
+    default: break;
     }
+    // 3 * 2^k lines read the V field (no separable table form)
+    if constexpr (!VSEP) {
+        if (N == 48) return red_x<48, BATCH, false>(ms, mv, md, a, ba, s);
+        if (N == 96) return red_x<96, BATCH, false>(ms, mv, md, a, ba, s);
+    }
+    return cudaErrorInvalidValue;
 }
 
 template <bool BATCH>
@@ -125,10 +134,13 @@ cudaError_t red_any(int axis, int N, int64_t nx, int K, const CUtensorMap *ms, c
         if (nx != N) return cudaErrorInvalidValue;
         if constexpr (!BATCH) {
             // a single grid with a separable potential takes the table form; the
-            // set-up call (no args) prepares both forms
+            // set-up call (no args) prepares both forms (the table form exists
+            // for power-of-two lines)
             if (!a) {
-                const cudaError_t e = red_x_n<false, true>(N, ms, mv, md, a, ba, s);
-                if (e != cudaSuccess) return e;
+                if (N % 3) {
+                    const cudaError_t e = red_x_n<false, true>(N, ms, mv, md, a, ba, s);
+                    if (e != cudaSuccess) return e;
+                }
             } else if (a->vyz) {
                 if (!a->vx) return cudaErrorInvalidValue;
                 return red_x_n<false, true>(N, ms, mv, md, a, ba, s);
@@ -142,7 +154,10 @@ cudaError_t red_any(int axis, int N, int64_t nx, int K, const CUtensorMap *ms, c
     case 64: return red_s_p<64, BATCH>(P, K, ms, md, a, ba, s);
     case 128: return red_s_p<128, BATCH>(P, K, ms, md, a, ba, s);
     case 256: return red_s_p<256, BATCH>(P, K, ms, md, a, ba, s);
-    default: return red_s_p<512, BATCH>(P, K, ms, md, a, ba, s);
+    case 512: return red_s_p<512, BATCH>(P, K, ms, md, a, ba, s);
+    case 48: return red_s_p<48, BATCH>(P, K, ms, md, a, ba, s);
+    case 96: return red_s_p<96, BATCH>(P, K, ms, md, a, ba, s);
+    default: return cudaErrorInvalidValue;
     }
 }
 

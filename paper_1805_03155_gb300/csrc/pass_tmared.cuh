@@ -176,10 +176,14 @@ __device__ __forceinline__ void red_timeout_exit(uint64_t *full, int k, int nk, 
 // element t + e N/E) and leaves it in the src tile.  No block barrier inside:
 // the rows of a line pair belong to its N/E threads (within one warp) alone.
 //
-// Rows are multiples of 32 floats apart, so the G = 32/(N/E) line pairs of a
+// Rows are multiples of 32 floats apart (or, for 48-point lines, rows of two
+// line pairs differ by a multiple of 32), so the G = 32/(N/E) line pairs of a
 // warp would read and write the same banks.  Line pair g of its warp
-// therefore moves element t + TT (e ^ g) through register slot e and the
-// registers are permuted into the FFT's natural order (and back) in between.
+// therefore moves element t + TT (e ^ g') through register slot e, g' = g mod
+// GP with GP = min(G, the largest power of two dividing E), and the registers
+// are permuted into the FFT's natural order (and back) in between.  (For E =
+// 12, GP = 4: the XOR stays inside each aligned group of four slots; the 8
+// line pairs of a 48-point warp then meet in pairs on a bank.)
 // The V term stays in registers (w) from the loads to the final write.
 // The two halves of an x tile, so that a fused kernel can run other work
 // between them.  Load: this thread's elements of rows 2l, 2l+1 into v (in
@@ -191,6 +195,7 @@ struct XTile {
     static constexpr int TT = N / E;
     static_assert(TT <= 32, "a line's threads must share one warp (the exchange uses warp barriers)");
     static constexpr int G = TT >= 32 ? 1 : 32 / TT;
+    static constexpr int GP = G < p2div(E) ? G : p2div(E);
     float2 v[E], w[E];
     int t, l, g;
 
@@ -200,7 +205,7 @@ struct XTile {
     {
         t = t_;
         l = l_;
-        g = l & (G - 1);
+        g = l & (GP - 1);
         const int r0 = 2 * l, r1 = 2 * l + 1;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
@@ -222,7 +227,7 @@ struct XTile {
     {
         t = t_;
         l = l_;
-        g = l & (G - 1);
+        g = l & (GP - 1);
         const int r0 = 2 * l, r1 = 2 * l + 1;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
@@ -237,8 +242,10 @@ struct XTile {
     __device__ __forceinline__ void finish(float *src, const float (&mr)[E], const float2 *tw, const float *yadd)
     {
         const int r0 = 2 * l, r1 = 2 * l + 1;
-        xor_permute<E, G>(v, g);
-        XcLineR<N> xc{reinterpret_cast<float2 *>(src) + l * N, TT < 16 ? (g & (16 / TT - 1)) * TT : 0};
+        xor_permute<E, GP>(v, g);
+        // exchange swizzle: line pairs of a warp on different bank pairs
+        const int gx = l & (G - 1);
+        XcLineR<N> xc{reinterpret_cast<float2 *>(src) + l * N, TT < 16 ? (gx & (16 / TT - 1)) * TT : 0};
         fft_line<float, N, E, false>(v, t, xc, tw);
 #pragma unroll
         for (int e = 0; e < E; ++e) {
@@ -246,7 +253,7 @@ struct XTile {
             v[e].y *= mr[e];
         }
         fft_line<float, N, E, true>(v, t, xc, tw);
-        xor_permute<E, G>(v, g);
+        xor_permute<E, GP>(v, g);
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             const int i = pos(e);

@@ -144,3 +144,24 @@ def test_aniso_256_graph_replay_is_bitwise(aniso2):
         out.append((R, Im, z))
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
     assert np.array_equal(out[0][2], out[1][2])
+
+
+@pytest.mark.slow
+def test_ho_3d_64_discrete_levels_long_window():
+    """The 64^3 oscillator's levels against the closed form omega (n + 3/2),
+    which the discrete spectral operator reproduces (the 64-point 1D factor's
+    eigenvalues equal n + 1/2 to about 1e-13): FP64, a window ten times the
+    workload's (T = 236, levels 38 bins apart, so Hann leakage between them
+    is negligible), peaks dispersion-corrected (Eq. 23/25: the integrator's
+    angle inverted), every peak of at least 1e-2 of the largest to 1e-6
+    relative."""
+    p = inputs.ho_3d(steps=100000)
+    s = gpu_solver(p, 64, cap=p.steps)
+    s.spstd_step(p.steps)
+    E, A = s.spstd_spectrum(-1, max_peaks=16, thresh=1e-3, phase_correct=True)
+    s.close()
+    strong = E[A >= 1e-2 * A.max()]
+    assert len(strong) >= 4
+    rel = np.array([abs(e - (np.round(e - 1.5) + 1.5)) / e for e in strong])
+    print("ho_3d_64 FP64 T=236 levels", np.round(strong, 9), "rel err vs n + 3/2", rel)
+    assert np.max(rel) <= 1e-6
