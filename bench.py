@@ -283,30 +283,91 @@ def batched_cpu_baseline(probs, dts, steps=2):
                       f"and divided over {cores} cores (one instance per core); FP64"}
 
 
-def peak_energy_errors(cases, local, stream, min_amp=1e-2):
+def accuracy_vs_fp64(cases, local, stream, min_amp=1e-2, sep_bins=4.0, max_bin=0.5):
     """The accuracy gate of the batched and served forms.  Each case is
-    (label, problem, dt, steps taken, probe capacity, spectrum kwargs, FP32
-    peak energies): the FP32 member's probe-spectrum peak energies against
-    those of a lone FP64 solve of the same problem, dt and step count on the
+    (label, problem, dt, steps, probe capacity, FP32 peak energies, FP32
+    probe series or None, FP32 state (psi_R, psi_I) or None).  The reference
+    is a lone FP64 solve of the same problem, dt and step count on the
     device -- the FP64 path that the parity tests hold to 1e-10 of the FP64
-    oracle.  Peaks of at least min_amp of the largest are compared, each
-    against the nearest FP32 peak; returns the largest relative error per case."""
+    oracle.
+    Energies: the dispersion-corrected peaks of the FP64 probe spectrum that
+    are levels the window resolves -- at least min_amp of the largest peak, at
+    least sep_bins Hann bins (2 pi hbar / (M dt), M samples) from every other
+    peak and from zero, in a window whose bin is at most max_bin (the levels of
+    these wells and oscillators lie about one energy unit apart) -- each
+    against the nearest FP32 peak; None where the window resolves no level.
+    State: relative L2 distance of the FP32 fields from the FP64 ones.
+    Series: the largest deviation of the FP32 probe series, relative to the
+    FP64 series' largest value (probes may sit where the state is small)."""
     from paper_1805_03155_gb300 import spstd
     out = {}
-    for label, p, dt, taken, cap, kw, E32 in cases:
+    kw = dict(max_peaks=16, thresh=1e-3, phase_correct=True)
+    for label, p, dt, steps, cap, E32, z32, st32 in cases:
         ref = spstd.solver_for(p, precision=64, probe_capacity=cap, stream=stream, device=local, dt=dt)
-        ref.spstd_step(taken)
+        ref.spstd_step(steps)
         E64, A64 = ref.spstd_spectrum(-1, **kw)
+        z64 = np.array([ref.spstd_probe(q) for q in range(len(p.probes))]) if z32 is not None else None
+        st64 = ref.spstd_get_state() if st32 is not None else None
         ref.close()
-        keep = E64[A64 >= min_amp * A64.max()] if len(A64) else E64
-        if len(keep) == 0 or len(E32) == 0:
-            out[label] = None
-            continue
-        out[label] = float(max(np.min(np.abs(E32 - e)) / abs(e) for e in keep))
+        M = min(steps, cap)
+        bin_e = 2 * np.pi * p.hbar / (M * dt)
+        resolved = [e for e, a in zip(E64, A64)
+                    if bin_e <= max_bin and a >= min_amp * A64.max() and e >= sep_bins * bin_e
+                    and all(abs(e - f) >= sep_bins * bin_e for f in E64 if f != e)]
+        err = (float(max(np.min(np.abs(np.asarray(E32) - e)) / abs(e) for e in resolved))
+               if resolved and len(E32) else None)
+        ser = float(np.max(np.abs(z32 - z64)) / np.max(np.abs(z64))) if z64 is not None else None
+        sterr = None
+        if st64 is not None:
+            num = np.sum((st32[0] - st64[0]) ** 2 + (st32[1] - st64[1]) ** 2)
+            sterr = float(np.sqrt(num / np.sum(st64[0] ** 2 + st64[1] ** 2)))
+        out[label] = {"energy_rel_err": err, "resolved_peaks": len(resolved), "bin": float(bin_e),
+                      "state_rel_l2": sterr, "series_rel_err": ser, "steps": int(steps)}
     return out
 
 
-def batched_vs_plain(count=512, steps=400, plain_steps=40, precision=32, local=0, plain=True, check=True):
+def accuracy_batch(probs, local, stream, steps=10000, precision=32):
+    """One member of every shape of the mix, stepped `steps` times in a batch
+    of their own (twice the workload's 5000, so that the window of most
+    members resolves their levels), against lone FP64 solves
+    (accuracy_vs_fp64)."""
+    from paper_1805_03155_gb300 import spstd
+    seen, sample = set(), []
+    for p in probs:
+        key = "%dd:%s" % (p.dims, "x".join(str(v) for v in p.n[: p.dims]))
+        if key not in seen:
+            seen.add(key)
+            sample.append((key, p))
+    solvers = [spstd.solver_for(p, precision=precision, probe_capacity=steps, stream=stream, device=local,
+                                merge=False) for _, p in sample]
+    b = spstd.Batch(len(solvers) + 1, device=local, stream=stream)
+    for s in solvers:
+        b.spstd_batch_add(s)
+    b.spstd_batch_step(steps)
+    b.spstd_batch_sync()
+    b.close()
+    kw = dict(max_peaks=16, thresh=1e-3, phase_correct=True)
+    cases = []
+    for (key, p), s in zip(sample, solvers):
+        z = np.array([s.spstd_probe(q) for q in range(len(p.probes))])
+        cases.append((key, p, s.spstd_get_dt(), steps, steps, s.spstd_spectrum(-1, **kw)[0], z,
+                      s.spstd_get_state()))
+    for s in solvers:
+        s.close()
+    return accuracy_vs_fp64(cases, local, stream)
+
+
+def gate_summary(acc):
+    e = [v["energy_rel_err"] for v in acc.values() if v["energy_rel_err"] is not None]
+    z = [v["series_rel_err"] for v in acc.values() if v["series_rel_err"] is not None]
+    st = [v["state_rel_l2"] for v in acc.values() if v["state_rel_l2"] is not None]
+    return {"energy_rel_err_max": max(e) if e else None,
+            "shapes_with_resolved_levels": len(e), "shapes": len(acc),
+            "state_rel_l2_max": max(st) if st else None,
+            "series_rel_err_max": max(z) if z else None}
+
+
+def batched_vs_plain(count=512, steps=800, plain_steps=40, precision=32, local=0, plain=True, check=True):
     """The mixed 512-solve workload (1D wells 128..8192, 2D oscillators
     64^2..512^2, 3D oscillators 32^3, 48^3, 64^3 and 96^3; FP32 fields, FP64
     reductions, FR4): every member stepped through one batch (graph-replayed
@@ -315,8 +376,8 @@ def batched_vs_plain(count=512, steps=400, plain_steps=40, precision=32, local=0
     time on the batch stream.  The batch is timed over `steps` steps (after a
     warm-up of as many, which captures its graph), the plain leg over
     `plain_steps` steps per member; solves/s is extrapolated to the 5000-step
-    solves of the workload.  Accuracy gate: one member of every shape, after
-    the batch's 2 * steps steps, against a lone FP64 solve (peak_energy_errors)."""
+    solves of the workload.  Accuracy gate: one member of every shape,
+    batched for 10000 steps, against lone FP64 solves (accuracy_batch)."""
     import torch
     from paper_1805_03155_gb300 import inputs, spstd
 
@@ -375,20 +436,10 @@ def batched_vs_plain(count=512, steps=400, plain_steps=40, precision=32, local=0
             norms.append(s.spstd_energy_norm()[0])
         except spstd.SpstdError as e:
             norms.append(getattr(e, "norm", float("nan")))
-    errs = {}
-    if check:
-        seen, cases = set(), []
-        for p, s in zip(probs, solvers):
-            key = "%dd:%s" % (p.dims, "x".join(str(v) for v in p.n[: p.dims]))
-            if key not in seen:
-                seen.add(key)
-                kw = dict(max_peaks=8, thresh=1e-3, phase_correct=True)
-                cases.append((key, p, s.spstd_get_dt(), 2 * steps, cap, kw, s.spstd_spectrum(-1, **kw)[0]))
-        errs = peak_energy_errors(cases, local, stream)
     dts = [s.spstd_get_dt() for s in solvers]
     for s in solvers:
         s.close()
-    worst = max((v for v in errs.values() if v is not None), default=None)
+    acc = accuracy_batch(probs, local, stream) if check else {}
     return {
         "workload": f"batch_mix_{count}",
         "members": count,
@@ -408,11 +459,14 @@ def batched_vs_plain(count=512, steps=400, plain_steps=40, precision=32, local=0
         "speedup": (plain_ms / plain_steps) / (batch_ms / steps),
         "unit": "grid-point-steps/s",
         "norm_drift_max": float(max(abs(n - 1.0) for n in norms)),
-        "energy_rel_err_max": worst,
-        "energy_rel_err": errs,
-        "energy_check": "one member per shape after the batch's %d steps: probe-spectrum peak energies (>= 1e-2 of "
-                        "the largest peak, dispersion-corrected) vs a lone FP64 device solve of the same member "
-                        "(the FP64 path matches the FP64 oracle to 1e-10 in the parity tests)" % (2 * steps),
+        **(gate_summary(acc) if acc else {}),
+        "accuracy": acc,
+        "accuracy_check": "one member per shape batched for 10000 steps vs a lone FP64 device solve of the same "
+                          "member (the FP64 path matches the FP64 oracle to 1e-10 in the parity tests): the "
+                          "dispersion-corrected probe-spectrum energies of the levels the window resolves (peaks "
+                          ">= 1e-2 of the largest, >= 4 Hann bins from their neighbours, bin <= 0.5; None where "
+                          "the window resolves no level: fine grids take small dt), the state's relative L2 "
+                          "distance, and the probe series",
         "_dts": dts,
         "_probs": probs,
     }
@@ -442,7 +496,7 @@ def serving(rate=200.0, duration=1.0, steps=1000, chunk=500, precision=32, seed=
             p = mix[i]
         probs.append(p)
     srv = serve.Server(hbm_cap_bytes=hbm_cap, max_slots=n + 1, chunk_steps=chunk, precision=precision,
-                       device=local, spectrum=True)
+                       device=local, spectrum=True, keep_series=True, keep_state=True)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for p, ta in zip(probs, t_arr):
@@ -462,10 +516,10 @@ def serving(rate=200.0, duration=1.0, steps=1000, chunk=500, precision=32, seed=
         if key in seen or "E" not in r.result:
             continue
         seen.add(key)
-        cases.append((key, p, r.result["dt"], r.steps, max(1, r.steps), dict(max_peaks=4), r.result["E"]))
+        cases.append((key, p, r.result["dt"], r.steps, max(1, r.steps), r.result["E"], r.result.get("series"),
+                      r.result.get("state")))
     srv.close()
-    errs = peak_energy_errors(cases, local, torch.cuda.current_stream(local))
-    worst = max((v for v in errs.values() if v is not None), default=None)
+    acc = accuracy_vs_fp64(cases, local, torch.cuda.current_stream(local))
     # plain: the same requests one at a time, each stepped alone
     torch.cuda.synchronize()
     t1 = time.perf_counter()
@@ -491,11 +545,11 @@ def serving(rate=200.0, duration=1.0, steps=1000, chunk=500, precision=32, seed=
                   "p50_s": float(np.percentile(plain_lat, 50)), "p99_s": float(np.percentile(plain_lat, 99)),
                   "wall_s": plain_wall},
         "diverged_requests": diverged,
-        "energy_rel_err_max": worst,
-        "energy_rel_err": errs,
-        "energy_check": "the first finished request of every shape: probe-spectrum peak energies (>= 1e-2 of the "
-                        "largest peak) vs a lone FP64 device solve of the same request (the FP64 path matches the "
-                        "FP64 oracle to 1e-10 in the parity tests)",
+        **gate_summary(acc),
+        "accuracy": acc,
+        "accuracy_check": "the first finished request of every shape vs a lone FP64 device solve of the same "
+                          "request: resolved level energies, state and probe series, as in batched_vs_plain (a "
+                          "1000-step request resolves the levels of few shapes)",
         "latency_note": "wall clock from arrival to retirement, host-side admission included; the arrival rate "
                         "exceeds the service rate, so the latency is mostly queueing",
     }
@@ -616,6 +670,8 @@ def main():
     ap.add_argument("--no-general-v", action="store_true", help="skip the leg with a potential that does not separate")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the default pass schedules (no autotuning launches; for profiler launch lists)")
+    ap.add_argument("--batch-steps", type=int, default=800,
+                    help="timed steps of the batched leg (a short run for profiler launch lists)")
     ap.add_argument("--batch-only", action="store_true",
                     help="run only the batched leg of the 512-solve mix and print its numbers (for profiler "
                          "launch lists of the batched passes)")
@@ -626,7 +682,7 @@ def main():
     if args.batch_only:
         import torch
         torch.cuda.set_device(0)
-        r = batched_vs_plain(plain=False, check=False)
+        r = batched_vs_plain(steps=args.batch_steps, plain=False, check=False)
         print(json.dumps({"batch_only": True, **{k: r[k] for k in ("workload", "members", "grid_points", "steps",
                                                                     "shapes3d", "batched", "unit")}}))
         return 0
@@ -856,7 +912,7 @@ def main():
         if args.workload == "aniso_ho_3d_256" and not args.no_general_v:
             out["general_v"] = general_v_leg(args.steps, args.warmup, peak, local=local)
         if not args.no_batch:
-            bvp = batched_vs_plain(local=local)
+            bvp = batched_vs_plain(steps=args.batch_steps, local=local)
             probs, dts = bvp.pop("_probs"), bvp.pop("_dts")
             if not args.no_cpu_baseline:
                 bvp["cpu_baseline"] = batched_cpu_baseline(probs, dts)

@@ -327,7 +327,10 @@ spstd_status spstd_get_xy_fusion(const spstd_ctx *ctx, int *on);
  * shares that array: calls that overlap on the GPU race and must be
  * serialised (e.g. one stream).  The first call on each device looks up the
  * array's device address (cudaGetSymbolAddress, with that device current);
- * make that first call before any stream capture.  SPSTD_EINVAL for NULL
+ * make that first call before any stream capture.  The address is kept per
+ * device ordinal for the life of the process, so the entry point assumes the
+ * CUDA runtime's primary context on each device: do not call it from another
+ * (driver-API) context on the same device, nor after cudaDeviceReset.  SPSTD_EINVAL for NULL
  * pointers, n <= 0, a bad precision, or n > SPSTD_NOALLOC_MAX_ELEMS;
  * SPSTD_ECUDA if the set-up or a launch fails. */
 #define SPSTD_NOALLOC_MAX_PARTIALS 65536

@@ -11,6 +11,9 @@
 // address: host code must pass the address cudaGetSymbolAddress returns for the
 // current device.  That lookup is done once per device, on the first call made
 // with that device current; make that first call before any stream capture.
+// The address is cached by device ordinal, which holds for the runtime's
+// primary context: a caller on a driver-API context of its own, or after a
+// cudaDeviceReset, would get an address from another context.
 // Every call on a device shares the one array, which keeps the last call's
 // contents: calls that overlap on the GPU race on it and must be serialised
 // (for example, issued on one stream).  Nothing needs clearing between calls:

@@ -149,6 +149,8 @@ cudaError_t build_separable_v(const float *vx, const float *vyz, float *V, int64
 // Fused x + y reduce-add pass (pass_tmared.cuh) for grids with nx = ny = N in
 // {32, 64}: units of fxy_planes(N) planes hold whole x and y lines.  The map
 // views the field as (x, y, 1, z) with box (N, N, 1, fxy_planes(N)).
+// (96-point planes -- one 36 KB plane per unit, one block per SM -- were
+// measured slower than the separate passes on the 512-solve mix.)
 // ---------------------------------------------------------------------------
 constexpr int fxy_planes(int N) { return 4096 / (N * N); }
 inline bool fxy_eligible(const int64_t *n, int dims)

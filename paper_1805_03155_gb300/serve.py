@@ -46,7 +46,7 @@ class Request:
 class Server:
     def __init__(self, hbm_cap_bytes: float = 150e9, max_slots: int = 1024, chunk_steps: int = 500,
                  precision: int = 32, device: int = 0, keep_state: bool = False, spectrum: bool = True,
-                 tune: bool = True):
+                 tune: bool = True, keep_series: bool = False):
         # the batch and the setup stream are made on first use (the device is
         # touched only once there is work)
         self.batch = None
@@ -57,6 +57,7 @@ class Server:
         self.precision = precision
         self.device = device
         self.keep_state = keep_state
+        self.keep_series = keep_series
         self.spectrum = spectrum
         self.queue: List[Request] = []
         self.ready: List[Request] = []      # set up, waiting for a batch slot
@@ -166,7 +167,10 @@ class Server:
                 r.result["status"] = "diverged"
             r.result["dt"] = s.spstd_get_dt()
             if self.spectrum and r.problem.probes and r.steps >= 2:
-                r.result["E"], r.result["amp"] = s.spstd_spectrum(-1, max_peaks=4)
+                # the strongest 16 peaks above 1e-3 of the largest, dispersion-corrected energies
+                r.result["E"], r.result["amp"] = s.spstd_spectrum(-1, max_peaks=16, thresh=1e-3, phase_correct=True)
+            if self.keep_series and r.problem.probes:
+                r.result["series"] = np.array([s.spstd_probe(q) for q in range(len(r.problem.probes))])
             if self.keep_state:
                 r.result["state"] = s.spstd_get_state()
             s.close()
