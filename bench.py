@@ -574,6 +574,8 @@ def general_v_leg(steps, warmup, peak, local=0):
     stream = torch.cuda.Stream(device=local)
     s = spstd.solver_for(p, precision=32, probe_capacity=warmup + steps + 8, stream=stream, device=local)
     sep = s.spstd_potential_separable()
+    s.spstd_tune(reps=10)  # as the main line: the tuner's pass schedules
+    schedules = [s.spstd_get_schedule(a) for a in range(3)]
     s.spstd_step(warmup)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -589,6 +591,7 @@ def general_v_leg(steps, warmup, peak, local=0):
     hs = (steps * 10 + 1) / steps  # SUZUKI6 with fused step boundaries: 10 half-stages a step within a call
     half_ms = ms / steps / hs
     return {"workload": "aniso_ho_3d_256 with V + 0.01 x y (not separable)", "v_separable": sep,
+            "schedules": schedules,
             "value": N * steps / (ms * 1e-3), "unit": "grid-point-steps/s", "ms_per_step": ms / steps,
             "steps": steps, "x_pass_ms": xms, "x_pass_frac": 16 * N / (xms * 1e-3) / 1e9 / peak,
             "half_stage_ms_in_graph": half_ms,
@@ -670,6 +673,9 @@ def main():
     ap.add_argument("--no-general-v", action="store_true", help="skip the leg with a potential that does not separate")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the default pass schedules (no autotuning launches; for profiler launch lists)")
+    ap.add_argument("--schedules", default=None,
+                    help="comma-separated pass schedule per axis to use instead of autotuning (for profiler runs, "
+                         "whose timings would mislead the tuner), e.g. 6,0,0")
     ap.add_argument("--batch-steps", type=int, default=800,
                     help="timed steps of the batched leg (a short run for profiler launch lists)")
     ap.add_argument("--batch-only", action="store_true",
@@ -710,7 +716,12 @@ def main():
     s = spstd.solver_for(problem, precision=prec, probe_capacity=total_steps, stream=stream, device=local)
     N = problem.n_total
     # autotune the pass schedules on this grid (outside the timed region)
-    tune_ms = s.spstd_tune(reps=10) if not args.no_tune else np.full((3, spstd.SCHEDULES), -1.0)
+    tune_ms = np.full((3, spstd.SCHEDULES), -1.0)
+    if args.schedules:
+        for a, v in enumerate(int(x) for x in args.schedules.split(",")):
+            s.spstd_set_schedule(a, v)
+    elif not args.no_tune:
+        tune_ms = s.spstd_tune(reps=10)
     schedules = [s.spstd_get_schedule(a) for a in range(problem.dims)]
     xy_fused = s.spstd_get_xy_fusion()
     v_sep = s.spstd_potential_separable()

@@ -279,6 +279,9 @@ spstd_status spstd_profile_steps(spstd_ctx *ctx, int64_t nsteps, double *ms, int
  *   4  plain pass, default plan (listed only where 0 is the TMA pass)
  *   5  TMA pass that loads the destination tile into shared memory, adds
  *      there and stores it back (listed only where 0 is the TMA pass)
+ *   6  x axes of 32..256 points of single FP32 2D/3D grids: the reduce-add
+ *      TMA pass with per-warp tiles (each warp its own ring of stages and
+ *      barriers); the same arithmetic as 0, so the same bits
  * Schedules 1..3 exist for FFT axes of 32..512 points.  0, 1, 2 and 4 give
  * bit-identical results on plain axes; 3 changes the rounding (FP32 ~1e-7).
  * spstd_schedule_candidates lists the schedules axis (0..dims-1) can run in
@@ -290,7 +293,7 @@ spstd_status spstd_profile_steps(spstd_ctx *ctx, int64_t nsteps, double *ms, int
  * not NULL, writes the mean milliseconds per pass to ms[axis * SPSTD_SCHEDULES
  * + schedule] (-1 where not a candidate).  It synchronises and leaves psi_R,
  * psi_I, the probes and the step count unchanged. */
-#define SPSTD_SCHEDULES 6
+#define SPSTD_SCHEDULES 7
 spstd_status spstd_schedule_candidates(const spstd_ctx *ctx, int axis, int *list, int *count);
 spstd_status spstd_get_schedule(const spstd_ctx *ctx, int axis, int *schedule);
 spstd_status spstd_set_schedule(spstd_ctx *ctx, int axis, int schedule);

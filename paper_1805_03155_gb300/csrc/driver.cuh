@@ -386,6 +386,9 @@ struct spstd_ctx {
     // y and z views of the fields, with the boxes of pass_tmared.cuh
     bool tma[3] = {false, false, false};
     CUtensorMap xrmap[4];
+    // x pass with per-warp tiles (schedule 6): eligible, maps (psi_R, psi_I, tmp, V)
+    bool xw_ok = false;
+    CUtensorMap xwmap[4];
     CUtensorMap srmap[3][2];
     // stored-tile passes (schedule 5, fused x-y): tma_st[axis]; [field][view]
     bool tma_st[3] = {false, false, false};
@@ -648,6 +651,16 @@ inline bool encode_map4(CUtensorMap *m, void *base, const uint64_t *d, const uin
 // exceeds 256.  v = 0: x view (x_lo, x_hi, row, 1); v = 1: y view (x, y_lo,
 // y_hi, z); v = 2: z view (x, y, z_lo, z_hi).  Strided boxes span
 // tmared_planes() planes of the outer axis.
+// x view (x_lo, x_hi, row, 1) with a box of `rows` rows.
+inline bool encode_x_rows_map(CUtensorMap *m, void *base, const int64_t *n, int rows)
+{
+    const uint64_t n0 = n[0], n1 = n[1], n2 = n[2];
+    const uint64_t L1 = n0 < 256 ? n0 : 256, L2 = n0 / L1;
+    const uint64_t d[4] = {L1, L2, n1 * n2, 1}, st[3] = {L1, n0, n0 * n1 * n2};
+    const uint32_t box[4] = {(uint32_t)L1, (uint32_t)L2, (uint32_t)rows, 1};
+    return encode_map4(m, base, d, st, box);
+}
+
 inline bool encode_red_map(CUtensorMap *m, void *base, const int64_t *n, int v)
 {
     const uint64_t n0 = n[0], n1 = n[1], n2 = n[2];
@@ -695,6 +708,14 @@ inline void setup_tma(spstd_ctx *ctx)
             else if (f < 3) ok = encode_red_map(&ctx->srmap[f][v - 1], base, cfg.n, v);
         }
         ctx->tma[v] = ok;
+        // per-warp x tiles (schedule 6)
+        if (v == 0 && ok && xwarp_eligible(cfg.n[0])) {
+            bool okw = true;
+            for (int f = 0; f < 4 && okw; ++f)
+                okw = encode_x_rows_map(&ctx->xwmap[f], f < 3 ? ctx->ptr(ctx->field_off(f)) : ctx->ptr(ctx->L.V),
+                                        cfg.n, xwarp_rows((int)cfg.n[0]));
+            ctx->xw_ok = okw;
+        }
     }
     // fused x-y pass: unit view (x, y, 1, z), box (N, N, 1, K)
     if (fxy_eligible(cfg.n, cfg.dims) && ctx->tma[0] && ctx->tma[1]) {
@@ -914,7 +935,8 @@ cudaError_t enqueue_apply(spstd_ctx *ctx, int fsrc, int fdst, int table, double 
         const cpx<T> *tw = (const cpx<T> *)ctx->ptr(ctx->L.tw[ax]);
         if constexpr (sizeof(T) == 4) {
             const bool red = ctx->tma[ax] && sv == 0, st = ctx->tma_st[ax] && sv == 5;
-            if ((red || st) && fsrc <= 2 && fdst <= 2) {
+            const bool xw = ax == 0 && ctx->xw_ok && sv == 6;
+            if ((red || st || xw) && fsrc <= 2 && fdst <= 2) {
                 TmaPassArgs ta{};
                 ta.tw = (const float2 *)tw;
                 ta.mult = (const float *)(mult + off[ax]);
@@ -928,11 +950,16 @@ cudaError_t enqueue_apply(spstd_ctx *ctx, int fsrc, int fdst, int table, double 
                 ta.nx = (int)n0;
                 ta.planes = red_planes(cfg.n, ax);
                 ta.inject = status + 1;
-                if (ax == 0 && red && ta.use_V && ctx->vsep) {
+                if (ax == 0 && (red || xw) && ta.use_V && ctx->vsep) {
                     ta.vx = (const float *)ctx->ptr(ctx->L.vsep_x);
                     ta.vyz = (const float *)ctx->ptr(ctx->L.vsep_yz);
                 }
-                if (red) {
+                if (xw) {
+                    const int R = xwarp_rows((int)N);
+                    ta.n_tiles = (int)((n1 * n2 + R - 1) / R);
+                    SPSTD_TIMED(timer, s, 0,
+                                launch_pass_xwarp((int)N, ctx->xwmap[fsrc], ctx->xwmap[3], ctx->xwmap[fdst], ta, s));
+                } else if (red) {
                     ta.n_tiles = tmared_tiles(ax, cfg.n, &ta.n_xt);
                     if (ax == 0)
                         SPSTD_TIMED(timer, s, ax,
@@ -1165,6 +1192,7 @@ spstd_status prepare_kernels(spstd_ctx *ctx)
     for (int ax = 0; ax < cfg.dims; ++ax) {
         if (ctx->tma[ax]) SPSTD_CU(ctx, prepare_pass_tmared(ax, (int)cfg.n[ax], cfg.n[0], red_planes(cfg.n, ax)));
         if (ctx->tma_st[ax]) SPSTD_CU(ctx, prepare_pass_tma(ax, (int)cfg.n[ax]));
+        if (ax == 0 && ctx->xw_ok && ctx->sched[0] == 6) SPSTD_CU(ctx, prepare_pass_xwarp((int)cfg.n[0]));
         if (ax == 0 && ctx->fxy_ok) SPSTD_CU(ctx, prepare_pass_fxy((int)cfg.n[0], false));
         const int sv = ctx->sched[ax];
         if (sv >= 1 && sv <= 3) {

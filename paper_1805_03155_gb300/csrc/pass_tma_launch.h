@@ -109,6 +109,16 @@ cudaError_t launch_pass_tmared(int axis, int N, const CUtensorMap &msrc, const C
 // before a stream capture); nx: points along x.
 cudaError_t prepare_pass_tmared(int axis, int N, int64_t nx, int planes);
 
+// x pass with per-warp tiles (schedule 6; single grids): lines of N in {32,
+// 64, 128, 256} points, tiles of xwarp_rows(N) rows (the box height of its
+// maps); a.n_tiles = ceil(rows / xwarp_rows(N)).  The table form is taken when
+// a.vyz is set.
+constexpr bool xwarp_eligible(int64_t N) { return N == 32 || N == 64 || N == 128 || N == 256; }
+constexpr int xwarp_rows(int N) { return 2 * (32 / (N / 16)); }
+cudaError_t launch_pass_xwarp(int N, const CUtensorMap &msrc, const CUtensorMap &mV, const CUtensorMap &mdst,
+                              const TmaPassArgs &a, cudaStream_t s);
+cudaError_t prepare_pass_xwarp(int N);
+
 // One member of a batched pass: tensor maps over its own fields (0 psi_R,
 // 1 psi_I, 2 scratch; index 3 of the x view is V) with the reduce-add boxes,
 // and its device status word.  Lives in device memory (64-byte aligned).

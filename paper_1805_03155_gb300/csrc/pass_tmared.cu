@@ -51,6 +51,33 @@ cudaError_t red_x(const CUtensorMap *ms, const CUtensorMap *mv, const CUtensorMa
                       BATCH ? none : *ms, BATCH ? none : *mv, BATCH ? none : *md, BATCH ? a0 : *a, BATCH ? *ba : b0);
 }
 
+template <int N, bool VSEP>
+cudaError_t red_xw(const CUtensorMap *ms, const CUtensorMap *mv, const CUtensorMap *md, const TmaPassArgs *a,
+                   cudaStream_t s)
+{
+    using G = XWarp<N, VSEP>;
+    int grid = 0;
+    cudaError_t e = persistent_grid<xpass_warp_kernel<N, VSEP>>(G::THREADS, G::SMEM, &grid);
+    if (e != cudaSuccess || !a) return e;
+    const int need = (a->n_tiles + G::WARPS - 1) / G::WARPS;  // blocks that get a tile
+    if (need < grid) grid = need;
+    if (grid <= 0) return cudaSuccess;
+    return launch_pdl(xpass_warp_kernel<N, VSEP>, dim3(grid), dim3(G::THREADS), G::SMEM, s, *ms, *mv, *md, *a);
+}
+
+template <bool VSEP>
+cudaError_t red_xw_n(int N, const CUtensorMap *ms, const CUtensorMap *mv, const CUtensorMap *md,
+                     const TmaPassArgs *a, cudaStream_t s)
+{
+    switch (N) {
+    case 32: return red_xw<32, VSEP>(ms, mv, md, a, s);
+    case 64: return red_xw<64, VSEP>(ms, mv, md, a, s);
+    case 128: return red_xw<128, VSEP>(ms, mv, md, a, s);
+    case 256: return red_xw<256, VSEP>(ms, mv, md, a, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 template <int N, int P, int K, bool BATCH>
 cudaError_t red_s(const CUtensorMap *ms, const CUtensorMap *md, const TmaPassArgs *a, const TmaBatchArgs *ba,
                   cudaStream_t s)
@@ -223,6 +250,22 @@ cudaError_t prepare_pass_fxy(int N, bool batch)
 {
     return batch ? fxy_any<true>(N, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr)
                  : fxy_any<false>(N, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+}
+
+cudaError_t launch_pass_xwarp(int N, const CUtensorMap &msrc, const CUtensorMap &mV, const CUtensorMap &mdst,
+                              const TmaPassArgs &a, cudaStream_t s)
+{
+    if (a.vyz) {
+        if (!a.vx) return cudaErrorInvalidValue;
+        return red_xw_n<true>(N, &msrc, &mV, &mdst, &a, s);
+    }
+    return red_xw_n<false>(N, &msrc, &mV, &mdst, &a, s);
+}
+
+cudaError_t prepare_pass_xwarp(int N)
+{
+    const cudaError_t e = red_xw_n<true>(N, nullptr, nullptr, nullptr, nullptr, nullptr);
+    return e != cudaSuccess ? e : red_xw_n<false>(N, nullptr, nullptr, nullptr, nullptr, nullptr);
 }
 
 cudaError_t launch_pass_tmared(int axis, int N, const CUtensorMap &msrc, const CUtensorMap &mV,

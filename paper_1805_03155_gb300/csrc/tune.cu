@@ -9,7 +9,8 @@ using namespace spstd_host;
 namespace {
 
 // Schedules an axis of this context can run (sched.h): 0 always; 1..3 for
-// plain FFT passes of tunable length; 4 and 5 where 0 is the pipelined TMA pass.
+// plain FFT passes of tunable length; 4 and 5 where 0 is the pipelined TMA
+// pass; 6 for x axes that take per-warp tiles.
 int schedule_candidates(const spstd_ctx *ctx, int ax, int *list)
 {
     int n = 0;
@@ -22,6 +23,7 @@ int schedule_candidates(const spstd_ctx *ctx, int ax, int *list)
     }
     if (ctx->tma[ax]) list[n++] = 4;
     if (ctx->tma[ax] && ctx->tma_st[ax]) list[n++] = 5;
+    if (ax == 0 && ctx->xw_ok) list[n++] = 6;
     return n;
 }
 
@@ -152,7 +154,7 @@ spstd_status spstd_set_xy_fusion(spstd_ctx *ctx, int on)
 spstd_status spstd_inject_wait_timeout(spstd_ctx *ctx)
 {
     if (!ctx) return SPSTD_EINVAL;
-    if (!fused_active(ctx) && ctx->tma[0] && ctx->sched[0] == 0) {
+    if (!fused_active(ctx) && ctx->tma[0] && (ctx->sched[0] == 0 || (ctx->sched[0] == 6 && ctx->xw_ok))) {
         // the next default x pass leaves its first tile unloaded: the word after
         // the status word is its injection flag
         const int one = 1;

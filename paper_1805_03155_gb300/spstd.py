@@ -24,7 +24,7 @@ PRESETS = {"CUSTOM": -1, "LEAPFROG": 0, "STRANG": 1, "PAPER3": 2, "FR4": 3, "SUZ
 PERIODIC, DIRICHLET, NEUMANN = 0, 1, 2
 MAX_STAGES = 8
 MAX_PROBES = 16
-SCHEDULES = 6
+SCHEDULES = 7
 
 
 class SpstdError(RuntimeError):

@@ -166,3 +166,26 @@ def test_reduce_fused_xy_matches_oracle_and_plain(n):
     assert rel_l2(R, Im, R0, I0) <= 2e-6
     # FR4 (7 half-stages) with fused step boundaries applies 5 * 6 + 1 half-stages
     assert launches0 - launches == 5 * 6 + 1
+
+
+def test_warp_tile_x_pass_wait_timeout_is_reported_and_recoverable():
+    """The same failure path on the per-warp-tile x pass (schedule 6): the
+    first tile of the grid's first warp is never loaded, that warp's bounded
+    wait runs out and it drains its own loads and returns while the other warps
+    finish; SPSTD_ETIMEOUT is reported and the context steps correctly again."""
+    from paper_1805_03155_gb300 import spstd
+
+    p = stable(inputs.gaussian_problem((64, 64, 64), steps=3))
+    s = gpu_solver(p, 32, cap=8, merge=False)
+    s.spstd_set_schedule(0, 6)
+    s.spstd_inject_wait_timeout()
+    s.spstd_step(1)
+    with pytest.raises(spstd.SpstdError) as ei:
+        s.spstd_get_state()
+    assert ei.value.status == spstd.SPSTD_ETIMEOUT
+    s.spstd_set_state(p.psiR, p.psiI)
+    s.spstd_step(3)
+    R, Im = s.spstd_get_state()
+    s.close()
+    oR, oI, _ = oracle_run(p)
+    assert rel_l2(R, Im, oR, oI) <= 1e-4

@@ -63,6 +63,17 @@ def test_every_schedule_same_step(n, precision):
                 assert np.array_equal(R, R0) and np.array_equal(Im, I0), (ax, v)
             else:
                 assert rel_l2(R, Im, R0, I0) <= (1e-13 if precision == 64 else 1e-5), (ax, v)
+        # per-warp x tiles run the default TMA x pass's arithmetic: the same bits,
+        # except where schedule 0 means the fused reduce-add x-y pass (nx = ny in
+        # {32, 64}), which sums the x and y terms in another order
+        if 6 in lst:
+            assert ax == 0 and 0 in lst
+            Rw, Iw = runs[(ax, 6)]
+            Rd, Id = runs[(ax, 0)]
+            if len(n) >= 2 and n[0] == n[1] and n[0] in (32, 64):
+                assert rel_l2(Rw, Iw, Rd, Id) <= 1e-5
+            else:
+                assert np.array_equal(Rw, Rd) and np.array_equal(Iw, Id)
 
 
 def test_set_schedule_rejects_unknown():
@@ -140,3 +151,25 @@ def test_tuned_batch_equals_lone_solves():
     batch.close()
     for s in solvers:
         s.close()
+
+
+@pytest.mark.parametrize("n", [(256, 48), (64, 32, 24), (128, 96)])
+def test_warp_x_tiles_with_a_potential_field(n):
+    """Schedule 6 with a potential that does not separate (a square well in
+    2D/3D is a box, not a sum), so the per-warp x pass reads the V field: the
+    same bits as schedule 0, and the oracle's step to the FP32 tolerance."""
+    from paper_1805_03155_gb300 import spstd
+
+    p = stable(inputs.gaussian_problem(n, steps=8, noise=1e-2, well=(6.0, 1.5)))
+    out = []
+    for v in (0, 6):
+        s = gpu_solver(p, 32, cap=8, merge=False)
+        assert not s.spstd_potential_separable()
+        assert 6 in s.spstd_schedule_candidates(0)
+        s.spstd_set_schedule(0, v)
+        s.spstd_step(p.steps)
+        out.append(s.spstd_get_state())
+        s.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    oR, oI, _ = oracle_run(p)
+    assert rel_l2(out[1][0], out[1][1], oR, oI) <= 1e-4
