@@ -131,10 +131,12 @@ def measured_peaks():
 # 256^3 FP32 kernels from one ncu capture (its summary is kept under profiles/),
 # valid while the kernel sources hash to the recorded value.
 MEASURED_TRAFFIC = {
-    "source_hash": "ab0ffb8547adb27e",
-    # x pass: the separable-potential form (V rebuilt from tables, no V field read)
-    "aniso_ho_3d_256": {"x_pass": 134.529024e6 + 6.635264e6, "y_pass": 134.248448e6 + 4.725248e6,
-                        "z_pass": 134.261248e6 + 5.904384e6},
+    "source_hash": "4794a9cc937c952b",
+    # per kernel kind and pass schedule; x pass: the separable-potential form
+    # (V rebuilt from tables, no V field read); schedule 6: per-warp x tiles
+    "aniso_ho_3d_256": {"x_pass": {0: 134.519040e6 + 6.759424e6, 6: 134.516736e6 + 6.964480e6},
+                        "y_pass": {0: 134.247424e6 + 5.478400e6},
+                        "z_pass": {0: 134.247680e6 + 5.447936e6}},
 }
 TRAFFIC_SOURCES = ["paper_1805_03155_gb300/csrc/pass_tmared.cuh", "paper_1805_03155_gb300/csrc/fft_line.cuh",
                    "paper_1805_03155_gb300/csrc/tma.cuh", "paper_1805_03155_gb300/csrc/pass_tma_launch.h"]
@@ -150,13 +152,11 @@ def traffic_source_hash():
 
 
 def measured_traffic(workload, kernel, schedule=0):
-    """Recorded traffic of the default (pipelined) kernel; None for another
-    schedule or once the kernel sources have changed."""
-    if schedule != 0:
-        return None
+    """Recorded traffic of a kernel under a pass schedule; None where none was
+    recorded or once the kernel sources have changed."""
     if traffic_source_hash() != MEASURED_TRAFFIC["source_hash"]:
         return None
-    return MEASURED_TRAFFIC.get(workload, {}).get(kernel)
+    return MEASURED_TRAFFIC.get(workload, {}).get(kernel, {}).get(schedule)
 
 
 KIND_AXIS = {"x_pass": 0, "y_pass": 1, "z_pass": 2, "xy_pass": 0}
