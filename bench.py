@@ -472,7 +472,8 @@ def batched_vs_plain(count=512, steps=800, plain_steps=40, precision=32, local=0
     }
 
 
-def serving(rate=200.0, duration=1.0, steps=1000, chunk=500, precision=32, seed=9, local=0, hbm_cap=150e9):
+def serving(rate=200.0, duration=1.0, steps=1000, chunk=500, precision=32, seed=9, local=0, hbm_cap=150e9,
+            tune=True, check=True):
     """Poisson arrivals (rate/s for `duration` s) of solves drawn from the
     mixed workload plus 128^3 oscillators, each `steps` steps, served by
     continuous batching in `chunk`-step rounds under an HBM cap; p50/p99
@@ -496,7 +497,7 @@ def serving(rate=200.0, duration=1.0, steps=1000, chunk=500, precision=32, seed=
             p = mix[i]
         probs.append(p)
     srv = serve.Server(hbm_cap_bytes=hbm_cap, max_slots=n + 1, chunk_steps=chunk, precision=precision,
-                       device=local, spectrum=True, keep_series=True, keep_state=True)
+                       device=local, spectrum=True, keep_series=check, keep_state=check, tune=tune)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for p, ta in zip(probs, t_arr):
@@ -519,7 +520,7 @@ def serving(rate=200.0, duration=1.0, steps=1000, chunk=500, precision=32, seed=
         cases.append((key, p, r.result["dt"], r.steps, max(1, r.steps), r.result["E"], r.result.get("series"),
                       r.result.get("state")))
     srv.close()
-    acc = accuracy_vs_fp64(cases, local, torch.cuda.current_stream(local))
+    acc = accuracy_vs_fp64(cases, local, torch.cuda.current_stream(local)) if check else {}
     # plain: the same requests one at a time, each stepped alone
     torch.cuda.synchronize()
     t1 = time.perf_counter()
@@ -545,7 +546,7 @@ def serving(rate=200.0, duration=1.0, steps=1000, chunk=500, precision=32, seed=
                   "p50_s": float(np.percentile(plain_lat, 50)), "p99_s": float(np.percentile(plain_lat, 99)),
                   "wall_s": plain_wall},
         "diverged_requests": diverged,
-        **gate_summary(acc),
+        **(gate_summary(acc) if acc else {}),
         "accuracy": acc,
         "accuracy_check": "the first finished request of every shape vs a lone FP64 device solve of the same "
                           "request: resolved level energies, state and probe series, as in batched_vs_plain (a "
@@ -815,13 +816,26 @@ def main():
         "a5_probe_ms_per_step": kinds.get("probe", (0.0, 1))[0] / max(1, kinds.get("probe", (0.0, 1))[1]),
         "a6_nfft": nfft,
         "what": "a5 from the per-launch events; a6 and a7 by host clock around the synchronising C-ABI calls "
-                "(spstd_spectrum over the sum of the probe series, spstd_energy_norm)",
+                "(spstd_spectrum over the sum of the probe series recorded so far, a6_samples of them; "
+                "a6_spectrum_ms_50000_samples: the same call on a 50000-sample series, as the 50000-step "
+                "workload records; spstd_energy_norm)",
     }
     try:
         rows["a6_spectrum_ms"] = host_ms(lambda: s.spstd_spectrum(-1, nfft=nfft), 3)
+        rows["a6_samples"] = int(min(args.warmup + args.steps + 8, s.spstd_steps_taken()))
         rows["a7_energy_norm_ms"] = host_ms(s.spstd_energy_norm, 5)
     except spstd.SpstdError as e:
         rows["error"] = str(e)
+    if args.workload == "aniso_ho_3d_256":
+        # a6 at the workload's own series length: 50000 samples per probe and a
+        # 2^16-point FFT (the cost depends on the series, not on the grid, so a
+        # 1D solve -- one resident launch -- records it)
+        from paper_1805_03155_gb300 import inputs
+        w1 = inputs.well_1d(steps=50000)
+        s1 = spstd.solver_for(w1, precision=32, probe_capacity=50000, stream=stream, device=local)
+        s1.spstd_step(50000)
+        rows["a6_spectrum_ms_50000_samples"] = host_ms(lambda: s1.spstd_spectrum(-1, nfft=1 << 16, max_peaks=32), 3)
+        s1.close()
     s.close()
 
     if rank == 0:

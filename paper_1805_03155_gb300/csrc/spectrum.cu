@@ -9,10 +9,11 @@
 //      S(theta_k) = sum_n zw_n exp(+i theta_k n), which peaks at theta =
 //      E dt/hbar for a component exp(-i E t/hbar);
 //   3. magnitudes |S_k| for k <= nfft/2;
-//   4. peak list (one block): k in [1, nfft/2 - 1) whose |S_k| is the largest
-//      within h = ceil(2 nfft/M) bins (the Hann main-lobe half width, which
-//      rejects side lobes) and >= thresh * max; the max_peaks largest, ties to
-//      the lower k;
+//   4. peak list: the largest |S_k| (one block); then, over the whole grid,
+//      a flag for every k in [1, nfft/2 - 1) whose |S_k| is the largest within
+//      h = ceil(2 nfft/M) bins (the Hann main-lobe half width, which rejects
+//      side lobes) and >= thresh * max; then (one block) the flagged k in
+//      order and the max_peaks largest of them, ties to the lower k;
 //   5. refinement (one block per peak): 60 golden-section steps maximising
 //      |sum_n zw_n exp(+i theta n)| on [theta_{k-1}, theta_{k+1}].
 #include <cuda_runtime.h>
@@ -87,17 +88,13 @@ __device__ __forceinline__ bool better(double a1, int64_t k1, double a2, int64_t
     return a1 > a2 || (a1 == a2 && k1 < k2);
 }
 
+// The largest |S_k| over 1 <= k < nfft/2 (one block).
 __global__ void __launch_bounds__(kPeakThreads)
-peaks_kernel(const double *__restrict__ mag, int64_t nfft, int64_t M, double thresh, int max_peaks,
-             int64_t *__restrict__ cand_k, double *__restrict__ cand_a, int64_t *__restrict__ peak_k,
-             int *__restrict__ npeaks)
+max_kernel(const double *__restrict__ mag, int64_t nfft, double *__restrict__ smax_out)
 {
     __shared__ double s_a[kPeakThreads];
-    __shared__ int64_t s_k[kPeakThreads];
-    __shared__ int64_t s_cnt[kPeakThreads];
     const int t = threadIdx.x;
     const int64_t half = nfft / 2;
-    // 1. largest |S_k| over 1 <= k < nfft/2
     double mx = 0.0;
     for (int64_t k = 1 + t; k < half; k += kPeakThreads) mx = fmax(mx, mag[k]);
     s_a[t] = mx;
@@ -106,25 +103,48 @@ peaks_kernel(const double *__restrict__ mag, int64_t nfft, int64_t M, double thr
         if (t < o) s_a[t] = fmax(s_a[t], s_a[t + o]);
         __syncthreads();
     }
-    const double smax = s_a[0];
-    __syncthreads();
-    // 2. candidates, compacted in k order: contiguous chunk per thread
+    if (t == 0) *smax_out = s_a[0];
+}
+
+// flag[k] = 1 where |S_k| >= thresh * max and no bin within h of k beats it
+// (ties go to the lower k), for 1 <= k < nfft/2 - 1; 0 elsewhere.
+__global__ void flag_kernel(const double *__restrict__ mag, int64_t nfft, int64_t M, double thresh,
+                            const double *__restrict__ smax, unsigned char *__restrict__ flag)
+{
+    const int64_t half = nfft / 2;
     const int64_t h = (2 * nfft + M - 1) / M;
+    const double lim = thresh * *smax;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < half;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        bool pk = k >= 1 && k < half - 1;
+        const double s1 = mag[k];
+        if (pk && s1 < lim) pk = false;
+        for (int64_t j = k - h; pk && j <= k + h; ++j) {
+            if (j < 0 || j > half || j == k) continue;
+            const double sj = mag[j];
+            if ((j < k && sj >= s1) || (j > k && sj > s1)) pk = false;
+        }
+        flag[k] = pk ? 1 : 0;
+    }
+}
+
+__global__ void __launch_bounds__(kPeakThreads)
+peaks_kernel(const double *__restrict__ mag, const unsigned char *__restrict__ flag, int64_t nfft, int max_peaks,
+             int64_t *__restrict__ cand_k, double *__restrict__ cand_a, int64_t *__restrict__ peak_k,
+             int *__restrict__ npeaks)
+{
+    __shared__ double s_a[kPeakThreads];
+    __shared__ int64_t s_k[kPeakThreads];
+    __shared__ int64_t s_cnt[kPeakThreads];
+    const int t = threadIdx.x;
+    const int64_t half = nfft / 2;
+    // candidates, compacted in k order: contiguous chunk per thread
     const int64_t k_lo = 1, k_hi = half - 1;  // k in [k_lo, k_hi)
     const int64_t span = k_hi > k_lo ? k_hi - k_lo : 0;
     const int64_t chunk = (span + kPeakThreads - 1) / kPeakThreads;
     const int64_t c_lo = k_lo + (int64_t)t * chunk;
     const int64_t c_hi = (c_lo + chunk < k_hi) ? c_lo + chunk : k_hi;
-    auto is_peak = [&](int64_t k) -> bool {
-        const double s1 = mag[k];
-        if (s1 < thresh * smax) return false;
-        for (int64_t j = k - h; j <= k + h; ++j) {
-            if (j < 0 || j > half || j == k) continue;
-            const double sj = mag[j];
-            if ((j < k && sj >= s1) || (j > k && sj > s1)) return false;
-        }
-        return true;
-    };
+    auto is_peak = [&](int64_t k) -> bool { return flag[k] != 0; };
     int64_t cnt = 0;
     for (int64_t k = c_lo; k < c_hi; ++k) cnt += is_peak(k) ? 1 : 0;
     s_cnt[t] = cnt;
@@ -190,15 +210,27 @@ peaks_kernel(const double *__restrict__ mag, int64_t nfft, int64_t M, double thr
 
 constexpr int kRefineThreads = 256;
 
+// |sum_n zw_n exp(+i theta n)| over the block.  Thread t takes n = t + j T
+// (T threads): its phase exp(i theta n) starts from one sincos and advances by
+// a complex multiply with exp(i theta T) per sample, so a 50 000-sample series
+// costs two sincos per thread instead of one per sample; the recurrence's
+// relative rounding stays near (M/T) eps, far below what the golden-section
+// search resolves (the square root of the noise of |S| near its maximum).
 __device__ double dtft_abs(const double2 *__restrict__ zw, int64_t M, double theta, double *s_re, double *s_im)
 {
     double re = 0.0, im = 0.0;
-    for (int64_t n = threadIdx.x; n < M; n += kRefineThreads) {
-        double s, c;
-        sincos(theta * (double)n, &s, &c);
-        const double2 z = zw[n];
-        re += z.x * c - z.y * s;
-        im += z.x * s + z.y * c;
+    if ((int64_t)threadIdx.x < M) {
+        double s, c, ws, wc;
+        sincos(theta * (double)threadIdx.x, &s, &c);
+        sincos(theta * (double)kRefineThreads, &ws, &wc);
+        for (int64_t n = threadIdx.x; n < M; n += kRefineThreads) {
+            const double2 z = zw[n];
+            re += z.x * c - z.y * s;
+            im += z.x * s + z.y * c;
+            const double c2 = c * wc - s * ws;
+            s = fma(c, ws, s * wc);
+            c = c2;
+        }
     }
     s_re[threadIdx.x] = re;
     s_im[threadIdx.x] = im;
@@ -273,7 +305,9 @@ size_t spectrum_scratch_bytes(int64_t max_nfft, int64_t cap)
          + al(sizeof(double) * (max_nfft / 2 + 1))  // magnitudes
          + al(sizeof(int64_t) * (max_nfft / 2))     // candidate k
          + al(sizeof(double) * (max_nfft / 2))      // candidate amplitude
-         + al(sizeof(int64_t) * kMaxSpectrumPeaks) + al(sizeof(double) * kMaxSpectrumPeaks) * 2 + al(sizeof(int));
+         + al(sizeof(int64_t) * kMaxSpectrumPeaks) + al(sizeof(double) * kMaxSpectrumPeaks) * 2 + al(sizeof(int))
+         + al(sizeof(double))              // largest magnitude
+         + al(max_nfft / 2);               // peak flags
 }
 
 cudaError_t launch_spectrum(const SpectrumArgs &a, cudaStream_t s)
@@ -299,6 +333,10 @@ cudaError_t launch_spectrum(const SpectrumArgs &a, cudaStream_t s)
     double *amp = (double *)w;
     w += al(sizeof(double) * kMaxSpectrumPeaks);
     int *np = (int *)w;
+    w += al(sizeof(int));
+    double *smax = (double *)w;
+    w += al(sizeof(double));
+    unsigned char *flag = (unsigned char *)w;
 
     auto grid = [](int64_t n) {
         int64_t b = (n + 255) / 256;
@@ -315,7 +353,9 @@ cudaError_t launch_spectrum(const SpectrumArgs &a, cudaStream_t s)
         out = t;
     }
     mag_kernel<<<grid(a.nfft / 2 + 1), 256, 0, s>>>(in, a.nfft / 2 + 1, mag);
-    peaks_kernel<<<1, kPeakThreads, 0, s>>>(mag, a.nfft, a.M, a.thresh, a.max_peaks, cand_k, cand_a, peak_k, np);
+    max_kernel<<<1, kPeakThreads, 0, s>>>(mag, a.nfft, smax);
+    flag_kernel<<<grid(a.nfft / 2), 256, 0, s>>>(mag, a.nfft, a.M, a.thresh, smax, flag);
+    peaks_kernel<<<1, kPeakThreads, 0, s>>>(mag, flag, a.nfft, a.max_peaks, cand_k, cand_a, peak_k, np);
     refine_kernel<<<a.max_peaks, kRefineThreads, 0, s>>>(zw, a.M, a.nfft, peak_k, np, theta, amp);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -332,7 +372,7 @@ int spectrum_launches(int64_t nfft)
 {
     int passes = 0;
     for (int64_t Ns = 1; Ns < nfft; Ns *= 2) ++passes;
-    return 1 + passes + 3;
+    return 1 + passes + 5;
 }
 
 }  // namespace spstd

@@ -103,7 +103,9 @@ def test_ho_3d_64_long_run_vs_oracle(golden, precision, tol):
     rel = match_peaks(E, oE)
     print(f"ho_3d_64 FP{precision} peaks {np.round(oE, 6)} rel err {rel}")
     assert len(E) == len(oE)
-    assert np.max(rel) <= (1e-9 if precision == 64 else 1e-5)
+    # FP64: the refined peak is a golden-section maximum of |S(theta)|, defined only to
+    # about the square root of the rounding noise of S near the peak
+    assert np.max(rel) <= (1e-7 if precision == 64 else 1e-5)
 
 
 @pytest.fixture(scope="module")
