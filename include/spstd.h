@@ -239,6 +239,15 @@ spstd_status spstd_probe(spstd_ctx *ctx, int p, double *re, double *im, int64_t 
 spstd_status spstd_spectrum(spstd_ctx *ctx, int p, int64_t nfft, int max_peaks, double thresh,
                             int phase_correct, double *E, double *amp, int *npeaks);
 
+/* Workspace canaries (a debugging aid: the GPU memory checker is not always
+ * available).  The workspace holds 256 guard bytes of a fixed pattern after
+ * each of its regions (fields, tables, rings, scratch); spstd_check_workspace
+ * reads them back after the work enqueued so far (it synchronises the
+ * context's stream) and sets *intact to 0 if any was overwritten -- a kernel
+ * wrote past the end of its region -- naming the first in spstd_last_error.
+ * The guards are not written again: a damaged workspace stays reported. */
+spstd_status spstd_check_workspace(spstd_ctx *ctx, int *intact);
+
 /* norm = dV sum(psi_R^2 + psi_I^2) and energy = dV sum(psi_R H psi_R +
  * psi_I H psi_I), H = hbar K, accumulated in FP64 on the device in a fixed
  * order (bitwise reproducible).  Synchronises.  SPSTD_EDIVERGED if either is

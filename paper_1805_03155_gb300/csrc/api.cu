@@ -125,6 +125,9 @@ spstd_status spstd_create(const spstd_config *cfg, void *d_workspace, size_t wor
     if (cudaSetDevice(cfg->device) != cudaSuccess) return bail(SPSTD_ECUDA);
     if (cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess) return bail(SPSTD_ECUDA);
     if (cudaMemsetAsync(ctx->ws, 0, ctx->L.total, ctx->stream) != cudaSuccess) return bail(SPSTD_ECUDA);
+    for (int g = 0; g < ctx->L.n_guard; ++g)
+        if (cudaMemsetAsync(ctx->ws + ctx->L.guard[g], kGuardByte, kGuardBytes, ctx->stream) != cudaSuccess)
+            return bail(SPSTD_ECUDA);
     st = set_dt(ctx, 0.0);
     if (st != SPSTD_OK) return bail(st);
     setup_tma(ctx);
@@ -270,6 +273,7 @@ spstd_status spstd_get_state(spstd_ctx *ctx, double *psiR, double *psiI)
 spstd_status spstd_step(spstd_ctx *ctx, int64_t nsteps)
 {
     if (!ctx || nsteps < 0) return SPSTD_EINVAL;
+    NvtxRange r("spstd_step");
     if (nsteps == 0) return SPSTD_OK;
     return ctx->cfg.precision == 32 ? step_impl<float>(ctx, nsteps) : step_impl<double>(ctx, nsteps);
 }
@@ -302,6 +306,7 @@ spstd_status spstd_spectrum(spstd_ctx *ctx, int p, int64_t nfft, int max_peaks, 
                             double *E, double *amp, int *npeaks)
 {
     if (!ctx || !E || !amp || !npeaks) return SPSTD_EINVAL;
+    NvtxRange r("spstd_spectrum");
     *npeaks = 0;
     if (p < -1 || p >= ctx->cfg.n_probe || ctx->cfg.n_probe == 0) return fail(ctx, SPSTD_EINVAL, "bad probe");
     if (max_peaks < 1 || max_peaks > kMaxSpectrumPeaks) return fail(ctx, SPSTD_EINVAL, "max_peaks must be 1..64");
@@ -409,9 +414,33 @@ spstd_status apply_h_impl(spstd_ctx *ctx, int which, double *out)
 
 extern "C" {
 
+spstd_status spstd_check_workspace(spstd_ctx *ctx, int *intact)
+{
+    if (!ctx || !intact) return SPSTD_EINVAL;
+    *intact = 1;
+    std::vector<unsigned char> g(kGuardBytes);
+    for (int k = 0; k < ctx->L.n_guard; ++k) {
+        SPSTD_CU(ctx, cudaMemcpyAsync(g.data(), ctx->ws + ctx->L.guard[k], kGuardBytes, cudaMemcpyDeviceToHost,
+                                      ctx->stream));
+        SPSTD_CU(ctx, cudaStreamSynchronize(ctx->stream));
+        for (size_t i = 0; i < kGuardBytes; ++i) {
+            if (g[i] != kGuardByte) {
+                *intact = 0;
+                char msg[96];
+                std::snprintf(msg, sizeof(msg), "guard word %d (workspace offset %zu) overwritten", k,
+                              ctx->L.guard[k] + i);
+                ctx->err = msg;
+                return SPSTD_OK;
+            }
+        }
+    }
+    return SPSTD_OK;
+}
+
 spstd_status spstd_energy_norm(spstd_ctx *ctx, double *norm, double *energy)
 {
     if (!ctx || !norm || !energy) return SPSTD_EINVAL;
+    NvtxRange r("spstd_energy_norm");
     return ctx->cfg.precision == 32 ? energy_norm_impl<float>(ctx, norm, energy)
                                     : energy_norm_impl<double>(ctx, norm, energy);
 }

@@ -557,6 +557,7 @@ spstd_status spstd_batch_step(spstd_batch *b, int64_t nsteps)
 {
     if (!b || nsteps < 0) return SPSTD_EINVAL;
     if (nsteps == 0) return SPSTD_OK;
+    NvtxRange r("spstd_batch_step");
     if (b->dirty) {
         spstd_status st = batch_build(b);
         if (st != SPSTD_OK) return st;
@@ -726,6 +727,7 @@ extern "C" {
 spstd_status spstd_batch_tune(spstd_batch *b, int reps)
 {
     if (!b || reps < 1) return SPSTD_EINVAL;
+    NvtxRange r("spstd_batch_tune");
     if (b->dirty) {
         spstd_status st = batch_build(b);
         if (st != SPSTD_OK) return st;

@@ -22,6 +22,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/spstd.h"
 #include "../../include/spstd_testing.h"
 #include "launch.cuh"
@@ -47,13 +49,32 @@ struct HalfStage {
     double scale; // s coef dt (multiplies a dense operator that carries hbar/2m*)
 };
 
+// Guard words: kGuardBytes after every nonempty workspace region, filled with
+// kGuardByte at creation; spstd_check_workspace reads them back, so that a
+// kernel writing past the end of its region shows (a canary check, since the
+// GPU sanitizer is not available to us).
+constexpr size_t kGuardBytes = 256;
+constexpr unsigned char kGuardByte = 0xA5;
+constexpr int kMaxGuards = 48;
+
 struct Layout {
     size_t psi[2], V, vsep_x, vsep_yz, tmp, staging, ring, counter, status, snap, partial, dout, tw[3], mult, dense[3], spec;
     size_t eig_acc, eig_theta, eig_step, rk[6], lscr, xy, total;
+    size_t guard[kMaxGuards];
+    int n_guard;
 };
 
 // Periodic lengths 3 * 2^k that the 2D/3D pass kernels transform with a
 // radix-3 first stage (line_e and the plans of fft_line.cuh).
+// A named NVTX range for the life of a scope (a no-op unless a profiler
+// attaches): spstd_step, spstd_batch_step, spectra, reductions and tuning.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
 inline bool is_radix3_len(int64_t n) { return n == 24 || n == 48 || n == 96 || n == 192 || n == 384; }
 
 // An axis uses the FFT passes when it is periodic with a power-of-two length
@@ -312,9 +333,14 @@ inline Layout make_layout(const spstd_config &cfg, int m)
     const int64_t ntot = cfg.n[0] * cfg.n[1] * cfg.n[2];
     const size_t es = cfg.precision == 32 ? 4 : 8;
     size_t off = 0;
+    L.n_guard = 0;
     auto take = [&](size_t bytes) {
         size_t o = off;
         off += al256(bytes);
+        if (bytes > 0 && L.n_guard < kMaxGuards) {
+            L.guard[L.n_guard++] = off;
+            off += kGuardBytes;
+        }
         return o;
     };
     L.psi[0] = take(es * ntot);

@@ -182,6 +182,7 @@ spstd_status spstd_get_xy_fusion(const spstd_ctx *ctx, int *on)
 spstd_status spstd_tune(spstd_ctx *ctx, int reps, double *ms)
 {
     if (!ctx || reps < 1) return SPSTD_EINVAL;
+    NvtxRange r("spstd_tune");
     if (ms)
         for (int i = 0; i < 3 * kSchedules; ++i) ms[i] = -1.0;
     return ctx->cfg.precision == 32 ? tune_impl<float>(ctx, reps, ms) : tune_impl<double>(ctx, reps, ms);

@@ -41,6 +41,7 @@ class Request:
     slot: int = -1
     solver: object = None
     result: Dict = field(default_factory=dict)
+    cancelled: bool = False
 
 
 class Server:
@@ -64,6 +65,7 @@ class Server:
         self.running: Dict[int, Request] = {}
         self.retiring: List[Request] = []   # out of the batch, results not read yet
         self.done: List[Request] = []
+        self.cancelled: List[Request] = []
         self.footprint = 0
         self._next = 0
         self.chunks = 0
@@ -144,6 +146,40 @@ class Server:
             self.batch.spstd_batch_tune(reps=2)
             self._untuned = False
 
+    def cancel(self, rid: int) -> bool:
+        """Withdraws request rid: at once if it is queued or set up but not yet
+        admitted; if it is running, its member leaves the batch at the next
+        chunk boundary (never while a chunk is on the device) and its context
+        is freed.  Its result then carries status "cancelled".  False if rid
+        is unknown or already finished."""
+        for lst in (self.queue, self.ready):
+            for r in lst:
+                if r.rid == rid:
+                    lst.remove(r)
+                    self._drop(r)
+                    return True
+        r = self.running.get(rid)
+        if r is not None:
+            r.cancelled = True
+            return True
+        return False
+
+    def _drop(self, r):
+        if r.solver is not None:
+            r.solver.close()
+            r.solver = None
+            self.footprint -= r.need
+        r.result["status"] = "cancelled"
+        r.finished = time.perf_counter()
+        self.cancelled.append(r)
+
+    def _remove_cancelled(self):
+        """Takes cancelled members out of the batch (after a chunk)."""
+        for rid in [rid for rid, r in self.running.items() if r.cancelled]:
+            r = self.running.pop(rid)
+            self.batch.spstd_batch_remove(r.slot)
+            self._drop(r)
+
     def _remove_finished(self):
         """Takes members whose steps are done out of the batch (after a chunk)."""
         for rid in [rid for rid, r in self.running.items() if r.done_steps >= r.steps]:
@@ -198,6 +234,7 @@ class Server:
         self.chunks += 1
         for r in self.running.values():
             r.done_steps += n
+        self._remove_cancelled()
         self._remove_finished()
         return True
 

@@ -97,6 +97,7 @@ def lib():
         "spstd_spectrum": (C.c_int, [vp, C.c_int, C.c_int64, C.c_int, C.c_double, C.c_int, dp, dp,
                                      C.POINTER(C.c_int)]),
         "spstd_energy_norm": (C.c_int, [vp, dp, dp]),
+        "spstd_check_workspace": (C.c_int, [vp, C.POINTER(C.c_int)]),
         "spstd_apply_hamiltonian": (C.c_int, [vp, C.c_int, dp]),
         "spstd_get_dt": (C.c_int, [vp, dp]),
         "spstd_steps_taken": (C.c_int, [vp, ip]),
@@ -207,6 +208,7 @@ class Solver:
         self._ws = torch.empty(nbytes.value + 256, dtype=torch.uint8, device=dev)
         base = self._ws.data_ptr()
         aligned = (base + 255) // 256 * 256
+        self.workspace_offset = aligned - base  # where the library's workspace starts in self._ws
         self.ctx = C.c_void_p(0)
         self._check(self.L.spstd_create(C.byref(cfg), C.c_void_p(aligned), nbytes.value, C.byref(self.ctx)), None)
         self.n_total = int(cfg.n[0] * cfg.n[1] * cfg.n[2])
@@ -280,6 +282,12 @@ class Solver:
             e.norm, e.energy = nv.value, ev.value
             raise
         return nv.value, ev.value
+
+    def spstd_check_workspace(self):
+        """True while every guard word of the workspace is intact."""
+        v = C.c_int(0)
+        self._check(self.L.spstd_check_workspace(self.ctx, C.byref(v)))
+        return bool(v.value)
 
     def spstd_apply_hamiltonian(self, which):
         out = np.empty(self.n_total)

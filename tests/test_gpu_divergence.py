@@ -98,3 +98,35 @@ def test_batch_hbm_cap_admission():
     small.close()
     for s in solvers:
         s.close()
+
+
+@pytest.mark.parametrize("n,precision,x_schedule", [((64, 64, 64), 32, 0), ((64, 64, 64), 32, 6),
+                                                    ((96, 48), 32, 0), ((48, 24, 96), 64, 0), ((2048,), 32, 0),
+                                                    ((256,), 64, 0), ((4096, 16), 32, 0)])
+def test_workspace_guards_intact_after_steps(n, precision, x_schedule):
+    """No pass writes past its workspace region: the guard words after every
+    region keep their pattern through steps, H applies, spectra and norms."""
+    p = inputs.gaussian_problem(n, dt=0.0, steps=20, n_probe=3)
+    s = gpu_solver(p, precision, cap=32)
+    if x_schedule:
+        s.spstd_set_schedule(0, x_schedule)
+    assert s.spstd_check_workspace()
+    s.spstd_step(20)
+    s.spstd_apply_hamiltonian(1)
+    s.spstd_spectrum(-1)
+    s.spstd_energy_norm()
+    assert s.spstd_check_workspace()
+    s.close()
+
+
+def test_workspace_guard_damage_is_reported():
+    """A byte of the guard after psi_R, overwritten from the host side through
+    the caller-owned workspace tensor, is reported (a made fault, no kernel
+    involved)."""
+    p = inputs.gaussian_problem((32, 32), dt=0.0, steps=2)
+    s = gpu_solver(p, 32, cap=4)
+    assert s.spstd_check_workspace()
+    psi_bytes = (4 * p.n_total + 255) // 256 * 256   # psi_R's region, then its guard
+    s._ws[s.workspace_offset + psi_bytes + 7] = 0
+    assert not s.spstd_check_workspace()
+    s.close()

@@ -80,3 +80,32 @@ def test_admission_respects_hbm_cap():
     assert len(srv.done) == 4 and most >= 1
     assert all(r.result["status"] == "ok" for r in srv.done)
     srv.close()
+
+
+def test_cancelled_request_leaves_at_a_chunk_boundary():
+    """Cancelling a running request takes its member out of the batch between
+    chunks and frees its context; the other requests still equal their lone
+    solves bit for bit (FP64, default schedules)."""
+    from paper_1805_03155_gb300 import serve, spstd
+
+    reqs = requests()[:4]
+    srv = serve.Server(hbm_cap_bytes=2e9, max_slots=8, chunk_steps=5, precision=64, keep_state=True, tune=False)
+    for p, steps in reqs:
+        srv.submit(p, steps)
+    assert srv.step()
+    victim = sorted(srv.running)[1]
+    assert srv.cancel(victim)
+    srv.run()
+    assert [r.rid for r in srv.cancelled] == [victim] and srv.cancelled[0].result["status"] == "cancelled"
+    assert sorted(r.rid for r in srv.done) == sorted(set(range(4)) - {victim})
+    assert srv.batch.spstd_batch_footprint()[0] == 0 and srv.footprint == 0
+    assert not srv.cancel(victim) and not srv.cancel(99)
+    srv.close()
+    for r in srv.done:
+        p, steps = reqs[r.rid]
+        s = spstd.solver_for(p, precision=64, probe_capacity=steps, merge=False)
+        s.spstd_step(steps)
+        R, Im = s.spstd_get_state()
+        s.close()
+        bR, bI = r.result["state"]
+        assert np.array_equal(bR, R) and np.array_equal(bI, Im), r.rid
