@@ -602,17 +602,17 @@ def general_v_leg(steps, warmup, peak, local=0):
 
 
 def next_rows_leg(peak, sm_mhz, local=0):
-    """The rows beyond the hot path, each timed once on a representative
-    grid (CUDA events around spstd_step on the solver's stream, after a
-    warm-up call), with the roofline each is held to:
-    * four-step long lines (1D FP32, 2^20 points, FR4): the measurement unit's
-      16 B/pt per applied half-stage against the copy peak (the kernels move
-      about 56 B/pt for a lone line, whose imaginary half is zero);
-    * Dirichlet walls (3D FP32 64^3, DST on every axis, FR4): dense n x n
+    """The rows beyond the hot path, each timed once on a grid larger than L2
+    where its bound is HBM (CUDA events around spstd_step on the solver's
+    stream, after a warm-up call), with the roofline each is held to:
+    * four-step long x lines (2D FP32, 65536 x 256, FR4): 16 B/pt per applied
+      half-stage (the measurement unit) against the copy peak; the kernels
+      move about 36 B/pt for the paired x lines plus 12 B/pt for y;
+    * Dirichlet walls (3D FP32 128^3, DST on every axis, FR4): dense n x n
       line operators, 2n flops per point per axis -- the FP32 ALU bound;
-    * the RK4 comparison scheme (3D FP32 128^3): 8 H applications a step, the
+    * the RK4 comparison scheme (3D FP32 256^3): 8 H applications a step, the
       unit's 16 B/pt each;
-    * eigenstate accumulation (3D FP32 128^3, FR4, 2 target energies): the
+    * eigenstate accumulation (3D FP32 256^3, FR4, 2 target energies): the
       extra time per step over plain unmerged steps, against the 72 B/pt the
       accumulator kernel moves (psi_R, psi_I read; two FP64 complex
       accumulators read and written)."""
@@ -632,33 +632,33 @@ def next_rows_leg(peak, sm_mhz, local=0):
         return e0.elapsed_time(e1) / steps
 
     out = {}
-    # long lines
-    p = inputs.gaussian_problem((1 << 20,), (-20.0,), (20.0,), seed=21, dt=0.0, steps=20, n_probe=2)
-    s = spstd.solver_for(p, precision=32, probe_capacity=64, stream=stream, device=local)
-    ms = timed(s, 20)
-    s.close()
-    h_applied = (20 * 6 + 1) / 20  # FR4 with fused step boundaries
-    out["long_line_1d_2^20_fp32"] = {"ms_per_step": ms, "value": p.n_total / (ms * 1e-3),
-                                     "half_stage_frac": 16 * p.n_total / (ms / h_applied * 1e-3) / 1e9 / peak,
-                                     "bound": "hbm"}
-    # walls
-    p = inputs.gaussian_problem((64, 64, 64), steps=10, seed=22, dt=0.0, n_probe=2, bc=(1, 1, 1))
+    h_applied = (10 * 6 + 1) / 10  # FR4 with fused step boundaries, 10 steps a call
+    # long x lines
+    p = inputs.gaussian_problem((65536, 256), (-64.0, -8.0), (64.0, 8.0), seed=21, dt=0.0, steps=10, n_probe=2)
     s = spstd.solver_for(p, precision=32, probe_capacity=64, stream=stream, device=local)
     ms = timed(s, 10)
     s.close()
-    flops = (3 * 2 * 64 + 2) * p.n_total * h_applied
-    out["walls_dirichlet_64^3_fp32"] = {"ms_per_step": ms, "value": p.n_total / (ms * 1e-3), "bound": "alu",
-                                        "alu_frac": flops / (ms * 1e-3) / 1e12 / alu_peak_tflops(32, sm_mhz)}
+    out["long_x_65536x256_fp32"] = {"ms_per_step": ms, "value": p.n_total / (ms * 1e-3), "bound": "hbm",
+                                    "half_stage_frac": 16 * p.n_total / (ms / h_applied * 1e-3) / 1e9 / peak,
+                                    "moved_frac": 48 * p.n_total / (ms / h_applied * 1e-3) / 1e9 / peak}
+    # walls
+    p = inputs.gaussian_problem((128, 128, 128), steps=10, seed=22, dt=0.0, n_probe=2, bc=(1, 1, 1))
+    s = spstd.solver_for(p, precision=32, probe_capacity=64, stream=stream, device=local)
+    ms = timed(s, 10)
+    s.close()
+    flops = (3 * 2 * 128 + 2) * p.n_total * h_applied
+    out["walls_dirichlet_128^3_fp32"] = {"ms_per_step": ms, "value": p.n_total / (ms * 1e-3), "bound": "alu",
+                                         "alu_frac": flops / (ms * 1e-3) / 1e12 / alu_peak_tflops(32, sm_mhz)}
     # RK4
-    p = inputs.gaussian_problem((128, 128, 128), (-8.0,) * 3, (8.0,) * 3, seed=23, integrator="RK4", dt=0.0,
+    p = inputs.gaussian_problem((256, 256, 256), (-12.0,) * 3, (12.0,) * 3, seed=23, integrator="RK4", dt=0.0,
                                 steps=10, n_probe=2)
     s = spstd.solver_for(p, precision=32, probe_capacity=64, stream=stream, device=local, norm_drift_limit=0.0)
     ms = timed(s, 10)
     s.close()
-    out["rk4_128^3_fp32"] = {"ms_per_step": ms, "value": p.n_total / (ms * 1e-3), "bound": "hbm",
+    out["rk4_256^3_fp32"] = {"ms_per_step": ms, "value": p.n_total / (ms * 1e-3), "bound": "hbm",
                              "step_frac": 16 * 8 * p.n_total / (ms * 1e-3) / 1e9 / peak}
     # eigenstate accumulation
-    p = inputs.gaussian_problem((128, 128, 128), (-8.0,) * 3, (8.0,) * 3, seed=24, dt=0.0, steps=10, n_probe=2)
+    p = inputs.gaussian_problem((256, 256, 256), (-12.0,) * 3, (12.0,) * 3, seed=24, dt=0.0, steps=10, n_probe=2)
     s = spstd.solver_for(p, precision=32, probe_capacity=64, stream=stream, device=local, merge=False,
                          max_eigenstates=2)
     plain = timed(s, 10)
@@ -667,7 +667,7 @@ def next_rows_leg(peak, sm_mhz, local=0):
     s.spstd_eigenstates_end()
     s.close()
     extra = max(acc - plain, 1e-9)
-    out["eigen_accum_128^3_fp32_2_targets"] = {"ms_per_step": acc, "plain_ms_per_step": plain,
+    out["eigen_accum_256^3_fp32_2_targets"] = {"ms_per_step": acc, "plain_ms_per_step": plain,
                                                "extra_ms_per_step": acc - plain, "bound": "hbm",
                                                "accum_frac": 72 * p.n_total / (extra * 1e-3) / 1e9 / peak}
     return out
