@@ -415,6 +415,11 @@ struct spstd_ctx {
     // x pass with per-warp tiles (schedule 6): eligible, maps (psi_R, psi_I, tmp, V)
     bool xw_ok = false;
     CUtensorMap xwmap[4];
+    // RK4 comparison scheme: reduce-add maps of its stage fields t_R, t_I, h_R,
+    // h_I (fields 3..6) in the x, y and z views, so its H applications take the
+    // TMA passes too
+    bool rk_tma[3] = {false, false, false};
+    CUtensorMap rkmap[4][3];
     CUtensorMap srmap[3][2];
     // stored-tile passes (schedule 5, fused x-y): tma_st[axis]; [field][view]
     bool tma_st[3] = {false, false, false};
@@ -734,6 +739,13 @@ inline void setup_tma(spstd_ctx *ctx)
             else if (f < 3) ok = encode_red_map(&ctx->srmap[f][v - 1], base, cfg.n, v);
         }
         ctx->tma[v] = ok;
+        // the RK4 stage fields on the same boxes
+        if (ok && ctx->rk4) {
+            bool okr = true;
+            for (int f = 3; f <= 6 && okr; ++f)
+                okr = encode_red_map(&ctx->rkmap[f - 3][v], ctx->ptr(ctx->field_off(f)), cfg.n, v);
+            ctx->rk_tma[v] = okr;
+        }
         // per-warp x tiles (schedule 6)
         if (v == 0 && ok && xwarp_eligible(cfg.n[0])) {
             bool okw = true;
@@ -960,9 +972,19 @@ cudaError_t enqueue_apply(spstd_ctx *ctx, int fsrc, int fdst, int table, double 
         }
         const cpx<T> *tw = (const cpx<T> *)ctx->ptr(ctx->L.tw[ax]);
         if constexpr (sizeof(T) == 4) {
-            const bool red = ctx->tma[ax] && sv == 0, st = ctx->tma_st[ax] && sv == 5;
-            const bool xw = ax == 0 && ctx->xw_ok && sv == 6;
-            if ((red || st || xw) && fsrc <= 2 && fdst <= 2) {
+            // reduce-add map of field f in the view of axis ax (null where none)
+            auto redmap = [&](int f, int a) -> const CUtensorMap * {
+                if (f <= 2) return a == 0 ? &ctx->xrmap[f] : &ctx->srmap[f][a - 1];
+                if (f <= 6 && ctx->rk_tma[a]) return &ctx->rkmap[f - 3][a];
+                return nullptr;
+            };
+            const bool std_fields = fsrc <= 2 && fdst <= 2;
+            // the RK4 stage fields have block-tile reduce-add maps only
+            const bool red = ctx->tma[ax] && (sv == 0 || (sv == 6 && !std_fields)) && redmap(fsrc, ax) &&
+                             redmap(fdst, ax);
+            const bool st = ctx->tma_st[ax] && sv == 5 && std_fields;
+            const bool xw = ax == 0 && ctx->xw_ok && sv == 6 && std_fields;
+            if (red || st || xw) {
                 TmaPassArgs ta{};
                 ta.tw = (const float2 *)tw;
                 ta.mult = (const float *)(mult + off[ax]);
@@ -987,14 +1009,9 @@ cudaError_t enqueue_apply(spstd_ctx *ctx, int fsrc, int fdst, int table, double 
                                 launch_pass_xwarp((int)N, ctx->xwmap[fsrc], ctx->xwmap[3], ctx->xwmap[fdst], ta, s));
                 } else if (red) {
                     ta.n_tiles = tmared_tiles(ax, cfg.n, &ta.n_xt);
-                    if (ax == 0)
-                        SPSTD_TIMED(timer, s, ax,
-                                    launch_pass_tmared(0, (int)N, ctx->xrmap[fsrc], ctx->xrmap[3], ctx->xrmap[fdst],
-                                                       ta, s));
-                    else
-                        SPSTD_TIMED(timer, s, ax,
-                                    launch_pass_tmared(ax, (int)N, ctx->srmap[fsrc][ax - 1], ctx->xrmap[3],
-                                                       ctx->srmap[fdst][ax - 1], ta, s));
+                    SPSTD_TIMED(timer, s, ax,
+                                launch_pass_tmared(ax, (int)N, *redmap(fsrc, ax), ctx->xrmap[3], *redmap(fdst, ax), ta,
+                                                   s));
                 } else {
                     if (ax == 0) {
                         ta.n_tiles = (int)((n1 * n2 + tma_rows_per_tile() - 1) / tma_rows_per_tile());

@@ -130,3 +130,13 @@ def test_workspace_guard_damage_is_reported():
     s._ws[s.workspace_offset + psi_bytes + 7] = 0
     assert not s.spstd_check_workspace()
     s.close()
+
+
+def test_workspace_guards_intact_rk4():
+    """The RK4 comparison scheme's stage fields (reduce-add TMA passes on
+    fields of their own) stay inside their regions too."""
+    p = inputs.gaussian_problem((64, 64, 64), integrator="RK4", dt=0.0, steps=6, n_probe=2)
+    s = gpu_solver(p, 32, cap=8, norm_drift_limit=0.0)
+    s.spstd_step(6)
+    assert s.spstd_check_workspace()
+    s.close()
