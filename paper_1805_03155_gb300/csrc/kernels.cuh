@@ -439,35 +439,49 @@ struct DenseArgs {
     int64_t stride, inner, outer_stride, n_lines;
 };
 
-constexpr int kDenseThreads = 128;
+// Lines per block of the dense pass: the operator column each thread reads
+// (one entry per j, coalesced across the block, from L1/L2) serves this many
+// lines, whose values sit in shared memory as [n][kDenseLines] (a broadcast
+// 16-byte read gives four lines' values).
+constexpr int kDenseLines = 16;
+constexpr int kDenseMaxThreads = 256;  // one thread per output point (n <= SPSTD_MAX_DENSE_N = 256)
 
+// dst(i, line) += a sum_j D(i, j) src(j, line) (+ bV V src on the x axis) for
+// kDenseLines lines per block; thread i accumulates over j in order, so every
+// output rounds as a plain per-line loop would.
 template <typename T>
-__global__ void __launch_bounds__(kDenseThreads) dense_pass_kernel(const DenseArgs<T> a)
+__global__ void __launch_bounds__(kDenseMaxThreads) dense_pass_kernel(const DenseArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    T *lines = reinterpret_cast<T *>(smem);
+    T *X = reinterpret_cast<T *>(smem);  // [n][kDenseLines]
     const int n = a.n;
-    const int lb = kDenseThreads / n > 0 ? kDenseThreads / n : 1;  // lines per block
-    const int64_t l0 = (int64_t)blockIdx.x * lb;
-    // stage the block's lines
-    for (int k = threadIdx.x; k < lb * n; k += blockDim.x) {
-        const int64_t l = l0 + k / n;
-        if (l < a.n_lines) {
-            const int64_t base = (l / a.inner) * a.outer_stride + (l % a.inner);
-            lines[k] = a.src[base + (int64_t)(k % n) * a.stride];
-        }
+    const int64_t l0 = (int64_t)blockIdx.x * kDenseLines;
+    for (int k = threadIdx.x; k < n * kDenseLines; k += blockDim.x) {
+        const int j = k / kDenseLines, c = k % kDenseLines;
+        const int64_t l = l0 + c;
+        T v = T(0);
+        if (l < a.n_lines) v = a.src[(l / a.inner) * a.outer_stride + (l % a.inner) + (int64_t)j * a.stride];
+        X[k] = v;
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < lb * n; k += blockDim.x) {
-        const int64_t l = l0 + k / n;
-        if (l >= a.n_lines) continue;
-        const int i = k % n;
-        const T *line = lines + (k / n) * n;
-        T acc = T(0);
-        for (int j = 0; j < n; ++j) acc = fma(__ldg(a.D + (int64_t)j * n + i), line[j], acc);
+    const int i = threadIdx.x;
+    if (i >= n) return;
+    T acc[kDenseLines];
+#pragma unroll
+    for (int c = 0; c < kDenseLines; ++c) acc[c] = T(0);
+    for (int j = 0; j < n; ++j) {
+        const T d = __ldg(a.D + (int64_t)j * n + i);
+        const T *xj = X + j * kDenseLines;
+#pragma unroll
+        for (int c = 0; c < kDenseLines; ++c) acc[c] = fma(d, xj[c], acc[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < kDenseLines; ++c) {
+        const int64_t l = l0 + c;
+        if (l >= a.n_lines) break;
         const int64_t off = (l / a.inner) * a.outer_stride + (l % a.inner) + (int64_t)i * a.stride;
-        T r = a.dst[off] + a.a * acc;
-        if (a.use_V) r = fma(a.bV * a.V[off], line[i], r);
+        T r = a.dst[off] + a.a * acc[c];
+        if (a.use_V) r = fma(a.bV * a.V[off], X[i * kDenseLines + c], r);
         a.dst[off] = r;
     }
 }
@@ -597,13 +611,27 @@ __global__ void eigen_accum_kernel(const T *__restrict__ psiR, const T *__restri
         }
         __syncthreads();
         for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
-            const double zr = (double)psiR[p], zi = (double)psiI[p];
-            for (int t = 0; t < n_target; ++t) {
-                const double2 ph = s_ph[t];
-                double2 a = acc[(int64_t)t * n + p];
-                a.x += zr * ph.x - zi * ph.y;
-                a.y += zr * ph.y + zi * ph.x;
-                acc[(int64_t)t * n + p] = a;
+            if constexpr (sizeof(T) == 4) {
+                // FP32 fields: the product in FP32 (the fields carry no more), the
+                // running sum in FP64 -- two FP64 adds a target instead of four
+                // FP64 products, on a part whose FP64 rate is a small fraction of FP32
+                const float zr = psiR[p], zi = psiI[p];
+                for (int t = 0; t < n_target; ++t) {
+                    const float px = (float)s_ph[t].x, py = (float)s_ph[t].y;
+                    double2 a = acc[(int64_t)t * n + p];
+                    a.x += (double)fmaf(zr, px, -zi * py);
+                    a.y += (double)fmaf(zr, py, zi * px);
+                    acc[(int64_t)t * n + p] = a;
+                }
+            } else {
+                const double zr = (double)psiR[p], zi = (double)psiI[p];
+                for (int t = 0; t < n_target; ++t) {
+                    const double2 ph = s_ph[t];
+                    double2 a = acc[(int64_t)t * n + p];
+                    a.x += zr * ph.x - zi * ph.y;
+                    a.y += zr * ph.y + zi * ph.x;
+                    acc[(int64_t)t * n + p] = a;
+                }
             }
         }
     }

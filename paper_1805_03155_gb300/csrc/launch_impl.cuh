@@ -218,10 +218,10 @@ template <typename T>
 cudaError_t Launch<T>::dense_pass(const DenseArgs<T> &a, cudaStream_t s)
 {
     if (a.n_lines <= 0) return cudaSuccess;
-    const int lb = kDenseThreads / a.n > 0 ? kDenseThreads / a.n : 1;
-    const int64_t blocks = (a.n_lines + lb - 1) / lb;
-    const size_t smem = sizeof(T) * (size_t)lb * a.n;
-    dense_pass_kernel<T><<<(unsigned)blocks, kDenseThreads, smem, s>>>(a);
+    const int64_t blocks = (a.n_lines + kDenseLines - 1) / kDenseLines;
+    const int threads = (a.n + 31) / 32 * 32;
+    const size_t smem = sizeof(T) * (size_t)kDenseLines * a.n;
+    dense_pass_kernel<T><<<(unsigned)blocks, threads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
