@@ -367,7 +367,8 @@ def gate_summary(acc):
             "series_rel_err_max": max(z) if z else None}
 
 
-def batched_vs_plain(count=512, steps=800, plain_steps=40, precision=32, local=0, plain=True, check=True):
+def batched_vs_plain(count=512, steps=800, plain_steps=40, precision=32, local=0, plain=True, check=True,
+                     general_v=True):
     """The mixed 512-solve workload (1D wells 128..8192, 2D oscillators
     64^2..512^2, 3D oscillators 32^3, 48^3, 64^3 and 96^3; FP32 fields, FP64
     reductions, FR4): every member stepped through one batch (graph-replayed
@@ -376,8 +377,10 @@ def batched_vs_plain(count=512, steps=800, plain_steps=40, precision=32, local=0
     time on the batch stream.  The batch is timed over `steps` steps (after a
     warm-up of as many, which captures its graph), the plain leg over
     `plain_steps` steps per member; solves/s is extrapolated to the 5000-step
-    solves of the workload.  Accuracy gate: one member of every shape,
-    batched for 10000 steps, against lone FP64 solves (accuracy_batch)."""
+    solves of the workload.  The members' potentials separate (harmonic wells),
+    so every batched x pass rebuilds V from two tables; `general_v` times the
+    batch again with potentials that do not.  Accuracy gate: one member of every
+    shape, batched for 10000 steps, against lone FP64 solves (accuracy_batch)."""
     import torch
     from paper_1805_03155_gb300 import inputs, spstd
 
@@ -437,6 +440,34 @@ def batched_vs_plain(count=512, steps=800, plain_steps=40, precision=32, local=0
         except spstd.SpstdError as e:
             norms.append(getattr(e, "norm", float("nan")))
     dts = [s.spstd_get_dt() for s in solvers]
+    # the same mix with potentials that do not separate (V + 0.01 x y on the
+    # 2D and 3D members; 1D members are unchanged): every x pass reads its
+    # member's V field (16 B/pt) instead of rebuilding V from two tables
+    gv = None
+    if general_v:
+        for p, s in zip(probs, solvers):
+            if p.dims > 1:
+                x, y = p.coords()[:2]
+                V = p.V.reshape(-1, len(y), len(x)) + 0.01 * y[None, :, None] * x[None, None, :]
+                s.spstd_set_potential(V.ravel())
+                s.spstd_set_state(p.psiR, p.psiI)
+        sep_left = sum(s.spstd_potential_separable() for p, s in zip(probs, solvers) if p.dims > 1)
+        b = spstd.Batch(count + 1, device=local, stream=stream)
+        for s in solvers:
+            b.spstd_batch_add(s)
+        gv_steps = max(1, steps // 4)
+        b.spstd_batch_step(gv_steps)  # warm-up: captures the batch graph
+        b.spstd_batch_tune(reps=3)
+        ev[2].record(stream)
+        b.spstd_batch_step(gv_steps)
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+        gv_ms = ev[2].elapsed_time(ev[3])
+        b.close()
+        gv = {"value": pts * gv_steps / (gv_ms * 1e-3), "ms": gv_ms, "steps_timed": gv_steps,
+              "separable_members_left": int(sep_left),
+              "what": "the same members with V + 0.01 x y on the 2D and 3D ones, so that no potential "
+                      "separates and every batched x pass reads the V field"}
     for s in solvers:
         s.close()
     acc = accuracy_batch(probs, local, stream) if check else {}
@@ -451,7 +482,9 @@ def batched_vs_plain(count=512, steps=800, plain_steps=40, precision=32, local=0
                     "extrapolated_from": f"{steps} steps of every member in {batch_ms:.0f} ms",
                     "gpu_launches": launches, "schedules": tuned, "tune_s": tune_s,
                     "default_schedule_ms": default_ms,
-                    "default_schedule_value": pts * steps / (default_ms * 1e-3)},
+                    "default_schedule_value": pts * steps / (default_ms * 1e-3),
+                    "v_separable": "x passes rebuild V from separable tables (all 2D/3D members)"},
+        "batched_general_v": gv,
         "plain": {"value": pts * plain_steps / (plain_ms * 1e-3), "ms": plain_ms, "steps_timed": plain_steps,
                   "solves_per_s_5000_steps": count / (plain_ms * 1e-3 * 5000 / plain_steps),
                   "extrapolated_from": f"{plain_steps} steps of every member, one after another, in {plain_ms:.0f} ms",
@@ -761,9 +794,10 @@ def main():
     if args.batch_only:
         import torch
         torch.cuda.set_device(0)
-        r = batched_vs_plain(steps=args.batch_steps, plain=False, check=False)
+        r = batched_vs_plain(steps=args.batch_steps, plain=False, check=False, general_v=not args.no_general_v)
         print(json.dumps({"batch_only": True, **{k: r[k] for k in ("workload", "members", "grid_points", "steps",
-                                                                    "shapes3d", "batched", "unit")}}))
+                                                                    "shapes3d", "batched", "batched_general_v",
+                                                                    "unit")}}))
         return 0
 
     import torch

@@ -138,6 +138,14 @@ typedef struct {
                              dt or corrupted fields.  spstd_config_init sets
                              1e-3; <= 0 turns the check off (e.g. for the RK4
                              comparison, whose norm decays by design). */
+    int v_field_only;     /* 0 (default): an FP32 grid whose potential separates,
+                             V(x, y, z) = vx(x) + vyz(y, z) to 4 units in the
+                             last place, gets the two FP32 tables, and the V
+                             field holds their FP32 sums; the reduce-add x passes
+                             (single grid and batched) then rebuild the V term
+                             from the tables (12 instead of 16 B per point) with
+                             the same bits.  1: every pass reads the V field
+                             (Eq. 16's V at every point, as for any potential). */
 } spstd_config;
 
 /* Boundary conditions (Section 2.2).  Periodic axes whose length is a power of

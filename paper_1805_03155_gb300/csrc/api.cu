@@ -216,11 +216,13 @@ spstd_status spstd_set_potential(spstd_ctx *ctx, const double *V)
         if (!std::isfinite(V[i])) return fail(ctx, SPSTD_EINVAL, "V has a non-finite value");
         vmax = std::max(vmax, V[i]);
     }
-    // kernel arguments name the tables (or not): replayed graphs are rebuilt
+    // kernel arguments name the tables (or not): replayed graphs are rebuilt,
+    // and so are the descriptors of a batch the context belongs to
     drop_graph(ctx);
+    batch_member_changed(ctx->batch);
     ctx->vsep = false;
-    // the table form of the x pass exists for power-of-two lines
-    if (ctx->cfg.precision == 32 && ctx->tma[0] && is_pow2(ctx->cfg.n[0])) {
+    // the table form belongs to the reduce-add x passes
+    if (ctx->cfg.precision == 32 && ctx->tma[0] && !ctx->cfg.v_field_only) {
         const int64_t n0 = ctx->cfg.n[0], rows = ctx->cfg.n[1] * ctx->cfg.n[2];
         std::vector<float> vx, vyz;
         if (separable_tables(V, n0, rows, vsep_rows_padded(rows), vx, vyz)) {

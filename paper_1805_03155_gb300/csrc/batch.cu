@@ -41,6 +41,7 @@ struct BatchGroupND {
     int sched[3];      // pass schedule per axis (0..4; 0 is the TMA pass where tma[ax])
     bool tma[3];       // axis can run the batched reduce-add TMA pass
     bool fxy;          // x and y run as the batched fused x-y pass (while both are on schedule 0)
+    bool vsep;         // every member has separable-potential tables: the x pass takes the table form
     size_t args_off;   // PassArgs<T> [nh * dims][M]
     size_t probe_off;  // ProbeMember<T> [M]
     size_t tma_off;    // TmaMember [M] (when any tma[ax])
@@ -116,6 +117,12 @@ PassArgs<T> member_pass_args(spstd_ctx *ctx, const HalfStage &h, int ax)
         a.bV = (T)h.bV;
         a.use_V = 1;
         a.n_rows = n1 * n2;
+        if constexpr (sizeof(T) == 4) {
+            if (ctx->vsep) {
+                a.vx = (const T *)ctx->ptr(ctx->L.vsep_x);
+                a.vyz = (const T *)ctx->ptr(ctx->L.vsep_yz);
+            }
+        }
     } else {
         a.stride = ax == 1 ? n0 : n0 * n1;
         a.outer_stride = ax == 1 ? n0 * n1 : n0;
@@ -198,6 +205,7 @@ cudaError_t group_pass(const BatchGroupND &g, int ax, int v, const PassArgs<T> *
             tmared_tiles(ax, g.n, &ta.n_xt);
             ta.nx = (int)g.n[0];
             ta.planes = red_planes(g.n, ax);
+            ta.vsep = ax == 0 && g.vsep;
             ta.axis = ax;
             return launch_pass_tmared_batch(ax, N, ta, s);
         }
@@ -240,6 +248,8 @@ void build_nd_descriptors(spstd_batch *b, BatchGroupND &g, std::vector<unsigned 
         any |= ok;
     }
     g.tma_off = 0;
+    g.vsep = g.tma[0];
+    for (int i = 0; i < M && g.vsep; ++i) g.vsep = b->slots[g.slots[i]]->vsep;
     g.fxy = any && g.tma[0] && g.tma[1];
     for (int i = 0; i < M && g.fxy; ++i) g.fxy = b->slots[g.slots[i]]->fxy_ok && b->slots[g.slots[i]]->fxy_on;
     if (any) {
@@ -429,6 +439,13 @@ cudaError_t batch_prepare(spstd_batch *b)
 }
 
 }  // namespace
+
+namespace spstd_host {
+void batch_member_changed(spstd_batch *b)
+{
+    if (b) b->dirty = true;
+}
+}  // namespace spstd_host
 
 extern "C" {
 

@@ -489,6 +489,11 @@ inline spstd_status check_device_status(spstd_ctx *ctx)
     return SPSTD_OK;
 }
 
+// A batch's descriptors hold its members' dt-derived coefficients and table
+// pointers: a member whose potential (hence dt or table form) changes makes the
+// batch rebuild them before its next step (batch.cu).
+void batch_member_changed(spstd_batch *b);
+
 inline void drop_graph(spstd_ctx *ctx)
 {
     if (ctx->gexec) {

@@ -31,6 +31,9 @@ struct PassArgs {
     int64_t n_outer;        // strided pass: number of line groups
     int nx;                 // strided pass: columns (points along x)
     int reverse;            // walk the tiles in reverse order (L2 reuse)
+    // x pass of a batch member with a separable potential (FP32): the tables
+    // V = vx(x) + vyz(row) whose FP32 sums the V field holds (null: none)
+    const T *vx, *vyz;
 };
 
 constexpr int kMaxHalfStages = 16;

@@ -146,6 +146,7 @@ struct TmaBatchArgs {
     int nx;            // points along x
     int planes;        // strided pass: tmared_planes()
     int axis;
+    int vsep;          // x pass: every member has separable-potential tables (pa[i].vx, pa[i].vyz)
 };
 
 cudaError_t launch_pass_tmared_batch(int axis, int N, const TmaBatchArgs &a, cudaStream_t s);

@@ -142,14 +142,10 @@ cudaError_t red_x_n(int N, const CUtensorMap *ms, const CUtensorMap *mv, const C
     case 128: return red_x<128, BATCH, VSEP>(ms, mv, md, a, ba, s);
     case 256: return red_x<256, BATCH, VSEP>(ms, mv, md, a, ba, s);
     case 512: return red_x<512, BATCH, VSEP>(ms, mv, md, a, ba, s);
-    default: break;
+    case 48: return red_x<48, BATCH, VSEP>(ms, mv, md, a, ba, s);
+    case 96: return red_x<96, BATCH, VSEP>(ms, mv, md, a, ba, s);
+    default: return cudaErrorInvalidValue;
     }
-    // 3 * 2^k lines read the V field (no separable table form)
-    if constexpr (!VSEP) {
-        if (N == 48) return red_x<48, BATCH, false>(ms, mv, md, a, ba, s);
-        if (N == 96) return red_x<96, BATCH, false>(ms, mv, md, a, ba, s);
-    }
-    return cudaErrorInvalidValue;
 }
 
 template <bool BATCH>
@@ -159,19 +155,18 @@ cudaError_t red_any(int axis, int N, int64_t nx, int K, const CUtensorMap *ms, c
     if (!tmared_eligible(N)) return cudaErrorInvalidValue;
     if (axis == 0) {
         if (nx != N) return cudaErrorInvalidValue;
-        if constexpr (!BATCH) {
-            // a single grid with a separable potential takes the table form; the
-            // set-up call (no args) prepares both forms (the table form exists
-            // for power-of-two lines)
-            if (!a) {
-                if (N % 3) {
-                    const cudaError_t e = red_x_n<false, true>(N, ms, mv, md, a, ba, s);
-                    if (e != cudaSuccess) return e;
-                }
-            } else if (a->vyz) {
-                if (!a->vx) return cudaErrorInvalidValue;
-                return red_x_n<false, true>(N, ms, mv, md, a, ba, s);
-            }
+        // a separable potential takes the table form (a single grid with
+        // a->vyz set; a batch whose members all have tables, ba->vsep); the
+        // set-up call (no args) prepares both forms
+        const bool setup = BATCH ? !ba : !a;
+        if (setup) {
+            const cudaError_t e = red_x_n<BATCH, true>(N, ms, mv, md, a, ba, s);
+            if (e != cudaSuccess) return e;
+        } else if constexpr (BATCH) {
+            if (ba->vsep) return red_x_n<true, true>(N, ms, mv, md, a, ba, s);
+        } else if (a->vyz) {
+            if (!a->vx) return cudaErrorInvalidValue;
+            return red_x_n<false, true>(N, ms, mv, md, a, ba, s);
         }
         return red_x_n<BATCH, false>(N, ms, mv, md, a, ba, s);
     }

@@ -366,18 +366,23 @@ __device__ __forceinline__ void reduce_tile(const CUtensorMap *map, const TileAt
 // ---------------------------------------------------------------------------
 template <int N, int E, bool BATCH, bool VSEP = false>
 struct XRed {
-    static_assert(!(BATCH && VSEP), "batches read the V field");
     static constexpr int TT = N / E;
     static constexpr int ROWS = tmared_rows_x(N);
     static constexpr int LP = ROWS / 2;
     static constexpr int THREADS = LP * TT;
     static constexpr int TILE = ROWS * N;
     // stage: src (+ V) tile; with a separable potential, src and the tile's
-    // ROWS values of vyz, so twice as many stages fit
+    // ROWS values of vyz, so more stages fit (single grids: three blocks per
+    // SM; batched, a stage also carries its member's multiplier and vx rows,
+    // and the stages are counted with them)
     static constexpr int PARTS = VSEP ? 1 : 2;
     static constexpr int BLOCKS = VSEP ? 3 : kRedBlocks;
-    static constexpr int S = tmared_stages<TILE, PARTS, BLOCKS>();
-    static constexpr size_t SEP_SMEM = VSEP ? 16 + (size_t)S * ROWS * sizeof(float) + N * sizeof(float) : 0;
+    static constexpr size_t SEP_STAGE = (size_t)(TILE + 2 * N + ROWS) * sizeof(float);
+    static constexpr int S = !(BATCH && VSEP) ? tmared_stages<TILE, PARTS, BLOCKS>()
+                             : kTmaRedRing / BLOCKS / SEP_STAGE < 8 ? (int)(kTmaRedRing / BLOCKS / SEP_STAGE) : 8;
+    // vyz values [S][ROWS], then vx (one row; batched [S] rows)
+    static constexpr size_t SEP_SMEM =
+        VSEP ? 16 + (size_t)S * ROWS * sizeof(float) + (BATCH ? S : 1) * (size_t)N * sizeof(float) : 0;
     static constexpr size_t SMEM = tmared_smem<N, TILE, PARTS, S, BATCH>() + SEP_SMEM;
 };
 
@@ -392,10 +397,11 @@ xpass_tmared_kernel(const __grid_constant__ CUtensorMap msrc, const __grid_const
     extern __shared__ unsigned char smem_raw[];
     const TmaRedSmem m = tmared_carve<N, TILE, G::PARTS, S, BATCH>(smem_raw);
     const int t = threadIdx.x, l = threadIdx.y, tid = l * TT + t;
-    // separable potential: [S][ROWS] vyz values (one bulk copy per stage), then vx
+    // separable potential: [S][ROWS] vyz values (one bulk copy per stage), then
+    // vx (single grid: one row; batched: [S] rows, the tile's member's)
     float *vrow = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(m.full + S) + 15) & ~uintptr_t(15));
     float *vxt = vrow + S * ROWS;
-    if constexpr (VSEP)
+    if constexpr (VSEP && !BATCH)
         for (int i = tid; i < N; i += G::THREADS) vxt[i] = a.vx[i];
     tmared_setup<N, S>(m, BATCH ? ba.tw : a.tw, BATCH ? nullptr : a.mult, tid, G::THREADS);
     const bool useV = BATCH || VSEP || a.use_V != 0;
@@ -415,10 +421,18 @@ xpass_tmared_kernel(const __grid_constant__ CUtensorMap msrc, const __grid_const
         const TileAt c = at(k);
         if constexpr (BATCH) {
             const TmaMember *mm = ba.mem + c.i;
-            mbar_arrive_expect_tx(&m.full[s], 2 * kTileBytes + N * sizeof(float));
-            load_tile(m.src + s * TILE, &mm->x[fsrc], c, &m.full[s]);
-            load_v_tile(m.vt + s * TILE, &mm->x[3], c, &m.full[s]);
-            bulk_load(m.mult + s * N, ba.pa[c.i].mult, N * sizeof(float), &m.full[s]);
+            const PassArgs<float> &pm = ba.pa[c.i];
+            if constexpr (VSEP) {
+                mbar_arrive_expect_tx(&m.full[s], kTileBytes + (2 * N + ROWS) * sizeof(float));
+                load_tile(m.src + s * TILE, &mm->x[fsrc], c, &m.full[s]);
+                bulk_load(vrow + s * ROWS, pm.vyz + c.c[2], ROWS * sizeof(float), &m.full[s]);
+                bulk_load(vxt + s * N, pm.vx, N * sizeof(float), &m.full[s]);
+            } else {
+                mbar_arrive_expect_tx(&m.full[s], 2 * kTileBytes + N * sizeof(float));
+                load_tile(m.src + s * TILE, &mm->x[fsrc], c, &m.full[s]);
+                load_v_tile(m.vt + s * TILE, &mm->x[3], c, &m.full[s]);
+            }
+            bulk_load(m.mult + s * N, pm.mult, N * sizeof(float), &m.full[s]);
         } else {
             mbar_arrive_expect_tx(&m.full[s], VSEP ? kTileBytes + ROWS * sizeof(float) : (useV ? 2 : 1) * kTileBytes);
             // failure-path test hook: the launch's first tile may be left unloaded
@@ -447,7 +461,13 @@ xpass_tmared_kernel(const __grid_constant__ CUtensorMap msrc, const __grid_const
             float mr[E];
 #pragma unroll
             for (int e = 0; e < E; ++e) mr[e] = m.mult[s * N + t + e * TT];
-            xred_tile<N, E>(src, m.vt + s * TILE, mr, m.tw, ba.pa[c.i].bV, true, t, l);
+            if constexpr (VSEP) {
+                XTile<N, E> x;
+                x.load_sep(src, vxt + s * N, vrow[s * ROWS + 2 * l], vrow[s * ROWS + 2 * l + 1], ba.pa[c.i].bV, t, l);
+                x.finish(src, mr, m.tw, nullptr);
+            } else {
+                xred_tile<N, E>(src, m.vt + s * TILE, mr, m.tw, ba.pa[c.i].bV, true, t, l);
+            }
         } else if constexpr (VSEP) {
             XTile<N, E> x;
             x.load_sep(src, vxt, vrow[s * ROWS + 2 * l], vrow[s * ROWS + 2 * l + 1], a.bV, t, l);

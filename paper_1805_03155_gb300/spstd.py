@@ -59,6 +59,7 @@ class spstd_config(C.Structure):
         ("unmerged_steps", C.c_int),
         ("no_graph", C.c_int),
         ("norm_drift_limit", C.c_double),
+        ("v_field_only", C.c_int),
     ]
 
 
@@ -148,7 +149,8 @@ def _dp(a):
 
 def make_config(dims, n, lo, hi, precision=64, integrator="FR4", dt=0.0, probes=(), probe_capacity=1024,
                 max_nfft=0, hbar=1.0, mass=1.0, nyquist_zero=False, c=None, d=None, device=0, stream=None,
-                bc=(0, 0, 0), merge=True, max_eigenstates=0, no_graph=False, norm_drift_limit=1e-3):
+                bc=(0, 0, 0), merge=True, max_eigenstates=0, no_graph=False, norm_drift_limit=1e-3,
+                v_field_only=False):
     cfg = spstd_config()
     lib().spstd_config_init(C.byref(cfg))
     cfg.dims = int(dims)
@@ -186,6 +188,7 @@ def make_config(dims, n, lo, hi, precision=64, integrator="FR4", dt=0.0, probes=
     cfg.max_eigenstates = int(max_eigenstates)
     cfg.no_graph = int(bool(no_graph))
     cfg.norm_drift_limit = float(norm_drift_limit)
+    cfg.v_field_only = int(bool(v_field_only))
     return cfg
 
 
@@ -501,7 +504,7 @@ def spstd_norm_noalloc(psiR_ptr, psiI_ptr, n, precision, cell_volume, out_ptr, s
 
 
 def solver_for(problem, precision=64, probe_capacity=None, stream=None, device=0, dt=None, merge=True,
-               max_eigenstates=0, no_graph=False, norm_drift_limit=1e-3):
+               max_eigenstates=0, no_graph=False, norm_drift_limit=1e-3, v_field_only=False):
     """Creates a Solver for an inputs.Problem and uploads V and the state."""
     cap = probe_capacity if probe_capacity is not None else max(1, problem.steps)
     cfg = make_config(problem.dims, problem.n[: problem.dims], problem.lo[: problem.dims],
@@ -509,7 +512,8 @@ def solver_for(problem, precision=64, probe_capacity=None, stream=None, device=0
                       dt=problem.dt if dt is None else dt, probes=problem.probes, probe_capacity=cap,
                       max_nfft=problem.nfft if problem.nfft else 0, hbar=problem.hbar, mass=problem.mass,
                       device=device, bc=getattr(problem, "bc", (0, 0, 0)), merge=merge,
-                      max_eigenstates=max_eigenstates, no_graph=no_graph, norm_drift_limit=norm_drift_limit)
+                      max_eigenstates=max_eigenstates, no_graph=no_graph, norm_drift_limit=norm_drift_limit,
+                      v_field_only=v_field_only)
     s = Solver(cfg, stream=stream)
     s.spstd_set_potential(problem.V)
     s.spstd_set_state(problem.psiR, problem.psiI)
