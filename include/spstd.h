@@ -296,9 +296,10 @@ spstd_status spstd_profile_steps(spstd_ctx *ctx, int64_t nsteps, double *ms, int
  *   4  plain pass, default plan (listed only where 0 is the TMA pass)
  *   5  TMA pass that loads the destination tile into shared memory, adds
  *      there and stores it back (listed only where 0 is the TMA pass)
- *   6  x axes of 32..256 points of single FP32 2D/3D grids: the reduce-add
- *      TMA pass with per-warp tiles (each warp its own ring of stages and
- *      barriers); the same arithmetic as 0, so the same bits
+ *   6  x axes of 32, 48, 64, 96, 128 or 256 points of FP32 2D/3D grids
+ *      (single and batched): the reduce-add TMA pass with per-warp tiles
+ *      (each warp its own ring of stages and barriers); the same arithmetic
+ *      as 0, so the same bits
  * Schedules 1..3 exist for FFT axes of 32..512 points.  0, 1, 2 and 4 give
  * bit-identical results on plain axes; 3 changes the rounding (FP32 ~1e-7).
  * spstd_schedule_candidates lists the schedules axis (0..dims-1) can run in
@@ -423,16 +424,25 @@ spstd_status spstd_batch_sync(spstd_batch *b);
 spstd_status spstd_batch_launch_count(const spstd_batch *b, int64_t nsteps, int64_t *launches);
 const char *spstd_batch_last_error(const spstd_batch *b);
 /* Autotunes the batched passes: for every 2D/3D member shape and axis, times
- * the batched pass under schedules 0..4 over all members of that shape
+ * the batched pass under schedules 0..4 and 6 over all members of that shape
  * (0 = the default: the pipelined TMA reduce-add pass over every member's
- * tiles for FP32 axes of 32..512 points, else the plain plan; 1..3 as for a
- * lone context; 4 = the plain plan where 0 is the TMA pass) -- H applied into each member's scratch field, once to
- * warm up then reps times -- and keeps the fastest.  The choice is kept per
+ * tiles for FP32 axes of 32..512, 48 or 96 points, else the plain plan; 1..3 as
+ * for a lone context; 4 = the plain plan where 0 is the TMA pass; 6 = the x
+ * pass on per-warp tiles, for x lines where a lone context lists it) -- H
+ * applied into each member's scratch field, once to warm up then reps times --
+ * and keeps the fastest.  The choice is kept per
  * shape (precision, dims, n) for as long as the batch lives, including members
  * added later; the states are not touched.  Synchronises the batch stream. */
 spstd_status spstd_batch_tune(spstd_batch *b, int reps);
 /* The batch's schedules for a member shape (0 where not tuned); n: 3 sizes. */
 spstd_status spstd_batch_get_schedule(const spstd_batch *b, int precision, int dims, const int64_t *n, int *schedule);
+/* Sets the schedules of a 2D/3D member shape (precision 32/64, dims, n: 3
+ * sizes, schedule: dims values) as spstd_batch_tune would, for members present
+ * and added later; the batch re-captures its graph at the next step.  Allowed
+ * per axis: 0, 4, 1..3 where a lone context of that shape lists them, and 6 on
+ * the x axis of FP32 shapes whose x lines take per-warp tiles (a group whose
+ * members lack those maps runs 0 instead).  SPSTD_EINVAL otherwise. */
+spstd_status spstd_batch_set_schedule(spstd_batch *b, int precision, int dims, const int64_t *n, const int *schedule);
 
 /* Human-readable text of the last failure on ctx (never NULL). */
 const char *spstd_last_error(const spstd_ctx *ctx);

@@ -22,7 +22,7 @@ namespace {
 
 constexpr int kBatchGraphSteps = 10;
 constexpr int kBatchStreams = 4;
-constexpr size_t kBatchBytesPerMember = 8192;
+constexpr size_t kBatchBytesPerMember = 16384;
 
 struct BatchGroup1D {
     int precision;
@@ -42,6 +42,7 @@ struct BatchGroupND {
     bool tma[3];       // axis can run the batched reduce-add TMA pass
     bool fxy;          // x and y run as the batched fused x-y pass (while both are on schedule 0)
     bool vsep;         // every member has separable-potential tables: the x pass takes the table form
+    bool xw;           // every member has per-warp x maps: the x axis may run schedule 6
     size_t args_off;   // PassArgs<T> [nh * dims][M]
     size_t probe_off;  // ProbeMember<T> [M]
     size_t tma_off;    // TmaMember [M] (when any tma[ax])
@@ -166,13 +167,22 @@ size_t put(std::vector<unsigned char> &img, const void *src, size_t bytes)
 }
 
 // Whether schedule v of axis ax runs the batched TMA pass.
-bool group_uses_tma(const BatchGroupND &g, int ax, int v) { return v == 0 && g.tma[ax]; }
+// Schedules of a batched pass (sched.h): 0 the reduce-add TMA pass (block
+// tiles) where g.tma[ax], 6 its per-warp x tiles where g.xw, 1..4 plain plans.
+bool group_uses_tma(const BatchGroupND &g, int ax, int v)
+{
+    return (v == 0 && g.tma[ax]) || (v == 6 && ax == 0 && g.xw);
+}
 
 // Blocks per member of a batched pass of axis ax under schedule v (4: the
 // plain default where 0 is the TMA pass).
 template <typename T>
 int group_tiles(const BatchGroupND &g, int ax, int v)
 {
+    if (v == 6 && group_uses_tma(g, ax, v)) {
+        const int R = xwarp_rows((int)g.n[0]);
+        return (int)((g.n[1] * g.n[2] + R - 1) / R);
+    }
     if (group_uses_tma(g, ax, v)) return tmared_tiles(ax, g.n, nullptr);
     if (v == 4) v = 0;
     if (ax == 0)
@@ -193,7 +203,7 @@ cudaError_t group_pass(const BatchGroupND &g, int ax, int v, const PassArgs<T> *
     const int N = (int)g.n[ax];
     if constexpr (sizeof(T) == 4) {
         if (group_uses_tma(g, ax, v)) {
-            if (!a) return prepare_pass_tmared_batch(ax, N, g.n[0], red_planes(g.n, ax));
+            if (!a) return v == 6 ? prepare_pass_xwarp_batch(N) : prepare_pass_tmared_batch(ax, N, g.n[0], red_planes(g.n, ax));
             TmaBatchArgs ta{};
             ta.mem = mem;
             ta.pa = a;
@@ -207,7 +217,7 @@ cudaError_t group_pass(const BatchGroupND &g, int ax, int v, const PassArgs<T> *
             ta.planes = red_planes(g.n, ax);
             ta.vsep = ax == 0 && g.vsep;
             ta.axis = ax;
-            return launch_pass_tmared_batch(ax, N, ta, s);
+            return v == 6 ? launch_pass_xwarp_batch(N, ta, s) : launch_pass_tmared_batch(ax, N, ta, s);
         }
     }
     if (v == 4) v = 0;
@@ -250,6 +260,8 @@ void build_nd_descriptors(spstd_batch *b, BatchGroupND &g, std::vector<unsigned 
     g.tma_off = 0;
     g.vsep = g.tma[0];
     for (int i = 0; i < M && g.vsep; ++i) g.vsep = b->slots[g.slots[i]]->vsep;
+    g.xw = g.tma[0];
+    for (int i = 0; i < M && g.xw; ++i) g.xw = b->slots[g.slots[i]]->xw_ok;
     g.fxy = any && g.tma[0] && g.tma[1];
     for (int i = 0; i < M && g.fxy; ++i) g.fxy = b->slots[g.slots[i]]->fxy_ok && b->slots[g.slots[i]]->fxy_on;
     if (any) {
@@ -258,8 +270,10 @@ void build_nd_descriptors(spstd_batch *b, BatchGroupND &g, std::vector<unsigned 
             spstd_ctx *ctx = b->slots[g.slots[i]];
             TmaMember &t = tm[i];
             std::memset(&t, 0, sizeof(t));
-            for (int f = 0; f < 4; ++f)
+            for (int f = 0; f < 4; ++f) {
                 if (g.tma[0]) t.x[f] = ctx->xrmap[f];
+                if (g.xw) t.xw[f] = ctx->xwmap[f];
+            }
             for (int f = 0; f < 3; ++f) {
                 if (g.tma[1]) t.y[f] = ctx->srmap[f][0];
                 if (g.tma[2]) t.z[f] = ctx->srmap[f][1];
@@ -270,6 +284,8 @@ void build_nd_descriptors(spstd_batch *b, BatchGroupND &g, std::vector<unsigned 
         }
         g.tma_off = put(img, tm.data(), sizeof(TmaMember) * tm.size());
     }
+    // a tuned per-warp x schedule needs every member's per-warp maps
+    if (g.sched[0] == 6 && !g.xw) g.sched[0] = 0;
     for (int ax = 0; ax < g.dims; ++ax) g.tiles[ax] = group_tiles<T>(g, ax, g.sched[ax]);
 }
 
@@ -685,15 +701,18 @@ const char *spstd_batch_last_error(const spstd_batch *b)
 namespace {
 
 // Times the batched passes of one member shape under each schedule on the
-// members' scratch fields and keeps the fastest per axis.
+// members' scratch fields and keeps the fastest per axis; where the group can
+// run the fused x-y pass (which schedule 0 on x and y selects), that pass is
+// timed against the fastest separate x and y passes.
 template <typename T>
 spstd_status tune_group(spstd_batch *b, BatchGroupND &g, int reps, cudaEvent_t e0, cudaEvent_t e1)
 {
     const int M = (int)g.slots.size();
     const size_t off = (b->img_bytes + 255) & ~size_t(255);
-    if (M == 0 || off + sizeof(PassArgs<T>) * (size_t)M > b->ws_bytes) return SPSTD_OK;  // no room: defaults
+    if (M == 0 || off + 2 * sizeof(PassArgs<T>) * (size_t)M > b->ws_bytes) return SPSTD_OK;  // no room: defaults
     PassArgs<T> *dargs = (PassArgs<T> *)(b->ws + off);
     std::vector<PassArgs<T>> args(M);
+    double axis_ms[3] = {0.0, 0.0, 0.0};
     for (int ax = 0; ax < g.dims; ++ax) {
         for (int i = 0; i < M; ++i) {
             spstd_ctx *ctx = b->slots[g.slots[i]];
@@ -705,9 +724,10 @@ spstd_status tune_group(spstd_batch *b, BatchGroupND &g, int reps, cudaEvent_t e
         double best_ms = 0.0;
         const TmaMember *mem = (const TmaMember *)(b->ws + g.tma_off);
         const int fsrc = 1 - b->slots[g.slots[0]]->hs[0].dst;
-        for (int v = 0; v <= 4; ++v) {
+        for (int v = 0; v <= 6; ++v) {
             if (v >= 1 && v <= 3 && !sched_valid<T>(ax, (int)g.n[ax], v)) continue;
             if (v == 4 && !g.tma[ax]) continue;
+            if (v == 5 || (v == 6 && !group_uses_tma(g, ax, 6))) continue;
             const int tiles = group_tiles<T>(g, ax, v);
             SPSTD_BCU(b, group_pass<T>(g, ax, v, dargs, M, tiles, b->stream, mem, fsrc, 2));
             SPSTD_BCU(b, cudaEventRecord(e0, b->stream));
@@ -724,6 +744,41 @@ spstd_status tune_group(spstd_batch *b, BatchGroupND &g, int reps, cudaEvent_t e
         }
         g.sched[ax] = best;
         g.tiles[ax] = group_tiles<T>(g, ax, best);
+        axis_ms[ax] = best_ms;
+    }
+    if constexpr (sizeof(T) == 4) {
+        if (g.fxy && (g.sched[0] != 0 || g.sched[1] != 0)) {
+            std::vector<PassArgs<T>> xy(2 * (size_t)M);
+            for (int i = 0; i < M; ++i) {
+                spstd_ctx *ctx = b->slots[g.slots[i]];
+                for (int ax = 0; ax < 2; ++ax) {
+                    xy[(size_t)ax * M + i] = member_pass_args<T>(ctx, ctx->hs[0], ax);
+                    xy[(size_t)ax * M + i].dst = field_ptr<T>(ctx, 2);
+                }
+            }
+            SPSTD_BCU(b, cudaMemcpyAsync(dargs, xy.data(), sizeof(PassArgs<T>) * 2 * M, cudaMemcpyHostToDevice,
+                                         b->stream));
+            TmaBatchArgs fa{};
+            fa.mem = (const TmaMember *)(b->ws + g.tma_off);
+            fa.pa = (const PassArgs<float> *)dargs;
+            fa.pa_y = (const PassArgs<float> *)dargs + M;
+            fa.tw = (const float2 *)g.tw[0];
+            fa.src = 1 - b->slots[g.slots[0]]->hs[0].dst;
+            fa.dst = 2;
+            fa.members = M;
+            fa.tiles = fxy_units(g.n);
+            SPSTD_BCU(b, launch_pass_fxy_batch((int)g.n[0], fa, b->stream));
+            SPSTD_BCU(b, cudaEventRecord(e0, b->stream));
+            for (int r = 0; r < reps; ++r) SPSTD_BCU(b, launch_pass_fxy_batch((int)g.n[0], fa, b->stream));
+            SPSTD_BCU(b, cudaEventRecord(e1, b->stream));
+            SPSTD_BCU(b, cudaEventSynchronize(e1));
+            float t = 0.f;
+            SPSTD_BCU(b, cudaEventElapsedTime(&t, e0, e1));
+            if (t < axis_ms[0] + axis_ms[1]) {
+                g.sched[0] = g.sched[1] = 0;
+                for (int ax = 0; ax < 2; ++ax) g.tiles[ax] = group_tiles<T>(g, ax, 0);
+            }
+        }
     }
     TunedShape ts{g.precision, g.dims, {g.n[0], g.n[1], g.n[2]}, {g.sched[0], g.sched[1], g.sched[2]}};
     bool found = false;
@@ -768,6 +823,30 @@ spstd_status spstd_batch_tune(spstd_batch *b, int reps)
         b->gexec = nullptr;
     }
     return st;
+}
+
+spstd_status spstd_batch_set_schedule(spstd_batch *b, int precision, int dims, const int64_t *n, const int *schedule)
+{
+    if (!b || !n || !schedule || (precision != 32 && precision != 64) || dims < 2 || dims > 3) return SPSTD_EINVAL;
+    TunedShape ts{precision, dims, {n[0], dims > 1 ? n[1] : 1, dims > 2 ? n[2] : 1}, {0, 0, 0}};
+    for (int a = 0; a < dims; ++a) {
+        const int v = schedule[a];
+        const bool ok = v == 0 || v == 4 || (v == 6 && a == 0 && precision == 32 && xwarp_eligible(n[0])) ||
+                        (v >= 1 && v <= 3 &&
+                         (precision == 32 ? sched_valid<float>(a, (int)n[a], v) : sched_valid<double>(a, (int)n[a], v)));
+        if (!ok) return bfail(b, SPSTD_EINVAL, "schedule not available for this shape and axis");
+        ts.sched[a] = v;
+    }
+    bool found = false;
+    for (TunedShape &t : b->tuned)
+        if (t.precision == ts.precision && t.dims == ts.dims && t.n[0] == ts.n[0] && t.n[1] == ts.n[1] &&
+            t.n[2] == ts.n[2]) {
+            t = ts;
+            found = true;
+        }
+    if (!found) b->tuned.push_back(ts);
+    b->dirty = true;  // groups pick the schedule up when the batch is rebuilt
+    return SPSTD_OK;
 }
 
 spstd_status spstd_batch_get_schedule(const spstd_batch *b, int precision, int dims, const int64_t *n, int *schedule)

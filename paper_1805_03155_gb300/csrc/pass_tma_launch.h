@@ -109,12 +109,16 @@ cudaError_t launch_pass_tmared(int axis, int N, const CUtensorMap &msrc, const C
 // before a stream capture); nx: points along x.
 cudaError_t prepare_pass_tmared(int axis, int N, int64_t nx, int planes);
 
-// x pass with per-warp tiles (schedule 6; single grids): lines of N in {32,
-// 64, 128, 256} points, tiles of xwarp_rows(N) rows (the box height of its
-// maps); a.n_tiles = ceil(rows / xwarp_rows(N)).  The table form is taken when
-// a.vyz is set.
-constexpr bool xwarp_eligible(int64_t N) { return N == 32 || N == 64 || N == 128 || N == 256; }
-constexpr int xwarp_rows(int N) { return 2 * (32 / (N / 16)); }
+// x pass with per-warp tiles (schedule 6): lines of N in {32, 48, 64, 96,
+// 128, 256} points (a line's N/E threads, E = 16 or 12 for 3 * 2^k, share a
+// warp with the other line pairs of its tile), tiles of xwarp_rows(N) rows (the
+// box height of its maps).  Single grid: a.n_tiles = ceil(rows /
+// xwarp_rows(N)); the table form is taken when a.vyz is set.
+constexpr bool xwarp_eligible(int64_t N)
+{
+    return N == 32 || N == 48 || N == 64 || N == 96 || N == 128 || N == 256;
+}
+constexpr int xwarp_rows(int N) { return 2 * (32 / (N / (N % 3 ? 16 : 12))); }
 cudaError_t launch_pass_xwarp(int N, const CUtensorMap &msrc, const CUtensorMap &mV, const CUtensorMap &mdst,
                               const TmaPassArgs &a, cudaStream_t s);
 cudaError_t prepare_pass_xwarp(int N);
@@ -124,6 +128,7 @@ cudaError_t prepare_pass_xwarp(int N);
 // and its device status word.  Lives in device memory (64-byte aligned).
 struct TmaMember {
     CUtensorMap x[4];  // x view, box N x tmared_rows_x(N)
+    CUtensorMap xw[4]; // x view, box N x xwarp_rows(N) (per-warp x tiles; xwarp_eligible lines)
     CUtensorMap y[3];  // y view, box 2P columns x N
     CUtensorMap z[3];  // z view, box 2P columns x 1 x N
     CUtensorMap f[4];  // fused x-y view (fxy_eligible grids), box N x N x fxy_planes(N)
@@ -150,6 +155,11 @@ struct TmaBatchArgs {
 };
 
 cudaError_t launch_pass_tmared_batch(int axis, int N, const TmaBatchArgs &a, cudaStream_t s);
+// Batched x pass with per-warp tiles (batch schedule 6; xwarp_eligible lines):
+// the members' xw maps, a.tiles = ceil(rows / xwarp_rows(N)) per member; the
+// table form when a.vsep.
+cudaError_t launch_pass_xwarp_batch(int N, const TmaBatchArgs &a, cudaStream_t s);
+cudaError_t prepare_pass_xwarp_batch(int N);
 
 // V[r nx + i] = vx[i] + vyz[r] in FP32 (rounded to nearest), the values the x
 // pass rebuilds from the tables of a separable potential; rows = ny nz.

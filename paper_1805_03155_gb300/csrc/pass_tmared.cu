@@ -51,29 +51,36 @@ cudaError_t red_x(const CUtensorMap *ms, const CUtensorMap *mv, const CUtensorMa
                       BATCH ? none : *ms, BATCH ? none : *mv, BATCH ? none : *md, BATCH ? a0 : *a, BATCH ? *ba : b0);
 }
 
-template <int N, bool VSEP>
+template <int N, bool VSEP, bool BATCH>
 cudaError_t red_xw(const CUtensorMap *ms, const CUtensorMap *mv, const CUtensorMap *md, const TmaPassArgs *a,
-                   cudaStream_t s)
+                   const TmaBatchArgs *ba, cudaStream_t s)
 {
-    using G = XWarp<N, VSEP>;
+    using G = XWarp<N, VSEP, BATCH>;
     int grid = 0;
-    cudaError_t e = persistent_grid<xpass_warp_kernel<N, VSEP>>(G::THREADS, G::SMEM, &grid);
-    if (e != cudaSuccess || !a) return e;
-    const int need = (a->n_tiles + G::WARPS - 1) / G::WARPS;  // blocks that get a tile
+    cudaError_t e = persistent_grid<xpass_warp_kernel<N, VSEP, BATCH>>(G::THREADS, G::SMEM, &grid);
+    if (e != cudaSuccess || !(BATCH ? (const void *)ba : (const void *)a)) return e;
+    const int total = BATCH ? ba->members * ba->tiles : a->n_tiles;
+    const int need = (total + G::WARPS - 1) / G::WARPS;  // blocks that get a tile
     if (need < grid) grid = need;
     if (grid <= 0) return cudaSuccess;
-    return launch_pdl(xpass_warp_kernel<N, VSEP>, dim3(grid), dim3(G::THREADS), G::SMEM, s, *ms, *mv, *md, *a);
+    const CUtensorMap none{};
+    const TmaPassArgs a0{};
+    const TmaBatchArgs b0{};
+    return launch_pdl(xpass_warp_kernel<N, VSEP, BATCH>, dim3(grid), dim3(G::THREADS), G::SMEM, s,
+                      BATCH ? none : *ms, BATCH ? none : *mv, BATCH ? none : *md, BATCH ? a0 : *a, BATCH ? *ba : b0);
 }
 
-template <bool VSEP>
+template <bool VSEP, bool BATCH>
 cudaError_t red_xw_n(int N, const CUtensorMap *ms, const CUtensorMap *mv, const CUtensorMap *md,
-                     const TmaPassArgs *a, cudaStream_t s)
+                     const TmaPassArgs *a, const TmaBatchArgs *ba, cudaStream_t s)
 {
     switch (N) {
-    case 32: return red_xw<32, VSEP>(ms, mv, md, a, s);
-    case 64: return red_xw<64, VSEP>(ms, mv, md, a, s);
-    case 128: return red_xw<128, VSEP>(ms, mv, md, a, s);
-    case 256: return red_xw<256, VSEP>(ms, mv, md, a, s);
+    case 32: return red_xw<32, VSEP, BATCH>(ms, mv, md, a, ba, s);
+    case 48: return red_xw<48, VSEP, BATCH>(ms, mv, md, a, ba, s);
+    case 64: return red_xw<64, VSEP, BATCH>(ms, mv, md, a, ba, s);
+    case 96: return red_xw<96, VSEP, BATCH>(ms, mv, md, a, ba, s);
+    case 128: return red_xw<128, VSEP, BATCH>(ms, mv, md, a, ba, s);
+    case 256: return red_xw<256, VSEP, BATCH>(ms, mv, md, a, ba, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -252,15 +259,27 @@ cudaError_t launch_pass_xwarp(int N, const CUtensorMap &msrc, const CUtensorMap 
 {
     if (a.vyz) {
         if (!a.vx) return cudaErrorInvalidValue;
-        return red_xw_n<true>(N, &msrc, &mV, &mdst, &a, s);
+        return red_xw_n<true, false>(N, &msrc, &mV, &mdst, &a, nullptr, s);
     }
-    return red_xw_n<false>(N, &msrc, &mV, &mdst, &a, s);
+    return red_xw_n<false, false>(N, &msrc, &mV, &mdst, &a, nullptr, s);
 }
 
 cudaError_t prepare_pass_xwarp(int N)
 {
-    const cudaError_t e = red_xw_n<true>(N, nullptr, nullptr, nullptr, nullptr, nullptr);
-    return e != cudaSuccess ? e : red_xw_n<false>(N, nullptr, nullptr, nullptr, nullptr, nullptr);
+    const cudaError_t e = red_xw_n<true, false>(N, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+    return e != cudaSuccess ? e : red_xw_n<false, false>(N, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+}
+
+cudaError_t launch_pass_xwarp_batch(int N, const TmaBatchArgs &a, cudaStream_t s)
+{
+    return a.vsep ? red_xw_n<true, true>(N, nullptr, nullptr, nullptr, nullptr, &a, s)
+                  : red_xw_n<false, true>(N, nullptr, nullptr, nullptr, nullptr, &a, s);
+}
+
+cudaError_t prepare_pass_xwarp_batch(int N)
+{
+    const cudaError_t e = red_xw_n<true, true>(N, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+    return e != cudaSuccess ? e : red_xw_n<false, true>(N, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
 }
 
 cudaError_t launch_pass_tmared(int axis, int N, const CUtensorMap &msrc, const CUtensorMap &mV,

@@ -490,100 +490,132 @@ xpass_tmared_kernel(const __grid_constant__ CUtensorMap msrc, const __grid_const
 }
 
 // ---------------------------------------------------------------------------
-// x pass with per-warp tiles (schedule 6; single grids, N in {32, 64, 128,
-// 256}).  The block pass above waits at two block barriers per tile (the
-// stage vote and the hand-over to the thread that issues the reduce-add), so a
-// warp that finishes its line pairs early idles until the slowest warp of the
-// block is done.  Here each warp owns a ring of S stages of its own tiles --
-// the 2 (32/TT) rows of its line pairs, 4 KB of src (plus V, or the rows' vyz
-// values for a separable potential) -- with its own mbarriers; lane 0 issues
-// the warp's loads and reduce-adds, and the lanes meet only at warp barriers.
-// The arithmetic of a tile (XTile) is the block pass's, so both give the same
-// bits.  Waits are bounded per warp; a warp whose wait runs out records the
-// timeout, drains its own loads and reduce-adds and returns.
+// x pass with per-warp tiles (schedule 6; N in {32, 48, 64, 96, 128, 256};
+// single grids and batches).  The block pass above waits at two block
+// barriers per tile (the stage vote and the hand-over to the thread that
+// issues the reduce-add), so a warp that finishes its line pairs early idles
+// until the slowest warp of the block is done.  Here each warp owns a ring of
+// S stages of its own tiles -- the 2 (32/TT) rows of its line pairs, 3-4 KB of
+// src (plus V, or the rows' vyz values for a separable potential; batched,
+// also the tile's member's multiplier row and, with tables, its vx row) --
+// with its own mbarriers; lane 0 issues the warp's loads and reduce-adds, and
+// the lanes meet only at warp barriers.  The arithmetic of a tile (XTile) is
+// the block pass's, so both give the same bits.  Waits are bounded per warp;
+// a warp whose wait runs out records the timeout, drains its own loads and
+// reduce-adds and returns.
 // ---------------------------------------------------------------------------
-template <int N, bool VSEP>
+template <int N, bool VSEP, bool BATCH = false>
 struct XWarp {
-    static constexpr int E = 16, TT = N / E;
-    static_assert(TT >= 2 && TT <= 16, "per-warp x tiles take 32..256-point lines");
+    static constexpr int E = line_e<float, N>::value, TT = N / E;
+    static_assert(TT >= 2 && TT <= 16, "per-warp x tiles take lines of 2..16 threads");
     static constexpr int LPW = 32 / TT;          // line pairs per warp
     static constexpr int ROWS = 2 * LPW;         // rows per warp tile
-    static constexpr int TILE = ROWS * N;        // floats: 1024 (4 KB)
+    static constexpr int TILE = ROWS * N;        // floats: 1024 (4 KB), 768 for 3 * 2^k lines
     static constexpr int WARPS = 4;
     static constexpr int THREADS = 32 * WARPS;
     static constexpr int PARTS = VSEP ? 1 : 2;   // src (and V) per stage
     static constexpr int BLOCKS = VSEP ? 3 : 2;
-    static constexpr int S0 = (int)(kTmaRedRing / BLOCKS / WARPS / ((size_t)PARTS * TILE * sizeof(float)));
+    // floats of a warp's stage: its tiles, the rows' vyz values (tables) and,
+    // batched, the member's multiplier row and vx row (tables)
+    static constexpr int STAGE = PARTS * TILE + (VSEP ? ROWS : 0) + (BATCH ? (VSEP ? 2 : 1) * N : 0);
+    // single grids count the tiles alone (the vyz values fit beside them)
+    static constexpr size_t RING_UNIT = (size_t)(BATCH ? STAGE : PARTS * TILE) * sizeof(float);
+    static constexpr int S0 = (int)(kTmaRedRing / BLOCKS / WARPS / RING_UNIT);
     static constexpr int S = S0 < 8 ? S0 : 8;
     static_assert(S >= 2, "a warp's ring needs two stages");
-    static constexpr size_t SMEM = (size_t)WARPS * S * PARTS * TILE * sizeof(float) +
-                                   (VSEP ? (size_t)WARPS * S * ROWS * sizeof(float) + N * sizeof(float) : 0) +
+    static constexpr size_t SMEM = (size_t)WARPS * S * STAGE * sizeof(float) + (VSEP && !BATCH ? N * sizeof(float) : 0) +
                                    N * sizeof(float2) + N * sizeof(float) + (size_t)WARPS * S * sizeof(uint64_t) + 1024;
 };
 
-template <int N, bool VSEP>
-__global__ void __launch_bounds__(XWarp<N, VSEP>::THREADS, XWarp<N, VSEP>::BLOCKS)
+template <int N, bool VSEP, bool BATCH>
+__global__ void __launch_bounds__(XWarp<N, VSEP, BATCH>::THREADS, XWarp<N, VSEP, BATCH>::BLOCKS)
 xpass_warp_kernel(const __grid_constant__ CUtensorMap msrc, const __grid_constant__ CUtensorMap mV,
-                  const __grid_constant__ CUtensorMap mdst, const TmaPassArgs a)
+                  const __grid_constant__ CUtensorMap mdst, const TmaPassArgs a, const TmaBatchArgs ba)
 {
-    using G = XWarp<N, VSEP>;
+    using G = XWarp<N, VSEP, BATCH>;
     constexpr int E = G::E, TT = G::TT, ROWS = G::ROWS, TILE = G::TILE, S = G::S, W = G::WARPS;
     constexpr uint32_t kTileBytes = TILE * sizeof(float);
     extern __shared__ unsigned char smem_raw[];
     const uint32_t pad = (1024u - (smem_u32(smem_raw) & 1023u)) & 1023u;
-    float *tiles = reinterpret_cast<float *>(smem_raw + pad);  // [W][S][PARTS][TILE]
-    float *vrows = tiles + (size_t)W * S * G::PARTS * TILE;    // VSEP: [W][S][ROWS]
-    float *vxt = vrows + (VSEP ? W * S * ROWS : 0);            // VSEP: vx[N]
-    float2 *tw = reinterpret_cast<float2 *>(vxt + (VSEP ? N : 0));
-    float *mult = reinterpret_cast<float *>(tw + N);
+    float *tbuf = reinterpret_cast<float *>(smem_raw + pad);   // [W][S][PARTS][TILE]
+    float *vrows = tbuf + (size_t)W * S * G::PARTS * TILE;     // tables: [W][S][ROWS]
+    float *brows = vrows + (VSEP ? W * S * ROWS : 0);          // batched: [W][S][N] multipliers, then vx
+    float *vxt = brows + (BATCH ? (VSEP ? 2 : 1) * W * S * N : 0);  // single grid with tables: vx[N]
+    float2 *tw = reinterpret_cast<float2 *>(vxt + (VSEP && !BATCH ? N : 0));
+    float *mult = reinterpret_cast<float *>(tw + N);           // single grid: the multiplier row
     uint64_t *full_all = reinterpret_cast<uint64_t *>(mult + N);  // [W][S]
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     const int t = lane % TT, l = lane / TT;
     uint64_t *full = full_all + w * S;
-    float *wt = tiles + (size_t)w * S * G::PARTS * TILE;
+    float *wt = tbuf + (size_t)w * S * G::PARTS * TILE;
     float *wv = vrows + w * S * ROWS;
+    float *wm = brows + w * S * N;            // batched: this warp's multiplier rows
+    float *wx = brows + (W + w) * S * N;      // batched, tables: this warp's vx rows
     if (lane == 0) {
         for (int s = 0; s < S; ++s) mbar_init(&full[s], 1);
         mbar_fence_init();
     }
     for (int i = tid; i < N; i += G::THREADS) {
-        tw[i] = a.tw[i];
-        mult[i] = a.mult[i];
-        if constexpr (VSEP) vxt[i] = a.vx[i];
+        if constexpr (BATCH) {
+            tw[i] = ba.tw[i];
+        } else {
+            tw[i] = a.tw[i];
+            mult[i] = a.mult[i];
+            if constexpr (VSEP) vxt[i] = a.vx[i];
+        }
     }
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     __syncthreads();
     float mrow[E];
 #pragma unroll
-    for (int e = 0; e < E; ++e) mrow[e] = mult[t + e * TT];
-    const bool useV = VSEP || a.use_V != 0;
+    for (int e = 0; e < E; ++e) mrow[e] = BATCH ? 0.f : mult[t + e * TT];
+    const bool useV = BATCH || VSEP || a.use_V != 0;
+    const int fsrc = BATCH ? (ba.src >= 0 ? ba.src : 1 - ba.dst) : 0;
 
-    const int total = a.n_tiles;
+    // tile g: member g / tiles (0 for a single grid), rows from (g mod tiles) ROWS
+    const int tiles = BATCH ? ba.tiles : a.n_tiles;
+    const int total = BATCH ? ba.members * ba.tiles : a.n_tiles;
     const int gw = (int)blockIdx.x * W + w, nw = (int)gridDim.x * W;
     const int nk = gw < total ? (total - 1 - gw) / nw + 1 : 0;
-    auto row0 = [&](int k) {
+    auto at = [&](int k) {
         int g = gw + k * nw;
-        if (a.reverse) g = total - 1 - g;
-        return g * ROWS;
+        if (!BATCH && a.reverse) g = total - 1 - g;
+        TileAt c;
+        c.i = BATCH ? g / tiles : 0;
+        c.c[0] = 0;
+        c.c[1] = 0;
+        c.c[2] = (g - c.i * tiles) * ROWS;
+        c.c[3] = 0;
+        return c;
     };
     auto issue = [&](int k) {
         const int s = k % S;
-        TileAt c;
-        c.i = 0;
-        c.c[0] = 0;
-        c.c[1] = 0;
-        c.c[2] = row0(k);
-        c.c[3] = 0;
-        mbar_arrive_expect_tx(&full[s], VSEP ? kTileBytes + ROWS * sizeof(float) : (useV ? 2 : 1) * kTileBytes);
-        // failure-path test hook: the first tile of the grid's first warp may be left unloaded
-        if (k == 0 && gw == 0 && a.inject && atomicExch(a.inject, 0) != 0) return;
+        const TileAt c = at(k);
         float *st = wt + (size_t)s * G::PARTS * TILE;
-        load_tile(st, &msrc, c, &full[s]);
-        if constexpr (VSEP)
-            bulk_load(wv + s * ROWS, a.vyz + c.c[2], ROWS * sizeof(float), &full[s]);
-        else if (useV)
-            load_v_tile(st + TILE, &mV, c, &full[s]);
+        if constexpr (BATCH) {
+            const TmaMember *mm = ba.mem + c.i;
+            const PassArgs<float> &pm = ba.pa[c.i];
+            mbar_arrive_expect_tx(&full[s], kTileBytes + (VSEP ? (ROWS + N) * sizeof(float) : kTileBytes) +
+                                                N * sizeof(float));
+            load_tile(st, &mm->xw[fsrc], c, &full[s]);
+            if constexpr (VSEP) {
+                bulk_load(wv + s * ROWS, pm.vyz + c.c[2], ROWS * sizeof(float), &full[s]);
+                bulk_load(wx + s * N, pm.vx, N * sizeof(float), &full[s]);
+            } else {
+                load_v_tile(st + TILE, &mm->xw[3], c, &full[s]);
+            }
+            bulk_load(wm + s * N, pm.mult, N * sizeof(float), &full[s]);
+        } else {
+            mbar_arrive_expect_tx(&full[s], VSEP ? kTileBytes + ROWS * sizeof(float) : (useV ? 2 : 1) * kTileBytes);
+            // failure-path test hook: the first tile of the grid's first warp may be left unloaded
+            if (k == 0 && gw == 0 && a.inject && atomicExch(a.inject, 0) != 0) return;
+            load_tile(st, &msrc, c, &full[s]);
+            if constexpr (VSEP)
+                bulk_load(wv + s * ROWS, a.vyz + c.c[2], ROWS * sizeof(float), &full[s]);
+            else if (useV)
+                load_v_tile(st + TILE, &mV, c, &full[s]);
+        }
     };
     if (lane == 0)
         for (int k = 0; k < S - 1 && k < nk; ++k) issue(k);
@@ -591,28 +623,36 @@ xpass_warp_kernel(const __grid_constant__ CUtensorMap msrc, const __grid_constan
 
     for (int k = 0; k < nk; ++k) {
         const int s = k % S;
+        const TileAt c = at(k);
         const bool ok = mbar_wait(&full[s], (uint32_t)((k / S) & 1));
         if (__any_sync(0xffffffffu, !ok)) {
-            if (lane == 0) red_timeout_exit<S>(full, k, nk, a.status);
+            if (lane == 0) red_timeout_exit<S>(full, k, nk, BATCH ? ba.mem[c.i].status : a.status);
             return;
         }
         float *src = wt + (size_t)s * G::PARTS * TILE;
         XTile<N, E> x;
-        if constexpr (VSEP)
-            x.load_sep(src, vxt, wv[s * ROWS + 2 * l], wv[s * ROWS + 2 * l + 1], a.bV, t, l);
-        else
-            x.load(src, src + TILE, a.bV, useV, t, l);
-        x.finish(src, mrow, tw, nullptr);
+        if constexpr (BATCH) {
+            // the tile's member: its multipliers and bV
+            float mr[E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) mr[e] = wm[s * N + t + e * TT];
+            const float bV = ba.pa[c.i].bV;
+            if constexpr (VSEP)
+                x.load_sep(src, wx + s * N, wv[s * ROWS + 2 * l], wv[s * ROWS + 2 * l + 1], bV, t, l);
+            else
+                x.load(src, src + TILE, bV, true, t, l);
+            x.finish(src, mr, tw, nullptr);
+        } else {
+            if constexpr (VSEP)
+                x.load_sep(src, vxt, wv[s * ROWS + 2 * l], wv[s * ROWS + 2 * l + 1], a.bV, t, l);
+            else
+                x.load(src, src + TILE, a.bV, useV, t, l);
+            x.finish(src, mrow, tw, nullptr);
+        }
         fence_proxy_async();
         __syncwarp();
         if (lane == 0) {
-            TileAt c;
-            c.i = 0;
-            c.c[0] = 0;
-            c.c[1] = 0;
-            c.c[2] = row0(k);
-            c.c[3] = 0;
-            reduce_tile(&mdst, c, src);
+            reduce_tile(BATCH ? &ba.mem[c.i].xw[ba.dst] : &mdst, c, src);
             bulk_commit();
             if (k + S - 1 < nk) {
                 bulk_wait_read<1>();

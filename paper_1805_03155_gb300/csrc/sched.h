@@ -10,8 +10,9 @@
 //      the lines per block
 //   4  plain, the default plan (differs from 0 only on TMA axes)
 //   5  the TMA pass with loaded and stored destination tiles (TMA axes only)
-//   6  x axes of 32..256 points (single FP32 grids): the reduce-add TMA pass
-//      with per-warp tiles (pass_tmared.cuh, xpass_warp_kernel); same bits as 0
+//   6  x axes of 32, 48, 64, 96, 128 or 256 points (FP32 2D/3D grids, single
+//      and batched): the reduce-add TMA pass with per-warp tiles
+//      (pass_tmared.cuh, xpass_warp_kernel); same bits as 0
 // Schedules 1..3 exist for lines of kSchedMinN..kSchedMaxN points; 1, 2 and 4
 // run exactly the arithmetic of the default plain kernel (same results bit for
 // bit), 3 changes the radix sequence and so the rounding.

@@ -132,6 +132,7 @@ def lib():
         "spstd_inject_wait_timeout": (C.c_int, [vp]),
         "spstd_batch_tune": (C.c_int, [vp, C.c_int]),
         "spstd_batch_get_schedule": (C.c_int, [vp, C.c_int, C.c_int, ip, C.POINTER(C.c_int)]),
+        "spstd_batch_set_schedule": (C.c_int, [vp, C.c_int, C.c_int, ip, C.POINTER(C.c_int)]),
         "spstd_last_error": (C.c_char_p, [vp]),
         "spstd_status_string": (C.c_char_p, [C.c_int]),
     }
@@ -479,6 +480,11 @@ class Batch:
         out = (C.c_int * 3)()
         self._check(self.L.spstd_batch_get_schedule(self.b, int(precision), int(dims), nn, out))
         return [out[i] for i in range(3)]
+
+    def spstd_batch_set_schedule(self, precision, dims, n, schedule):
+        nn = (C.c_int64 * 3)(*(list(n) + [1] * (3 - len(n))))
+        sv = (C.c_int * 3)(*(list(schedule) + [0] * (3 - len(schedule))))
+        self._check(self.L.spstd_batch_set_schedule(self.b, int(precision), int(dims), nn, sv))
 
     def close(self):
         if getattr(self, "b", None) is not None and self.b.value:

@@ -43,7 +43,7 @@ def schedule_runs(p, precision, steps):
 @pytest.mark.parametrize("n,precision", [((128, 64), 32), ((128, 64), 64), ((64, 64, 64), 32),
                                          ((32, 256, 16), 64), ((512, 32), 32), ((64, 512), 32),
                                          ((16, 32, 512), 32), ((16, 128, 64), 32), ((32, 32, 32), 32),
-                                         ((32, 64), 32)])
+                                         ((32, 64), 32), ((96, 48, 16), 32), ((48, 32), 32)])
 def test_every_schedule_same_step(n, precision):
     p = stable(inputs.gaussian_problem(n, steps=12, noise=1e-2))
     cands, runs = schedule_runs(p, precision, p.steps)
@@ -51,7 +51,7 @@ def test_every_schedule_same_step(n, precision):
     tol = 1e-10 if precision == 64 else 1e-4
     plain_exact = {0, 1, 2, 4}
     for ax, lst in cands.items():
-        if 32 <= n[ax] <= 512:
+        if 32 <= n[ax] <= 512 and n[ax] & (n[ax] - 1) == 0:
             assert 3 in lst and len(lst) >= 3, (ax, lst)   # a radix variant and a tile variant at least
         # plain schedules with the default radix plan agree bit for bit
         ref_v = 4 if 4 in lst else 0
@@ -137,7 +137,8 @@ def test_tuned_batch_equals_lone_solves():
     batch.spstd_batch_tune(reps=3)
     for sh in set(shapes):
         sched = batch.spstd_batch_get_schedule(32, len(sh), sh)
-        assert all(0 <= v <= 4 for v in sched)
+        assert all(v in (0, 1, 2, 3, 4, 6) for v in sched)
+        assert all(v != 6 for v in sched[1:])
     # tuning touched no state
     for s, p in zip(solvers, probs):
         R, Im = s.spstd_get_state()
@@ -153,7 +154,7 @@ def test_tuned_batch_equals_lone_solves():
         s.close()
 
 
-@pytest.mark.parametrize("n", [(256, 48), (64, 32, 24), (128, 96)])
+@pytest.mark.parametrize("n", [(256, 48), (64, 32, 24), (128, 96), (96, 32, 8), (48, 64)])
 def test_warp_x_tiles_with_a_potential_field(n):
     """Schedule 6 with a potential that does not separate (a square well in
     2D/3D is a box, not a sum), so the per-warp x pass reads the V field: the
@@ -173,3 +174,59 @@ def test_warp_x_tiles_with_a_potential_field(n):
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
     oR, oI, _ = oracle_run(p)
     assert rel_l2(out[1][0], out[1][1], oR, oI) <= 1e-4
+
+
+def test_batch_warp_x_tiles_equal_lone_solves():
+    """Batch schedule 6 (per-warp x tiles) on x lines of 32, 48, 96, 128 and 256
+    points, in groups whose members all have separable tables and in groups
+    that read V fields (a square well, or a member that asks for the field):
+    every member ends bit for bit where its lone solve (block x tiles) ends."""
+    from paper_1805_03155_gb300 import spstd
+
+    shapes = [((32, 64), "ho"), ((32, 64), "ho"), ((48, 32, 8), "ho"), ((48, 32, 8), "well"),
+              ((96, 48, 16), "ho"), ((96, 48, 16), "ho"), ((128, 32, 8), "ho"), ((128, 32, 8), "field"),
+              ((256, 64), "ho"), ((256, 64), "well")]
+    probs = []
+    for k, (sh, kind) in enumerate(shapes):
+        kw = dict(well=(5.0, 1.5)) if kind == "well" else {}
+        probs.append(stable(inputs.gaussian_problem(sh, seed=900 + k, steps=0, n_probe=2, **kw)))
+    steps = 9
+    alone = []
+    for p, (_, kind) in zip(probs, shapes):
+        s = gpu_solver(p, 32, cap=steps, merge=False, v_field_only=kind == "field")
+        assert s.spstd_get_schedule(0) == 0
+        s.spstd_step(steps)
+        alone.append(s.spstd_get_state())
+        s.close()
+    batch = spstd.Batch(len(probs))
+    solvers = [gpu_solver(p, 32, cap=steps, v_field_only=kind == "field") for p, (_, kind) in zip(probs, shapes)]
+    for s in solvers:
+        batch.spstd_batch_add(s)
+    for sh in {sh for sh, _ in shapes}:
+        batch.spstd_batch_set_schedule(32, len(sh), sh, [6] + [0] * (len(sh) - 1))
+        assert batch.spstd_batch_get_schedule(32, len(sh), sh)[0] == 6
+    batch.spstd_batch_step(steps)
+    batch.spstd_batch_sync()
+    for i, (s, (R, Im)) in enumerate(zip(solvers, alone)):
+        bR, bI = s.spstd_get_state()
+        assert np.array_equal(bR, R) and np.array_equal(bI, Im), i
+    batch.close()
+    for s in solvers:
+        s.close()
+
+
+def test_batch_set_schedule_rejects_unknown():
+    from paper_1805_03155_gb300 import spstd
+
+    batch = spstd.Batch(2)
+    for prec, sh, sched in [(32, (96, 48, 16), [0, 6, 0]),     # per-warp tiles are an x schedule
+                            (64, (128, 32), [6, 0]),            # FP32 only
+                            (32, (96, 48, 16), [3, 0, 0]),      # no plain variants for 3 * 2^k lines
+                            (32, (512, 64), [6, 0]),            # 512-point x lines: block tiles only
+                            (32, (128, 32), [7, 0])]:
+        with pytest.raises(spstd.SpstdError) as ei:
+            batch.spstd_batch_set_schedule(prec, len(sh), sh, sched)
+        assert ei.value.status == spstd.SPSTD_EINVAL
+    batch.spstd_batch_set_schedule(32, 2, (128, 32), [6, 3])
+    assert batch.spstd_batch_get_schedule(32, 2, (128, 32))[:2] == [6, 3]
+    batch.close()
