@@ -368,7 +368,7 @@ def gate_summary(acc):
 
 
 def batched_vs_plain(count=512, steps=800, plain_steps=40, precision=32, local=0, plain=True, check=True,
-                     general_v=True):
+                     general_v=True, schedules=None):
     """The mixed 512-solve workload (1D wells 128..8192, 2D oscillators
     64^2..512^2, 3D oscillators 32^3, 48^3, 64^3 and 96^3; FP32 fields, FP64
     reductions, FR4): every member stepped through one batch (graph-replayed
@@ -425,7 +425,13 @@ def batched_vs_plain(count=512, steps=800, plain_steps=40, precision=32, local=0
     default_ms = timed_batch()  # also the warm-up: captures the batch graph
     # autotuned schedules per member shape (timed on the members' scratch fields)
     t_tune = time.perf_counter()
-    b.spstd_batch_tune(reps=3)
+    if schedules:
+        # fixed schedules (profiler runs, whose serialised timings would mislead the tuner)
+        for key, sched in schedules.items():
+            dims, sizes = key.split(":")
+            b.spstd_batch_set_schedule(precision, int(dims[0]), [int(v) for v in sizes.split("x")], sched)
+    else:
+        b.spstd_batch_tune(reps=3)
     tune_s = time.perf_counter() - t_tune
     shapes = sorted({(p.dims, tuple(p.n)) for p in probs if p.dims > 1})
     tuned = {"%dd:%s" % (d, "x".join(str(v) for v in n[:d])): b.spstd_batch_get_schedule(precision, d, n)[:d]
@@ -782,6 +788,9 @@ def main():
     ap.add_argument("--schedules", default=None,
                     help="comma-separated pass schedule per axis to use instead of autotuning (for profiler runs, "
                          "whose timings would mislead the tuner), e.g. 6,0,0")
+    ap.add_argument("--batch-schedules", default=None,
+                    help='batch pass schedules per member shape instead of the batch autotuner (for profiler '
+                         'runs), as JSON, e.g. {"3d:96x96x96": [6, 0, 0]}')
     ap.add_argument("--batch-steps", type=int, default=800,
                     help="timed steps of the batched leg (a short run for profiler launch lists)")
     ap.add_argument("--batch-only", action="store_true",
@@ -794,7 +803,8 @@ def main():
     if args.batch_only:
         import torch
         torch.cuda.set_device(0)
-        r = batched_vs_plain(steps=args.batch_steps, plain=False, check=False, general_v=not args.no_general_v)
+        r = batched_vs_plain(steps=args.batch_steps, plain=False, check=False, general_v=not args.no_general_v,
+                             schedules=json.loads(args.batch_schedules) if args.batch_schedules else None)
         print(json.dumps({"batch_only": True, **{k: r[k] for k in ("workload", "members", "grid_points", "steps",
                                                                     "shapes3d", "batched", "batched_general_v",
                                                                     "unit")}}))
