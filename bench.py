@@ -119,6 +119,18 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def tf32_peak_tflops():
+    """Dense TF32 tensor peak: the measured bf16 burst figure times the
+    nominal TF32 / bf16 ratio (1.1 / 2.25); the nominal 1.1 PFLOP/s without a
+    measurement."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        bf16 = json.load(open(p)).get("bf16_tflops")
+        if bf16:
+            return bf16 * 1.1 / 2.25
+    return 1100.0
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -648,7 +660,12 @@ def next_rows_leg(peak, sm_mhz, local=0):
       half-stage (the measurement unit) against the copy peak; the kernels
       move about 36 B/pt for the paired x lines plus 12 B/pt for y;
     * Dirichlet walls (3D FP32 128^3, DST on every axis, FR4): dense n x n
-      line operators, 2n flops per point per axis -- the FP32 ALU bound;
+      line operators as tensor-core products (tcgen05 TF32, 3xTF32: 6n flops
+      per point per axis) -- the passes' bytes (16 B/pt x with V, 12 B/pt y
+      and z) against the copy peak, the flops against the TF32 peak (the
+      measured bf16 peak x 1.1/2.25, the nominal ratio); and the same steps
+      with the CUDA-core dense pass (schedule 4, 2n FP32 flops per point per
+      axis) for comparison;
     * the RK4 comparison scheme (3D FP32 256^3): 8 H applications a step, the
       unit's 16 B/pt each;
     * eigenstate accumulation (3D FP32 256^3, FR4, 2 target energies): the
@@ -684,10 +701,25 @@ def next_rows_leg(peak, sm_mhz, local=0):
     p = inputs.gaussian_problem((128, 128, 128), steps=10, seed=22, dt=0.0, n_probe=2, bc=(1, 1, 1))
     s = spstd.solver_for(p, precision=32, probe_capacity=64, stream=stream, device=local)
     ms = timed(s, 10)
+    prof = s.spstd_profile_steps(2)
+    pass_ms = sum(prof[k][0] for k in ("x_pass", "y_pass", "z_pass")) / max(1, sum(prof[k][1] for k in (
+        "x_pass", "y_pass", "z_pass")))
+    for a in range(3):
+        s.spstd_set_schedule(a, 4)
+    core_ms = timed(s, 10)
     s.close()
-    flops = (3 * 2 * 128 + 2) * p.n_total * h_applied
-    out["walls_dirichlet_128^3_fp32"] = {"ms_per_step": ms, "value": p.n_total / (ms * 1e-3), "bound": "alu",
-                                         "alu_frac": flops / (ms * 1e-3) / 1e12 / alu_peak_tflops(32, sm_mhz)}
+    tf32_peak = tf32_peak_tflops()
+    row = {"ms_per_step": ms, "value": p.n_total / (ms * 1e-3), "bound": "hbm", "dense_pass_ms": pass_ms,
+           "pass_frac": (40 / 3) * p.n_total / (pass_ms * 1e-3) / 1e9 / peak,
+           "tensor_tflops": 6 * 128 * p.n_total / (pass_ms * 1e-3) / 1e12,
+           "cuda_core_ms_per_step": core_ms,
+           "cuda_core_alu_frac": (3 * 2 * 128 + 2) * p.n_total * h_applied / (core_ms * 1e-3) / 1e12 /
+                                 alu_peak_tflops(32, sm_mhz)}
+    row["tensor_frac"] = row["tensor_tflops"] / tf32_peak
+    row["what"] = ("dense passes on the tensor cores (3 TF32 MMAs per product): pass_frac = their 13.3 B/pt "
+                   "average over the event-timed pass, tensor_frac = 6n flops/pt over the TF32 peak "
+                   f"({tf32_peak:.0f} TFLOP/s: measured bf16 x 1.1/2.25); the 25 MB grid stays in L2")
+    out["walls_dirichlet_128^3_fp32"] = row
     # RK4
     p = inputs.gaussian_problem((256, 256, 256), (-12.0,) * 3, (12.0,) * 3, seed=23, integrator="RK4", dt=0.0,
                                 steps=10, n_probe=2)
@@ -793,6 +825,9 @@ def main():
                          'runs), as JSON, e.g. {"3d:96x96x96": [6, 0, 0]}')
     ap.add_argument("--batch-steps", type=int, default=800,
                     help="timed steps of the batched leg (a short run for profiler launch lists)")
+    ap.add_argument("--next-rows-only", action="store_true",
+                    help="run only the rows beyond the hot path (long lines, walls, RK4, eigenstates) and print "
+                         "their numbers (for profiler runs of their kernels)")
     ap.add_argument("--batch-only", action="store_true",
                     help="run only the batched leg of the 512-solve mix and print its numbers (for profiler "
                          "launch lists of the batched passes)")
@@ -800,6 +835,14 @@ def main():
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
+    if args.next_rows_only:
+        import torch
+        torch.cuda.set_device(0)
+        from paper_1805_03155_gb300 import build
+        if not os.path.exists(build.LIB):
+            build.build()
+        print(json.dumps({"next_rows_only": True, "next_rows": next_rows_leg(measured_peaks()[0], None)}))
+        return 0
     if args.batch_only:
         import torch
         torch.cuda.set_device(0)

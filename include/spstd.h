@@ -152,7 +152,9 @@ typedef struct {
  * two use the FFT passes; wall axes, and periodic axes of any other length
  * 2 <= n <= 256, apply the same spectral operator as a dense n x n matrix
  * (FP64-built, rounded once), which for such short lines costs no more than the
- * transforms.  Grid points: periodic x_j = lo + j L/n; Dirichlet
+ * transforms.  On FP32 2D/3D grids, axes of 32..128 points apply it on the
+ * tensor cores as one product over all lines (TF32 with the 3xTF32 split, FP32
+ * accumulation: FP32 accuracy, not the CUDA-core sum's exact rounding).  Grid points: periodic x_j = lo + j L/n; Dirichlet
  * x_j = lo + (j+1) L/(n+1); Neumann x_j = lo + j L/(n-1). */
 enum { SPSTD_PERIODIC = 0, SPSTD_DIRICHLET = 1, SPSTD_NEUMANN = 2 };
 #define SPSTD_MAX_DENSE_N 256
@@ -293,7 +295,9 @@ spstd_status spstd_profile_steps(spstd_ctx *ctx, int64_t nsteps, double *ms, int
  *   1  plain pass, half the lines per block
  *   2  plain pass, twice the lines per block
  *   3  plain pass, half the points per thread (one radix lower per stage)
- *   4  plain pass, default plan (listed only where 0 is the TMA pass)
+ *   4  plain pass, default plan (listed only where 0 is the TMA pass); on a
+ *      dense wall axis whose 0 is the tensor-core product (FP32 2D/3D, 32..128
+ *      points): the CUDA-core dense pass
  *   5  TMA pass that loads the destination tile into shared memory, adds
  *      there and stores it back (listed only where 0 is the TMA pass)
  *   6  x axes of 32, 48, 64, 96, 128 or 256 points of FP32 2D/3D grids

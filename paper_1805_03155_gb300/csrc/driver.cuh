@@ -26,6 +26,7 @@
 
 #include "../../include/spstd.h"
 #include "../../include/spstd_testing.h"
+#include "dense_tc.h"
 #include "launch.cuh"
 #include "longline.h"
 #include "pass_tma_launch.h"
@@ -59,6 +60,7 @@ constexpr int kMaxGuards = 48;
 
 struct Layout {
     size_t psi[2], V, vsep_x, vsep_yz, tmp, staging, ring, counter, status, snap, partial, dout, tw[3], mult, dense[3], spec;
+    size_t dense_tc[3];  // tensor-core form of a dense axis: D_hi then D_lo, [np][np] FP32 each
     size_t eig_acc, eig_theta, eig_step, rk[6], lscr, xy, total;
     size_t guard[kMaxGuards];
     int n_guard;
@@ -327,6 +329,14 @@ inline int64_t effective_max_nfft(const spstd_config &cfg)
 
 inline int64_t vsep_rows_padded(int64_t rows) { return (rows + 127) / 128 * 128; }
 
+// A dense axis of an FP32 2D/3D grid with 32..128 points runs on the tensor
+// cores (dense_tc.h); 1D grids keep the resident dense kernel.
+inline bool dense_tc_axis(const spstd_config &cfg, int a)
+{
+    return a < cfg.dims && cfg.dims >= 2 && cfg.precision == 32 && !axis_is_fft(cfg, a) && !axis_is_long(cfg, a) &&
+           dense_tc_eligible(cfg.n[a]);
+}
+
 inline Layout make_layout(const spstd_config &cfg, int m)
 {
     Layout L{};
@@ -374,6 +384,8 @@ inline Layout make_layout(const spstd_config &cfg, int m)
     for (int a = 0; a < 3; ++a)
         L.dense[a] = take(a < cfg.dims && !axis_is_fft(cfg, a) && !axis_is_long(cfg, a)
                               ? es * (size_t)cfg.n[a] * cfg.n[a] : 0);
+    for (int a = 0; a < 3; ++a)
+        L.dense_tc[a] = take(dense_tc_axis(cfg, a) ? 2 * 4 * (size_t)dense_tc_pad(cfg.n[a]) * dense_tc_pad(cfg.n[a]) : 0);
     L.spec = take(spectrum_scratch_bytes(effective_max_nfft(cfg), cfg.probe_capacity));
     L.eig_acc = take(16 * (size_t)cfg.max_eigenstates * ntot);
     L.eig_theta = take(8 * SPSTD_MAX_EIGENSTATES);
@@ -566,6 +578,18 @@ inline double table_a(const spstd_ctx *ctx, int t)
                    : +ctx->c[t / 2] * ctx->dt * cfg.hbar / (2.0 * cfg.mass);
 }
 
+// x rounded to TF32 (FP32 with the 13 low mantissa bits zero: the bits a
+// TF32 MMA reads), to nearest, ties away from zero, via FP32.
+inline double tf32_of(double x)
+{
+    float f = (float)x;
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    if ((u & 0x7f800000u) != 0x7f800000u) u = (u + 0x1000u) & 0xffffe000u;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
 template <typename T>
 spstd_status upload_tables(spstd_ctx *ctx)
 {
@@ -610,6 +634,7 @@ spstd_status upload_tables(spstd_ctx *ctx)
                                   cudaMemcpyHostToDevice, ctx->stream));
     // dense operators of the non-FFT axes, times hbar/2m*
     std::vector<std::vector<T>> dense(3);
+    std::vector<std::vector<float>> tc(3);
     for (int a = 0; a < cfg.dims; ++a) {
         if (!ctx->dense[a]) continue;
         // stored transposed (column-major), so that the threads of a line, one
@@ -622,6 +647,24 @@ spstd_status upload_tables(spstd_ctx *ctx)
                 dense[a][(size_t)j * n + i] = (T)(cfg.hbar / (2.0 * cfg.mass) * D[(size_t)i * n + j]);
         SPSTD_CU(ctx, cudaMemcpyAsync(ctx->ptr(ctx->L.dense[a]), dense[a].data(), sizeof(T) * dense[a].size(),
                                       cudaMemcpyHostToDevice, ctx->stream));
+        if (dense_tc_axis(cfg, a)) {
+            // tensor-core form: rows i, columns j, zero padded to np, in the
+            // MMA operand layout; each entry split in FP64 as hi = TF32(D),
+            // lo = TF32(D - hi)
+            const int np = dense_tc_pad(n);
+            std::vector<float> &t = tc[a];
+            t.assign(2 * (size_t)np * np, 0.f);
+            for (int64_t i = 0; i < n; ++i)
+                for (int64_t j = 0; j < n; ++j) {
+                    const double d = cfg.hbar / (2.0 * cfg.mass) * D[(size_t)i * n + j];
+                    const double hi = tf32_of(d);
+                    const size_t o = dense_tc_offset((int)i, (int)j, np);
+                    t[o] = (float)hi;
+                    t[(size_t)np * np + o] = (float)tf32_of(d - hi);
+                }
+            SPSTD_CU(ctx, cudaMemcpyAsync(ctx->ptr(ctx->L.dense_tc[a]), t.data(), sizeof(float) * t.size(),
+                                          cudaMemcpyHostToDevice, ctx->stream));
+        }
     }
     // the host vectors die here: wait until the copies have read them
     SPSTD_CU(ctx, cudaStreamSynchronize(ctx->stream));
@@ -972,6 +1015,29 @@ cudaError_t enqueue_apply(spstd_ctx *ctx, int fsrc, int fdst, int table, double 
                 da.outer_stride = 0;
                 da.n_lines = n0 * n1;
             }
+            if constexpr (sizeof(T) == 4) {
+                // the tensor-core form (schedule 0 where it applies; 4 keeps the CUDA cores)
+                if (dense_tc_axis(cfg, ax) && sv != 4) {
+                    DenseTcArgs ta{};
+                    ta.src = (const float *)src;
+                    ta.dst = (float *)dst;
+                    ta.V = (const float *)da.V;
+                    ta.Dhi = (const float *)ctx->ptr(ctx->L.dense_tc[ax]);
+                    ta.np = dense_tc_pad(N);
+                    ta.Dlo = ta.Dhi + (size_t)ta.np * ta.np;
+                    ta.a = (float)da.a;
+                    ta.bV = (float)da.bV;
+                    ta.use_V = da.use_V;
+                    ta.n = (int)N;
+                    ta.stride = da.stride;
+                    ta.inner = da.inner;
+                    ta.outer_stride = da.outer_stride;
+                    ta.n_lines = da.n_lines;
+                    ta.status = status;
+                    SPSTD_TIMED(timer, s, ax, launch_dense_tc(ta, s));
+                    continue;
+                }
+            }
             SPSTD_TIMED(timer, s, ax, Launch<T>::dense_pass(da, s));
             continue;
         }
@@ -1238,6 +1304,7 @@ spstd_status prepare_kernels(spstd_ctx *ctx)
     if (cfg.dims == 3 && !ctx->dense[2]) SPSTD_CU(ctx, Launch<T>::spass((int)cfg.n[2], none, ctx->stream));
     if (ctx->fuse_xy) SPSTD_CU(ctx, prepare_xypass_tma((int)cfg.n[0]));
     for (int ax = 0; ax < cfg.dims; ++ax) {
+        if (dense_tc_axis(cfg, ax)) SPSTD_CU(ctx, launch_dense_tc(DenseTcArgs{}, ctx->stream));
         if (ctx->tma[ax]) SPSTD_CU(ctx, prepare_pass_tmared(ax, (int)cfg.n[ax], cfg.n[0], red_planes(cfg.n, ax)));
         if (ctx->tma_st[ax]) SPSTD_CU(ctx, prepare_pass_tma(ax, (int)cfg.n[ax]));
         if (ax == 0 && ctx->xw_ok && ctx->sched[0] == 6) SPSTD_CU(ctx, prepare_pass_xwarp((int)cfg.n[0]));

@@ -8,7 +8,8 @@
 //   2  plain, twice the lines per block
 //   3  plain, half the points per thread (one radix lower per stage), half
 //      the lines per block
-//   4  plain, the default plan (differs from 0 only on TMA axes)
+//   4  plain, the default plan (differs from 0 only on TMA axes); on a dense
+//      wall axis whose 0 is the tensor-core pass: the CUDA-core dense pass
 //   5  the TMA pass with loaded and stored destination tiles (TMA axes only)
 //   6  x axes of 32, 48, 64, 96, 128 or 256 points (FP32 2D/3D grids, single
 //      and batched): the reduce-add TMA pass with per-warp tiles

@@ -10,11 +10,13 @@ namespace {
 
 // Schedules an axis of this context can run (sched.h): 0 always; 1..3 for
 // plain FFT passes of tunable length; 4 and 5 where 0 is the pipelined TMA
-// pass; 6 for x axes that take per-warp tiles.
+// pass; 6 for x axes that take per-warp tiles; on a dense axis whose 0 is the
+// tensor-core pass, 4 (the CUDA-core dense pass).
 int schedule_candidates(const spstd_ctx *ctx, int ax, int *list)
 {
     int n = 0;
     list[n++] = 0;
+    if (ax >= 0 && ax < ctx->cfg.dims && ctx->dense[ax] && dense_tc_axis(ctx->cfg, ax)) list[n++] = 4;
     if (ax < 0 || ax >= ctx->cfg.dims || ctx->dense[ax] || (ax == 0 && ctx->long_x)) return n;
     const int N = (int)ctx->cfg.n[ax];
     for (int v = 1; v <= 3; ++v) {

@@ -1,7 +1,9 @@
 """Wall boundaries (Section 2.2: DST for Dirichlet, DCT for Neumann) and
 lengths that are not powers of two, on the device (dense spectral operator per
-such axis) vs the oracle (transforms of the odd/even extension); and the
-paper's own infinite wells (Tables 2 and 3) run on the device."""
+such axis: on the tensor cores for FP32 2D/3D axes of 32..128 points, else on
+the CUDA cores) vs the oracle (transforms of the odd/even extension); the two
+dense forms against each other; and the paper's own infinite wells (Tables 2
+and 3) run on the device."""
 import os
 
 import numpy as np
@@ -21,6 +23,9 @@ CASES = [
     ((9,), (D,)), ((33,), (D,)), ((10,), (N_,)), ((48,), (P,)), ((96,), (P,)), ((200,), (N_,)),
     ((9, 9), (D, D)), ((12, 64), (D, P)), ((64, 20), (P, N_)),
     ((48, 32, 24), (P, P, P)), ((12, 16, 10), (N_, D, P)), ((16, 9, 64), (P, D, P)),
+    # dense axes of 32..128 points (FP32: the tensor-core pass, ragged lengths padded to 32)
+    ((40, 64), (D, P)), ((64, 33, 16), (P, N_, D)), ((128, 16, 8), (D, P, P)), ((16, 100, 12), (P, D, N_)),
+    ((32, 32, 32), (D, N_, D)),
 ]
 
 
@@ -143,3 +148,33 @@ def test_table3_on_device():
         assert np.min(np.abs(exact - o)) < 0.3 * b, (o / b, exact / b)
     found = sum(np.min(np.abs(om - spstd)) < 0.15 * b for _, _, spstd, _ in tab)
     assert found >= 4, (om / b, tab[:, 2] / b)
+
+
+@pytest.mark.parametrize("case", [((40, 64), (D, P)), ((64, 33, 16), (P, N_, D)), ((128, 16, 8), (D, P, P)),
+                                  ((16, 100, 12), (P, D, N_)), ((96, 48, 40), (N_, D, D))], ids=ids)
+def test_tensor_core_dense_pass_matches_cuda_core_pass(case):
+    """FP32 dense axes of 32..128 points: schedule 0 (tcgen05 TF32 MMAs, 3xTF32
+    split, FP32 accumulation in tensor memory) against schedule 4 (the CUDA-core
+    pass, FP32 products summed in order): H agrees to FP32 rounding of the
+    operator's terms, a few steps to 1e-5, and the steps match the oracle."""
+    p = wall_problem(*case, steps=6)
+    dense_axes = [a for a in range(p.dims) if p.bc[a] != P and 32 <= p.n[a] <= 128]
+    out, hs = [], []
+    for v in (0, 4):
+        s = gpu_solver(p, 32, merge=False)
+        for a in dense_axes:
+            assert 4 in s.spstd_schedule_candidates(a)
+            s.spstd_set_schedule(a, v)
+        hs.append([s.spstd_apply_hamiltonian(w) for w in (0, 1)])
+        s.spstd_step(p.steps)
+        out.append(s.spstd_get_state())
+        s.close()
+    # the bound of the oracle comparison: FP32 rounding of terms as large as
+    # the operator's norm times the field
+    hnorm = p.hbar ** 2 / (2 * p.mass) * sum((np.pi * p.n[a] / (p.hi[a] - p.lo[a])) ** 2
+                                             for a in range(p.dims)) + np.max(np.abs(p.V))
+    for w, f in ((0, p.psiR), (1, p.psiI)):
+        assert np.max(np.abs(hs[0][w] - hs[1][w])) <= 1e-6 * hnorm * np.max(np.abs(f))
+    assert rel_l2(*out[0], *out[1]) <= 1e-5
+    oR, oI, _ = oracle_run(p)
+    assert rel_l2(*out[0], oR, oI) <= 1e-4
