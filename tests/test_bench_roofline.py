@@ -52,8 +52,8 @@ def test_recorded_traffic_only_for_the_recorded_sources(bench, monkeypatch):
     rec = bench.MEASURED_TRAFFIC["aniso_ho_3d_256"]
     # reported while the sources hash to the recorded value
     monkeypatch.setitem(bench.MEASURED_TRAFFIC, "source_hash", bench.traffic_source_hash())
-    assert bench.measured_traffic("aniso_ho_3d_256", "x_pass", 0) == rec["x_pass"][0]
     assert bench.measured_traffic("aniso_ho_3d_256", "x_pass", 6) == rec["x_pass"][6]
+    assert bench.measured_traffic("aniso_ho_3d_256", "y_pass", 0) == rec["y_pass"][0]
     # recorded bytes stay below the algorithmic ones (no re-reads; write-backs land later)
     for k in ("x_pass", "y_pass", "z_pass"):
         for v in rec[k].values():
@@ -61,4 +61,4 @@ def test_recorded_traffic_only_for_the_recorded_sources(bench, monkeypatch):
     assert bench.measured_traffic("aniso_ho_3d_256", "x_pass", 5) is None      # not recorded
     assert bench.measured_traffic("ho_3d_64_fp32", "x_pass", 0) is None         # not recorded
     monkeypatch.setitem(bench.MEASURED_TRAFFIC, "source_hash", "0000000000000000")
-    assert bench.measured_traffic("aniso_ho_3d_256", "x_pass", 0) is None       # kernels changed
+    assert bench.measured_traffic("aniso_ho_3d_256", "x_pass", 6) is None       # kernels changed
