@@ -1333,23 +1333,22 @@ cudaError_t enqueue_rk4_step(spstd_ctx *ctx, cudaStream_t s, LaunchTimer *timer 
     const double b[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
     const double a[4] = {0.0, 0.5, 0.5, 1.0};
     const double k = ctx->dt / ctx->cfg.hbar;
-    cudaError_t e;
-    for (int f = 0; f < 2; ++f) {
-        if ((e = cudaMemcpyAsync(t[f], y[f], bytes, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
-        if ((e = cudaMemcpyAsync(acc[f], y[f], bytes, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
-    }
     const int tH = 2 * ctx->m;
+    cudaError_t e;
     for (int j = 0; j < 4; ++j) {
         for (int f = 0; f < 2; ++f)
             if ((e = cudaMemsetAsync(h[f], 0, bytes, s)) != cudaSuccess) return e;
-        if ((e = enqueue_apply<T>(ctx, 4, 5, tH, 1.0, 0, s, timer)) != cudaSuccess) return e;  // h_R = H t_I
-        if ((e = enqueue_apply<T>(ctx, 3, 6, tH, 1.0, 1, s, timer)) != cudaSuccess) return e;  // h_I = H t_R
-        e = Launch<T>::rk4_update(y[0], y[1], h[0], h[1], acc[0], acc[1], t[0], t[1], ctx->ntot, (T)(b[j] * k),
+        // the first stage's state is y itself (fields 0, 1); later ones t (3, 4)
+        const int tR = j == 0 ? 0 : 3, tI = j == 0 ? 1 : 4;
+        if ((e = enqueue_apply<T>(ctx, tI, 5, tH, 1.0, 0, s, timer)) != cudaSuccess) return e;  // h_R = H t_I
+        if ((e = enqueue_apply<T>(ctx, tR, 6, tH, 1.0, 1, s, timer)) != cudaSuccess) return e;  // h_I = H t_R
+        // the running sum starts from y and, at the last stage, lands in y
+        const T *aR = j == 0 ? y[0] : acc[0], *aI = j == 0 ? y[1] : acc[1];
+        T *oR = j == 3 ? y[0] : acc[0], *oI = j == 3 ? y[1] : acc[1];
+        e = Launch<T>::rk4_update(y[0], y[1], h[0], h[1], aR, aI, oR, oI, t[0], t[1], ctx->ntot, (T)(b[j] * k),
                                   (T)(j < 3 ? a[j + 1] * k : 0.0), j == 3, s);
         if (e != cudaSuccess) return e;
     }
-    for (int f = 0; f < 2; ++f)
-        if ((e = cudaMemcpyAsync(y[f], acc[f], bytes, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
     if (ctx->cfg.n_probe > 0) SPSTD_TIMED(timer, s, 3, Launch<T>::probe(y[0], y[1], probe_args<T>(ctx), s));
     return cudaSuccess;
 }

@@ -614,26 +614,36 @@ __global__ void eigen_accum_kernel(const T *__restrict__ psiR, const T *__restri
         }
         __syncthreads();
         for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+            // every target's accumulator is loaded before any is stored, so the
+            // loads of a point are in flight together
+            double2 a[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+                if (t < n_target) a[t] = acc[(int64_t)t * n + p];
             if constexpr (sizeof(T) == 4) {
                 // FP32 fields: the product in FP32 (the fields carry no more), the
                 // running sum in FP64 -- two FP64 adds a target instead of four
                 // FP64 products, on a part whose FP64 rate is a small fraction of FP32
                 const float zr = psiR[p], zi = psiI[p];
-                for (int t = 0; t < n_target; ++t) {
-                    const float px = (float)s_ph[t].x, py = (float)s_ph[t].y;
-                    double2 a = acc[(int64_t)t * n + p];
-                    a.x += (double)fmaf(zr, px, -zi * py);
-                    a.y += (double)fmaf(zr, py, zi * px);
-                    acc[(int64_t)t * n + p] = a;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    if (t < n_target) {
+                        const float px = (float)s_ph[t].x, py = (float)s_ph[t].y;
+                        a[t].x += (double)fmaf(zr, px, -zi * py);
+                        a[t].y += (double)fmaf(zr, py, zi * px);
+                        acc[(int64_t)t * n + p] = a[t];
+                    }
                 }
             } else {
                 const double zr = (double)psiR[p], zi = (double)psiI[p];
-                for (int t = 0; t < n_target; ++t) {
-                    const double2 ph = s_ph[t];
-                    double2 a = acc[(int64_t)t * n + p];
-                    a.x += zr * ph.x - zi * ph.y;
-                    a.y += zr * ph.y + zi * ph.x;
-                    acc[(int64_t)t * n + p] = a;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    if (t < n_target) {
+                        const double2 ph = s_ph[t];
+                        a[t].x += zr * ph.x - zi * ph.y;
+                        a[t].y += zr * ph.y + zi * ph.x;
+                        acc[(int64_t)t * n + p] = a[t];
+                    }
                 }
             }
         }
@@ -649,21 +659,23 @@ __global__ void eigen_accum_kernel(const T *__restrict__ psiR, const T *__restri
 }
 
 // One Runge-Kutta stage update (Fig. 3's comparison scheme) given hR = H t_I,
-// hI = H t_R:  a_R += cb hR, a_I -= cb hI;  and, unless last, the next stage
-// state t_R = y_R + ca hR, t_I = y_I - ca hI  (cb, ca = stage weight x dt/hbar).
+// hI = H t_R:  o_R = a_R + cb hR, o_I = a_I - cb hI (the running sum: a = y at
+// the first stage, o = y at the last);  and, unless last, the next stage state
+// t_R = y_R + ca hR, t_I = y_I - ca hI  (cb, ca = stage weight x dt/hbar).
 template <typename T>
-__global__ void rk4_update_kernel(const T *__restrict__ yR, const T *__restrict__ yI, const T *__restrict__ hR,
-                                  const T *__restrict__ hI, T *__restrict__ aR, T *__restrict__ aI,
-                                  T *__restrict__ tR, T *__restrict__ tI, int64_t n, T cb, T ca, int last)
+__global__ void rk4_update_kernel(const T *yR, const T *yI, const T *__restrict__ hR, const T *__restrict__ hI,
+                                  const T *aR, const T *aI, T *oR, T *oI, T *__restrict__ tR, T *__restrict__ tI,
+                                  int64_t n, T cb, T ca, int last)
 {
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
         const T r = hR[p], i = hI[p];
-        aR[p] = fma(cb, r, aR[p]);
-        aI[p] = fma(-cb, i, aI[p]);
+        const T ar = aR[p], ai = aI[p];
         if (!last) {
             tR[p] = fma(ca, r, yR[p]);
             tI[p] = fma(-ca, i, yI[p]);
         }
+        oR[p] = fma(cb, r, ar);
+        oI[p] = fma(-cb, i, ai);
     }
 }
 

@@ -148,8 +148,8 @@ template <typename T> struct Launch {
                                       cudaStream_t s);
     static cudaError_t probe_batch(const ProbeMember<T> *members, int count, cudaStream_t s);
     static cudaError_t dense_pass(const DenseArgs<T> &a, cudaStream_t s);
-    static cudaError_t rk4_update(const T *yR, const T *yI, const T *hR, const T *hI, T *aR, T *aI, T *tR, T *tI,
-                                  int64_t n, T cb, T ca, int last, cudaStream_t s);
+    static cudaError_t rk4_update(const T *yR, const T *yI, const T *hR, const T *hI, const T *aR, const T *aI,
+                                  T *oR, T *oI, T *tR, T *tI, int64_t n, T cb, T ca, int last, cudaStream_t s);
     static cudaError_t eigen_accum(const T *psiR, const T *psiI, double2 *acc, int64_t n, int n_target,
                                    const double *theta, int64_t window, int64_t *step, unsigned *done,
                                    cudaStream_t s);

@@ -204,13 +204,13 @@ cudaError_t Launch<T>::eigen_accum(const T *psiR, const T *psiI, double2 *acc, i
 }
 
 template <typename T>
-cudaError_t Launch<T>::rk4_update(const T *yR, const T *yI, const T *hR, const T *hI, T *aR, T *aI, T *tR, T *tI,
-                                  int64_t n, T cb, T ca, int last, cudaStream_t s)
+cudaError_t Launch<T>::rk4_update(const T *yR, const T *yI, const T *hR, const T *hI, const T *aR, const T *aI,
+                                  T *oR, T *oI, T *tR, T *tI, int64_t n, T cb, T ca, int last, cudaStream_t s)
 {
     int64_t b = (n + 255) / 256;
     if (b > 4096) b = 4096;
     if (b < 1) b = 1;
-    rk4_update_kernel<T><<<(unsigned)b, 256, 0, s>>>(yR, yI, hR, hI, aR, aI, tR, tI, n, cb, ca, last);
+    rk4_update_kernel<T><<<(unsigned)b, 256, 0, s>>>(yR, yI, hR, hI, aR, aI, oR, oI, tR, tI, n, cb, ca, last);
     return cudaGetLastError();
 }
 
