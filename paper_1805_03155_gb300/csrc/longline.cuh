@@ -53,19 +53,25 @@ template <typename T, int N2>
 __host__ __device__ constexpr int lrow_tt() { return N2 / line_e<T, N2>::value; }
 template <typename T, int N2>
 __host__ __device__ constexpr int lrow_lpc() { return lrow_tt<T, N2>() >= 256 ? 1 : 256 / lrow_tt<T, N2>(); }
+// The row kernel keeps its twiddle table in shared memory up to kMaxStagedN
+// points; above that it reads the table through L1.  (Staging 4096 FP32
+// twiddles, 32 KB, was measured slower: 155 against 114 us per row launch at
+// 65536-point lines.)
+template <typename T, int N2>
+__host__ __device__ constexpr bool lrow_staged() { return N2 <= kMaxStagedN; }
 template <typename T, int N2>
 __host__ __device__ constexpr size_t lrow_smem()
 {
-    return (N2 <= kMaxStagedN ? align16(sizeof(cpx<T>) * N2) : 0) +
+    return (lrow_staged<T, N2>() ? align16(sizeof(cpx<T>) * N2) : 0) +
            2 * (size_t)lrow_lpc<T, N2>() * (N2 + N2 / 32) * sizeof(cpx<T>);
 }
 
-// W_N^j for 0 <= j < N from the two tables (one complex product).
-template <typename T>
-__device__ __forceinline__ cpx<T> long_twiddle(const LongArgs<T> &a, int64_t j)
+// W_N^j for 0 <= j < N (N <= 2^22) from the two tables (one complex
+// product); N2 is a power of two, so the split of j is a shift and a mask.
+template <typename T, int N2>
+__device__ __forceinline__ cpx<T> long_twiddle(const LongArgs<T> &a, uint32_t j)
 {
-    const int64_t h = j / a.N2;
-    return cmul<T>(a.tw1[h], a.twl[j - h * a.N2]);
+    return cmul<T>(__ldg(a.tw1 + j / N2), __ldg(a.twl + j % N2));
 }
 
 // Column tile of block b: pair p, first column n2.
@@ -112,8 +118,13 @@ lcol_fwd_kernel(const LongArgs<T> a)
     for (int e = 0; e < E; ++e) c[(int64_t)(t + e * TT) * a.N2] = v[e];
 }
 
+// FP32: two blocks per SM.  At one (201 registers a thread for N2 = 4096) the
+// row kernel ran with 8 warps per SM and was bound by latency; FP64 lines
+// (512 threads a block) keep one block, two would spill heavily.
+template <typename T>
+__host__ __device__ constexpr int lrow_min_blocks() { return sizeof(T) == 4 ? 2 : 1; }
 template <typename T, int N2>
-__global__ void __launch_bounds__(lrow_tt<T, N2>() * lrow_lpc<T, N2>())
+__global__ void __launch_bounds__(lrow_tt<T, N2>() * lrow_lpc<T, N2>(), lrow_min_blocks<T>())
 lrow_kernel(const LongArgs<T> a)
 {
     constexpr int E = line_e<T, N2>::value;
@@ -121,11 +132,11 @@ lrow_kernel(const LongArgs<T> a)
     constexpr int LPC = lrow_lpc<T, N2>();
     constexpr int LS = N2 + N2 / 32;
     extern __shared__ __align__(16) unsigned char smem[];
-    constexpr size_t tb = N2 <= kMaxStagedN ? align16(sizeof(cpx<T>) * N2) : 0;
+    constexpr size_t tb = lrow_staged<T, N2>() ? align16(sizeof(cpx<T>) * N2) : 0;
     cpx<T> *s_ex = reinterpret_cast<cpx<T> *>(smem + tb);
     const int t = threadIdx.x, l = threadIdx.y;
     const cpx<T> *tw = a.tw2;
-    if constexpr (N2 <= kMaxStagedN) {
+    if constexpr (lrow_staged<T, N2>()) {
         cpx<T> *s_tw = reinterpret_cast<cpx<T> *>(smem);
         for (int i = l * TT + t; i < N2; i += TT * LPC) s_tw[i] = a.tw2[i];
         __syncthreads();
@@ -145,7 +156,7 @@ lrow_kernel(const LongArgs<T> a)
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         const int n2 = t + e * TT;
-        v[e] = cmul<T>(c[n2], long_twiddle(a, (int64_t)n2 * k1));
+        v[e] = cmul<T>(c[n2], long_twiddle<T, N2>(a, (uint32_t)n2 * (uint32_t)k1));
     }
     XcRow<T, (TT > 32)> xc{s_ex + l * LS, LPC * LS, 0, lane_mask(TT * LPC)};
     fft_line<T, N2, E, false>(v, t, xc, tw);
@@ -163,7 +174,7 @@ lrow_kernel(const LongArgs<T> a)
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             const int n2 = t + e * TT;
-            c[n2] = cmulc<T>(v[e], long_twiddle(a, (int64_t)n2 * k1));
+            c[n2] = cmulc<T>(v[e], long_twiddle<T, N2>(a, (uint32_t)n2 * (uint32_t)k1));
         }
     }
 }
