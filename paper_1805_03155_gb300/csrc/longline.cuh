@@ -171,11 +171,11 @@ lrow_kernel(const LongArgs<T> a)
     }
     fft_line<T, N2, E, true>(v, t, xc, tw);
     if (ok) {
+        // the conjugate twiddles of all elements first, then the products and stores
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const int n2 = t + e * TT;
-            c[n2] = cmulc<T>(v[e], long_twiddle<T, N2>(a, (uint32_t)n2 * (uint32_t)k1));
-        }
+        for (int e = 0; e < E; ++e) v[e] = cmulc<T>(v[e], long_twiddle<T, N2>(a, (uint32_t)(t + e * TT) * (uint32_t)k1));
+#pragma unroll
+        for (int e = 0; e < E; ++e) c[t + e * TT] = v[e];
     }
 }
 
@@ -207,11 +207,30 @@ lcol_inv_kernel(const LongArgs<T> a)
 
     const bool ok1 = 2 * p + 1 < a.n_rows;
     const int64_t b0 = 2 * p * N + n2;
+    // four elements of both lines at a time: their dst, V and src loads are
+    // issued together before the stores (dst may alias nothing the compiler
+    // can see, so it would otherwise wait on each store)
+    constexpr int G = E % 4 == 0 ? 4 : 1;
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const int64_t o = b0 + (int64_t)(t + e * TT) * a.N2;
-        a.dst[o] = fma(a.bV * a.V[o], a.src[o], a.dst[o] + v[e].x);
-        if (ok1) a.dst[o + N] = fma(a.bV * a.V[o + N], a.src[o + N], a.dst[o + N] + v[e].y);
+    for (int e0 = 0; e0 < E; e0 += G) {
+        T d0[G], d1[G], q0[G], q1[G], s0[G], s1[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const int64_t o = b0 + (int64_t)(t + (e0 + g) * TT) * a.N2;
+            d0[g] = a.dst[o];
+            q0[g] = __ldg(a.V + o);
+            s0[g] = __ldg(a.src + o);
+            d1[g] = ok1 ? a.dst[o + N] : T(0);
+            q1[g] = ok1 ? __ldg(a.V + o + N) : T(0);
+            s1[g] = ok1 ? __ldg(a.src + o + N) : T(0);
+        }
+        // the same rounding as one element at a time: dst + result, then + bV V src in one fma
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const int64_t o = b0 + (int64_t)(t + (e0 + g) * TT) * a.N2;
+            a.dst[o] = fma(a.bV * q0[g], s0[g], d0[g] + v[e0 + g].x);
+            if (ok1) a.dst[o + N] = fma(a.bV * q1[g], s1[g], d1[g] + v[e0 + g].y);
+        }
     }
 }
 
