@@ -150,6 +150,9 @@ __device__ __forceinline__ void stage_tables(const PassArgs<T> &a, cpx<T> *s_tw,
 // x pass: contiguous lines.  Block (TT, LPC); line pair lp covers rows 2lp and
 // 2lp+1 (the second may be past the end: its half of the complex line is 0).
 // ---------------------------------------------------------------------------
+// Elements per group of a pass epilogue whose loads are issued together.
+__host__ __device__ constexpr int epi_group(int E) { return E % 4 == 0 ? 4 : E % 2 == 0 ? 2 : 1; }
+
 template <typename T, int N, int LPC, int E = line_e<T, N>::value>
 __device__ __forceinline__ void xpass_body(const PassArgs<T> &a, int64_t blk)
 {
@@ -197,18 +200,35 @@ __device__ __forceinline__ void xpass_body(const PassArgs<T> &a, int64_t blk)
     T *d1 = a.dst + r1 * N;
     const T *V0 = a.use_V ? a.V + r0 * N : nullptr;
     const T *V1 = a.use_V ? a.V + r1 * N : nullptr;
+    // G elements of both lines at a time: their dst, V and src loads are issued
+    // before the stores (which the compiler may not move loads across)
+    constexpr int G = epi_group(E);
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const int i = t + e * TT;
-        if (ok0) {
-            T acc = d0[i] + v[e].x;
-            if (a.use_V) acc = fma(a.bV * V0[i], s0[i], acc);
-            d0[i] = acc;
+    for (int e0 = 0; e0 < E; e0 += G) {
+        T x0[G], x1[G], q0[G], q1[G], u0[G], u1[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const int i = t + (e0 + g) * TT;
+            x0[g] = ok0 ? d0[i] : T(0);
+            x1[g] = ok1 ? d1[i] : T(0);
+            q0[g] = ok0 && a.use_V ? V0[i] : T(0);
+            q1[g] = ok1 && a.use_V ? V1[i] : T(0);
+            u0[g] = ok0 && a.use_V ? s0[i] : T(0);
+            u1[g] = ok1 && a.use_V ? s1[i] : T(0);
         }
-        if (ok1) {
-            T acc = d1[i] + v[e].y;
-            if (a.use_V) acc = fma(a.bV * V1[i], s1[i], acc);
-            d1[i] = acc;
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const int i = t + (e0 + g) * TT;
+            if (ok0) {
+                T acc = x0[g] + v[e0 + g].x;
+                if (a.use_V) acc = fma(a.bV * q0[g], u0[g], acc);
+                d0[i] = acc;
+            }
+            if (ok1) {
+                T acc = x1[g] + v[e0 + g].y;
+                if (a.use_V) acc = fma(a.bV * q1[g], u1[g], acc);
+                d1[i] = acc;
+            }
         }
     }
 }
@@ -278,30 +298,41 @@ __device__ __forceinline__ void spass_body(const PassArgs<T> &a, int64_t blk)
     }
     fft_line<T, N, E, true>(v, t, xc, s_tw);
 
+    // G elements of the column pair at a time: loads before the stores
+    constexpr int G = epi_group(E);
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const int64_t off = base + (int64_t)(t + e * TT) * a.stride;
-        if (vec) {
-            cpx<T> d = *reinterpret_cast<const cpx<T> *>(a.dst + off);
-            d.x += v[e].x;
-            d.y += v[e].y;
+    for (int e0 = 0; e0 < E; e0 += G) {
+        cpx<T> d[G], w[G], sv[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const int64_t off = base + (int64_t)(t + (e0 + g) * TT) * a.stride;
+            if (vec) {
+                d[g] = *reinterpret_cast<const cpx<T> *>(a.dst + off);
+                if (a.use_V) {
+                    sv[g] = *reinterpret_cast<const cpx<T> *>(a.src + off);
+                    w[g] = *reinterpret_cast<const cpx<T> *>(a.V + off);
+                }
+            } else {
+                d[g] = mk<T>(ok0 ? a.dst[off] : T(0), ok1 ? a.dst[off + 1] : T(0));
+                if (a.use_V) {
+                    sv[g] = mk<T>(ok0 ? a.src[off] : T(0), ok1 ? a.src[off + 1] : T(0));
+                    w[g] = mk<T>(ok0 ? a.V[off] : T(0), ok1 ? a.V[off + 1] : T(0));
+                }
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const int64_t off = base + (int64_t)(t + (e0 + g) * TT) * a.stride;
+            cpx<T> r = mk<T>(d[g].x + v[e0 + g].x, d[g].y + v[e0 + g].y);
             if (a.use_V) {
-                const cpx<T> s = *reinterpret_cast<const cpx<T> *>(a.src + off);
-                const cpx<T> w = *reinterpret_cast<const cpx<T> *>(a.V + off);
-                d.x = fma(a.bV * w.x, s.x, d.x);
-                d.y = fma(a.bV * w.y, s.y, d.y);
+                r.x = fma(a.bV * w[g].x, sv[g].x, r.x);
+                r.y = fma(a.bV * w[g].y, sv[g].y, r.y);
             }
-            *reinterpret_cast<cpx<T> *>(a.dst + off) = d;
-        } else {
-            if (ok0) {
-                T acc = a.dst[off] + v[e].x;
-                if (a.use_V) acc = fma(a.bV * a.V[off], a.src[off], acc);
-                a.dst[off] = acc;
-            }
-            if (ok1) {
-                T acc = a.dst[off + 1] + v[e].y;
-                if (a.use_V) acc = fma(a.bV * a.V[off + 1], a.src[off + 1], acc);
-                a.dst[off + 1] = acc;
+            if (vec) {
+                *reinterpret_cast<cpx<T> *>(a.dst + off) = r;
+            } else {
+                if (ok0) a.dst[off] = r.x;
+                if (ok1) a.dst[off + 1] = r.y;
             }
         }
     }
