@@ -191,6 +191,26 @@ spstd_status upload_field(spstd_ctx *ctx, const double *host, size_t off)
     }
     return SPSTD_OK;
 }
+// Uploads state field f (0: psi_R, 1: psi_I) like upload_field and sums the
+// squares of its FP64 values on the device into dout[4 + f]: half of
+// N0 = dV sum(psi_R^2 + psi_I^2), the norm the divergence rule compares with,
+// which the next spstd_energy_norm reads back with its own results.  The sum is
+// taken from the FP64 values before any rounding to FP32, and no host pass
+// over the arrays is needed.
+template <typename T>
+spstd_status upload_state_field(spstd_ctx *ctx, const double *host, int f)
+{
+    cudaStream_t s = ctx->stream;
+    double *v64 = sizeof(T) == 8 ? (double *)ctx->ptr(ctx->L.psi[f]) : (double *)ctx->ptr(ctx->L.staging);
+    double *part = (double *)ctx->ptr(ctx->L.partial);
+    double *dout = (double *)ctx->ptr(ctx->L.dout);
+    const int nb = (int)std::min<int64_t>(kPartials, (ctx->ntot + 255) / 256);
+    SPSTD_CU(ctx, cudaMemcpyAsync(v64, host, 8 * ctx->ntot, cudaMemcpyHostToDevice, s));
+    SPSTD_CU(ctx, Launch<double>::dot2(v64, v64, nullptr, nullptr, ctx->ntot, part, nb, s));
+    SPSTD_CU(ctx, launch_sum_partials(part, nb, dout + 4 + f, s));
+    if (sizeof(T) == 4) SPSTD_CU(ctx, Launch<T>::from_f64(v64, (T *)ctx->ptr(ctx->L.psi[f]), ctx->ntot, s));
+    return SPSTD_OK;
+}
 template <typename T>
 spstd_status download_field(spstd_ctx *ctx, const void *dev, double *host)
 {
@@ -246,19 +266,15 @@ spstd_status spstd_set_potential(spstd_ctx *ctx, const double *V)
 spstd_status spstd_set_state(spstd_ctx *ctx, const double *psiR, const double *psiI)
 {
     if (!ctx || !psiR || !psiI) return SPSTD_EINVAL;
-    spstd_status s = ctx->cfg.precision == 32 ? upload_field<float>(ctx, psiR, ctx->L.psi[0])
-                                              : upload_field<double>(ctx, psiR, ctx->L.psi[0]);
+    spstd_status s = ctx->cfg.precision == 32 ? upload_state_field<float>(ctx, psiR, 0)
+                                              : upload_state_field<double>(ctx, psiR, 0);
     if (s != SPSTD_OK) return s;
-    s = ctx->cfg.precision == 32 ? upload_field<float>(ctx, psiI, ctx->L.psi[1])
-                                 : upload_field<double>(ctx, psiI, ctx->L.psi[1]);
+    s = ctx->cfg.precision == 32 ? upload_state_field<float>(ctx, psiI, 1)
+                                 : upload_state_field<double>(ctx, psiI, 1);
     if (s != SPSTD_OK) return s;
     SPSTD_CU(ctx, cudaMemsetAsync(ctx->ptr(ctx->L.counter), 0, 8, ctx->stream));
     ctx->steps_taken = 0;
-    // N0 = dV sum(psi_R^2 + psi_I^2) of the given state, for the divergence rule
-    double acc = 0.0, dV = 1.0;
-    for (int64_t i = 0; i < ctx->ntot; ++i) acc += psiR[i] * psiR[i] + psiI[i] * psiI[i];
-    for (int a = 0; a < ctx->cfg.dims; ++a) dV *= axis_spacing(ctx->cfg, a);
-    ctx->norm0 = dV * acc;
+    ctx->norm0_pending = true;
     return SPSTD_OK;
 }
 
@@ -382,13 +398,18 @@ spstd_status energy_norm_impl(spstd_ctx *ctx, double *norm, double *energy)
     SPSTD_CU(ctx, enqueue_apply<T>(ctx, 1, 2, tH, 1.0, 0, s));
     SPSTD_CU(ctx, Launch<T>::dot2(pi, tmp, nullptr, nullptr, ctx->ntot, part, nb, s));
     SPSTD_CU(ctx, launch_sum_partials(part, nb, dout + 2, s));
-    double h[3];
+    // dout[4], dout[5]: the sums of squares of the state last set (N0)
+    double h[6];
     SPSTD_CU(ctx, cudaMemcpyAsync(h, dout, sizeof(h), cudaMemcpyDeviceToHost, s));
     SPSTD_CU(ctx, cudaStreamSynchronize(s));
     spstd_status ds = check_device_status(ctx);
     if (ds != SPSTD_OK) return ds;
     double dV = 1.0;
     for (int a = 0; a < ctx->cfg.dims; ++a) dV *= axis_spacing(ctx->cfg, a);
+    if (ctx->norm0_pending) {
+        ctx->norm0 = dV * (h[4] + h[5]);
+        ctx->norm0_pending = false;
+    }
     *norm = dV * h[0];
     *energy = dV * (h[1] + h[2]);
     if (!std::isfinite(*norm) || !std::isfinite(*energy)) return fail(ctx, SPSTD_EDIVERGED, "norm or energy is not finite");

@@ -417,6 +417,7 @@ struct spstd_ctx {
     std::vector<HalfStage> hs;
     int64_t steps_taken = 0;
     double norm0 = 0.0;  // norm of the state last set (divergence rule)
+    bool norm0_pending = false;  // its two FP64 sums wait in dout[4], dout[5] on the device
     cudaGraphExec_t gexec = nullptr;
     std::string err;
     // pipelined FP32 passes: tensor maps [field: psi_R, psi_I, tmp][view: x, y, z]
@@ -1367,11 +1368,38 @@ cudaError_t enqueue_eigen_step(spstd_ctx *ctx, cudaStream_t s, LaunchTimer *time
     return cudaSuccess;
 }
 
+// Captures the graph that 2D/3D steps replay: kGraphSteps units with merged
+// step boundaries, else kGraphSteps steps.  It is done on the first step call
+// of a context (or the first after a change that dropped the graph), whatever
+// that call's length, so that the capture and instantiation never fall inside
+// a later, longer call.
+template <typename T>
+spstd_status ensure_graph(spstd_ctx *ctx)
+{
+    if (ctx->gexec || ctx->cfg.no_graph) return SPSTD_OK;
+    spstd_status ps = prepare_kernels<T>(ctx);
+    if (ps != SPSTD_OK) return ps;
+    cudaGraph_t g = nullptr;
+    SPSTD_CU(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = ctx->merge ? enqueue_merged_piece<T>(ctx, 1, kGraphSteps, ctx->cap_stream)
+                               : enqueue_steps<T>(ctx, kGraphSteps, ctx->cap_stream);
+    cudaError_t e2 = cudaStreamEndCapture(ctx->cap_stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(ctx, e != cudaSuccess ? e : e2, "graph capture");
+    }
+    e = cudaGraphInstantiate(&ctx->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        ctx->gexec = nullptr;
+        return cuda_fail(ctx, e, "cudaGraphInstantiate");
+    }
+    return SPSTD_OK;
+}
+
 template <typename T>
 spstd_status step_impl(spstd_ctx *ctx, int64_t nsteps)
 {
-    T *psi0 = (T *)ctx->ptr(ctx->L.psi[0]);
-    T *psi1 = (T *)ctx->ptr(ctx->L.psi[1]);
     if (ctx->rk4 && !ctx->eig_active) {
         for (int64_t i = 0; i < nsteps; ++i) SPSTD_CU(ctx, enqueue_rk4_step<T>(ctx, ctx->stream));
         ctx->steps_taken += nsteps;
@@ -1387,31 +1415,15 @@ spstd_status step_impl(spstd_ctx *ctx, int64_t nsteps)
         ctx->steps_taken += nsteps;
         return SPSTD_OK;
     }
+    spstd_status gs = ensure_graph<T>(ctx);
+    if (gs != SPSTD_OK) return gs;
     cudaError_t e;
     if (ctx->merge) {
         // head, graph-replayed units, remaining units, tail
         const int64_t units = nsteps - 1;
         SPSTD_CU(ctx, enqueue_merged_piece<T>(ctx, 0, 0, ctx->stream));
         int64_t done = 0;
-        if (units >= kGraphSteps && !ctx->cfg.no_graph) {
-            if (!ctx->gexec) {
-                spstd_status ps = prepare_kernels<T>(ctx);
-                if (ps != SPSTD_OK) return ps;
-                cudaGraph_t g = nullptr;
-                SPSTD_CU(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
-                e = enqueue_merged_piece<T>(ctx, 1, kGraphSteps, ctx->cap_stream);
-                cudaError_t e2 = cudaStreamEndCapture(ctx->cap_stream, &g);
-                if (e != cudaSuccess || e2 != cudaSuccess) {
-                    if (g) cudaGraphDestroy(g);
-                    return cuda_fail(ctx, e != cudaSuccess ? e : e2, "graph capture");
-                }
-                e = cudaGraphInstantiate(&ctx->gexec, g, 0);
-                cudaGraphDestroy(g);
-                if (e != cudaSuccess) {
-                    ctx->gexec = nullptr;
-                    return cuda_fail(ctx, e, "cudaGraphInstantiate");
-                }
-            }
+        if (ctx->gexec) {
             for (int64_t r = 0; r < units / kGraphSteps; ++r) SPSTD_CU(ctx, cudaGraphLaunch(ctx->gexec, ctx->stream));
             done = units / kGraphSteps * kGraphSteps;
         }
@@ -1420,26 +1432,7 @@ spstd_status step_impl(spstd_ctx *ctx, int64_t nsteps)
         ctx->steps_taken += nsteps;
         return SPSTD_OK;
     }
-    if (nsteps >= kGraphSteps && !ctx->cfg.no_graph) {
-        if (!ctx->gexec) {
-            spstd_status ps = prepare_kernels<T>(ctx);
-            if (ps != SPSTD_OK) return ps;
-            cudaGraph_t g = nullptr;
-            SPSTD_CU(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
-            e = enqueue_steps<T>(ctx, kGraphSteps, ctx->cap_stream);
-            if (e != cudaSuccess) {
-                cudaStreamEndCapture(ctx->cap_stream, &g);
-                if (g) cudaGraphDestroy(g);
-                return cuda_fail(ctx, e, "graph capture");
-            }
-            SPSTD_CU(ctx, cudaStreamEndCapture(ctx->cap_stream, &g));
-            e = cudaGraphInstantiate(&ctx->gexec, g, 0);
-            cudaGraphDestroy(g);
-            if (e != cudaSuccess) {
-                ctx->gexec = nullptr;
-                return cuda_fail(ctx, e, "cudaGraphInstantiate");
-            }
-        }
+    if (ctx->gexec) {
         const int64_t reps = nsteps / kGraphSteps;
         for (int64_t i = 0; i < reps; ++i) SPSTD_CU(ctx, cudaGraphLaunch(ctx->gexec, ctx->stream));
         nsteps -= reps * kGraphSteps;
