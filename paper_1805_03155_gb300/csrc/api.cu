@@ -211,6 +211,8 @@ spstd_status upload_state_field(spstd_ctx *ctx, const double *host, int f)
     if (sizeof(T) == 4) SPSTD_CU(ctx, Launch<T>::from_f64(v64, (T *)ctx->ptr(ctx->L.psi[f]), ctx->ntot, s));
     return SPSTD_OK;
 }
+// Enqueues the copy of a field to host FP64 values (through the FP64 staging
+// field for FP32); the caller synchronises (check_device_status does).
 template <typename T>
 spstd_status download_field(spstd_ctx *ctx, const void *dev, double *host)
 {
@@ -221,8 +223,7 @@ spstd_status download_field(spstd_ctx *ctx, const void *dev, double *host)
         SPSTD_CU(ctx, Launch<T>::to_f64((const T *)dev, st, ctx->ntot, ctx->stream));
         SPSTD_CU(ctx, cudaMemcpyAsync(host, st, 8 * ctx->ntot, cudaMemcpyDeviceToHost, ctx->stream));
     }
-    SPSTD_CU(ctx, cudaStreamSynchronize(ctx->stream));
-    return check_device_status(ctx);
+    return SPSTD_OK;
 }
 }  // namespace
 
@@ -281,11 +282,15 @@ spstd_status spstd_set_state(spstd_ctx *ctx, const double *psiR, const double *p
 spstd_status spstd_get_state(spstd_ctx *ctx, double *psiR, double *psiI)
 {
     if (!ctx || !psiR || !psiI) return SPSTD_EINVAL;
+    // both fields are enqueued before the one synchronisation (the status read):
+    // in stream order the staging field is not reused before its copy is done
     spstd_status s = ctx->cfg.precision == 32 ? download_field<float>(ctx, ctx->ptr(ctx->L.psi[0]), psiR)
                                               : download_field<double>(ctx, ctx->ptr(ctx->L.psi[0]), psiR);
     if (s != SPSTD_OK) return s;
-    return ctx->cfg.precision == 32 ? download_field<float>(ctx, ctx->ptr(ctx->L.psi[1]), psiI)
-                                    : download_field<double>(ctx, ctx->ptr(ctx->L.psi[1]), psiI);
+    s = ctx->cfg.precision == 32 ? download_field<float>(ctx, ctx->ptr(ctx->L.psi[1]), psiI)
+                                 : download_field<double>(ctx, ctx->ptr(ctx->L.psi[1]), psiI);
+    if (s != SPSTD_OK) return s;
+    return check_device_status(ctx);
 }
 
 spstd_status spstd_step(spstd_ctx *ctx, int64_t nsteps)
@@ -303,18 +308,24 @@ spstd_status spstd_probe(spstd_ctx *ctx, int p, double *re, double *im, int64_t 
     if (ctx->steps_taken == 0) return fail(ctx, SPSTD_ENOTREADY, "no step recorded since set_state");
     const int64_t C = ctx->cfg.probe_capacity;
     const int64_t kept = std::min(ctx->steps_taken, C);
-    std::vector<double2> row(C);
-    SPSTD_CU(ctx, cudaMemcpyAsync(row.data(), (double2 *)ctx->ptr(ctx->L.ring) + (size_t)p * C, sizeof(double2) * C,
-                                  cudaMemcpyDeviceToHost, ctx->stream));
-    SPSTD_CU(ctx, cudaStreamSynchronize(ctx->stream));
-    spstd_status ds = check_device_status(ctx);
-    if (ds != SPSTD_OK) return ds;
     const int64_t nout = std::min(kept, cap);
     const int64_t first = ctx->steps_taken - nout;  // global index of the first sample returned
+    // only the samples returned are copied: one piece of the ring, or two where
+    // it wraps; the status read below synchronises the stream for them
+    std::vector<double2> row((size_t)nout);
+    const double2 *ring = (const double2 *)ctx->ptr(ctx->L.ring) + (size_t)p * C;
+    const int64_t i0 = nout > 0 ? first % C : 0;
+    const int64_t n1 = std::min(nout, C - i0);
+    if (n1 > 0)
+        SPSTD_CU(ctx, cudaMemcpyAsync(row.data(), ring + i0, sizeof(double2) * n1, cudaMemcpyDeviceToHost, ctx->stream));
+    if (nout > n1)
+        SPSTD_CU(ctx, cudaMemcpyAsync(row.data() + n1, ring, sizeof(double2) * (nout - n1), cudaMemcpyDeviceToHost,
+                                      ctx->stream));
+    spstd_status ds = check_device_status(ctx);
+    if (ds != SPSTD_OK) return ds;
     for (int64_t i = 0; i < nout; ++i) {
-        const double2 v = row[(first + i) % C];
-        re[i] = v.x;
-        im[i] = v.y;
+        re[i] = row[i].x;
+        im[i] = row[i].y;
     }
     *len = nout;
     return SPSTD_OK;
@@ -431,7 +442,8 @@ spstd_status apply_h_impl(spstd_ctx *ctx, int which, double *out)
     SPSTD_CU(ctx, cudaMemsetAsync(tmp, 0, sizeof(T) * ctx->ntot, ctx->stream));
     (void)src;
     SPSTD_CU(ctx, enqueue_apply<T>(ctx, which, 2, 2 * ctx->m, 1.0, 0, ctx->stream));
-    return download_field<T>(ctx, tmp, out);
+    spstd_status st = download_field<T>(ctx, tmp, out);
+    return st != SPSTD_OK ? st : check_device_status(ctx);
 }
 }  // namespace
 
