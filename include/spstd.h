@@ -217,7 +217,12 @@ spstd_status spstd_separable_split(const double *V, int64_t nx, int64_t rows, fl
                                    int *separable);
 
 /* Copies the state (host, FP64, n_total values each) to the device and resets
- * the probe recorder (step counter 0, no samples). */
+ * the probe recorder (step counter 0, no samples).  The norm N0 of the
+ * divergence rule is summed on the device from these FP64 values; the next
+ * spstd_energy_norm reads it back.  Enqueued on cfg.stream: pageable host
+ * arrays are read before the call returns; pinned (page-locked) ones are read
+ * by the copies as the stream reaches them, so they must not change until
+ * then. */
 spstd_status spstd_set_state(spstd_ctx *ctx, const double *psiR, const double *psiI);
 
 /* Copies the current state to the host as FP64 (synchronises). */
@@ -227,7 +232,9 @@ spstd_status spstd_get_state(spstd_ctx *ctx, double *psiR, double *psiI);
  *     psi_R += c_l dt K psi_I,  then  psi_I -= d_l dt K psi_R,
  * K = -(hbar/2m*) lap + V/hbar (Eq. 16), zero coefficients skipped, and after
  * every step records psi_R + i psi_I at each probe.  nsteps = 0 is a no-op.
- * Asynchronous; repeated chunks are replayed from a captured CUDA graph. */
+ * Asynchronous; repeated chunks are replayed from a captured CUDA graph (2D
+ * and 3D grids), which the first call on a context captures whatever its
+ * length (and the first call after a change of schedule or potential). */
 spstd_status spstd_step(spstd_ctx *ctx, int64_t nsteps);
 
 /* Copies the recorded series of probe p (0 <= p < n_probe), oldest first,
