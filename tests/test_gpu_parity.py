@@ -164,6 +164,12 @@ def test_probe_ring_keeps_latest_samples():
     _, _, opr = oracle_run(p, steps=50)
     assert len(z) == 16
     assert np.max(np.abs(z - opr[1, -16:])) < 1e-12
+    # shorter reads return the latest samples: across the ring's wrap (50 steps
+    # in a 16-slot ring: samples 45..49 sit in slots 13, 14, 15, 0, 1) and not
+    for cap in (5, 3, 2, 1):
+        z = s.spstd_probe(1, cap=cap)
+        assert len(z) == cap
+        assert np.max(np.abs(z - opr[1, -cap:])) < 1e-12
 
 
 @pytest.mark.parametrize("precision", [64, 32])
