@@ -11,11 +11,11 @@ Workloads (atomic units, hbar = m* = 1; periodic boxes, x fastest):
 
 * ``well_1d``  -- finite quantum well: N = 256 on [-20, 20], V = 0 for |x| < 2
   and V0 = 5 outside; psi_R a Gaussian (centre U(-1, 1), width 0.5) plus 1e-3
-  N(0, 1) noise per point, psi_I = 0, normalised; 4 probes with |x| < 3;
+  N(0, 1) noise per point, psi_I = 0, normalised; 4 probes with |x| <= 3;
   FR4 integrator, 20000 steps.
 * ``ho_3d``    -- isotropic harmonic oscillator: 64^3 on [-8, 8]^3, V =
   omega^2 r^2 / 2 with omega = 1; a Gaussian of width 0.7 displaced by
-  U(-0.5, 0.5) per axis; 8 probes with |r_d| < 2; FR4, 10000 steps.
+  U(-0.5, 0.5) per axis; 8 probes with |r_d| <= 2; FR4, 10000 steps.
 * ``aniso_ho_3d`` -- anisotropic oscillator at scale: 256^3 on [-12, 12]^3,
   omegas (1.0, 1.3, 1.7); five Gaussians (centres U(-2, 2)^3, widths
   U(0.5, 1.0), amplitudes +-U(0.5, 1)); SUZUKI6, 50000 steps, 8 probes,
@@ -136,7 +136,8 @@ def _normalise(psiR, psiI, n, lo, hi, dims, bc=(0, 0, 0)):
 
 
 def _central_probes(rng, n, lo, hi, dims, half_width, count):
-    """Flat indices of grid points drawn uniformly with |x_d| < half_width."""
+    """Flat indices of grid points drawn uniformly with |x_d| <= half_width
+    (the grid points at +-half_width included)."""
     ranges = []
     for a in range(3):
         if a >= dims:
