@@ -99,3 +99,16 @@ def test_batch_mix_composition(count):
     # the same seed gives the same mix
     again = inputs.batch_mix(count=count, steps=7)
     assert all(np.array_equal(a.psiR, b.psiR) and np.array_equal(a.V, b.V) for a, b in zip(mix, again))
+
+
+def test_aniso_ho_3d_recipe():
+    p = inputs.aniso_ho_3d()
+    assert p.dims == 3 and p.n == (256, 256, 256) and p.lo == (-12.0,) * 3 and p.hi == (12.0,) * 3
+    x = p.coords()
+    idx = inputs.SplitMix64(5).integers(2000, 0, p.n_total)
+    i, j, k = idx % 256, (idx // 256) % 256, idx // 65536
+    want = 0.5 * (x[0][i] ** 2 + 1.3 ** 2 * x[1][j] ** 2 + 1.7 ** 2 * x[2][k] ** 2)
+    assert np.allclose(p.V[idx], want, rtol=1e-15, atol=0)
+    assert abs(_cell(p) * np.sum(p.psiR ** 2) - 1.0) < 1e-12 and not np.any(p.psiI)
+    assert len(p.probes) == 8 and all(max(abs(c) for c in _coords_of(p, q)) <= 2 for q in p.probes)
+    assert p.integrator == "SUZUKI6" and p.dt == 6.52e-4 and p.steps == 50000 and p.nfft == 1 << 16
