@@ -90,8 +90,31 @@ def test_graph_replay_equals_single_steps(shape):
     a = gpu_run(p, 64, chunks=[40], merge=False)
     b = gpu_run(p, 64, chunks=[1] * 40, merge=False)
     c = gpu_run(p, 64, chunks=[17, 3, 16, 4], merge=False)
-    for x, y in ((a, b), (a, c)):
+    # a short first call captures the graph without replaying it; the next,
+    # longer call replays it
+    d = gpu_run(p, 64, chunks=[5, 20, 15], merge=False)
+    for x, y in ((a, b), (a, c), (a, d)):
         assert np.array_equal(x[0], y[0]) and np.array_equal(x[1], y[1]) and np.array_equal(x[2], y[2])
+
+
+@pytest.mark.parametrize("shape", [(16, 32), (8, 16, 32)], ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("precision", [64, 32])
+def test_graph_captured_by_a_short_first_call(shape, precision):
+    """With merged step boundaries, a short first call (which captures the
+    step graph) and a longer second call (which replays it) give the same bits
+    as the same calls with every kernel launched directly."""
+    p = small_problem(shape, integrator="SUZUKI6", steps=23)
+    out = []
+    for no_graph in (False, True):
+        s = gpu_solver(p, precision, cap=23, no_graph=no_graph)
+        s.spstd_step(3)
+        s.spstd_step(20)
+        R, Im = s.spstd_get_state()
+        z = np.array([s.spstd_probe(q) for q in range(len(p.probes))])
+        s.close()
+        out.append((R, Im, z))
+    for k in range(3):
+        assert np.array_equal(out[0][k], out[1][k])
 
 
 @pytest.mark.parametrize("shape,integrator", [((16, 32), "FR4"), ((8, 16, 32), "SUZUKI6"), ((32, 16), "STRANG"),
